@@ -1,0 +1,188 @@
+"""Pins of the oracle's genetic layer (Section IV): operation statistics,
+5%/95% adaptive choice, island neighbour for Xrossover, pool insertion as
+top-C of the union without duplicates, determinism, and solution quality
+against brute force on the n = 20 twin of the small dense workload."""
+import numpy as np
+import pytest
+
+from paper_2207_03069_gb300 import workloads as wl
+
+
+def fixed_pools(orc, n, P, C, algo=3, op=None, xs=None):
+    X = np.zeros((P, C, n), np.uint8)
+    for p in range(P):
+        X[p, :, :] = xs[p] if xs is not None else 0
+    E = np.tile(np.arange(C, dtype=np.int64), (P, 1))
+    a = np.full((P, C), algo, np.int32)
+    o = np.full((P, C), 0 if op is None else op, np.int32)
+    return X, E, a, o
+
+
+def offspring_stats(orc, n, op, xs, gens=40, S=64, P=2):
+    W = wl.dense_qubo(n, -5, 5, 1)
+    so = orc.Solver(W, orc.make_params(searches=S, pools=P, pool_cap=16), seed=99)
+    so.set_pools(*fixed_pools(orc, n, P, 16, op=op, xs=xs))
+    out = []
+    for g in range(gens):
+        D, a, o = so.offspring(g)
+        keep = o == op
+        out.append((D[keep], np.arange(S)[keep] % P, a[keep]))
+    return out
+
+
+def test_mutation_zero_one_rates(orc):
+    n = 256
+    rng = np.random.default_rng(3)
+    xs = [rng.integers(0, 2, n).astype(np.uint8) for _ in range(2)]
+    for op, name in ((0, "mut"), (3, "zero"), (4, "one")):
+        changed, base = 0, 0
+        for D, pool, _ in offspring_stats(orc, n, op, xs):
+            for d, p in zip(D, pool):
+                x = xs[p]
+                if name == "mut":
+                    changed += int((d != x).sum()); base += n
+                elif name == "zero":
+                    assert not ((x == 0) & (d == 1)).any()
+                    changed += int(((x == 1) & (d == 0)).sum()); base += int((x == 1).sum())
+                else:
+                    assert not ((x == 1) & (d == 0)).any()
+                    changed += int(((x == 0) & (d == 1)).sum()); base += int((x == 0).sum())
+        rate = changed / base
+        assert abs(rate - 1 / 8) < 0.01, (name, rate)
+
+
+def test_crossover_xrossover_best_random_intervalzero(orc):
+    n = 200
+    rng = np.random.default_rng(4)
+    xs = [rng.integers(0, 2, n).astype(np.uint8) for _ in range(2)]
+    # Crossover within one pool of identical vectors reproduces the vector
+    for D, pool, _ in offspring_stats(orc, n, 1, xs):
+        for d, p in zip(D, pool):
+            assert np.array_equal(d, xs[p])
+    # Xrossover mixes own pool p with pool (p+1) mod P about half/half
+    frac = []
+    for D, pool, _ in offspring_stats(orc, n, 2, xs):
+        for d, p in zip(D, pool):
+            a, b = xs[p], xs[(p + 1) % 2]
+            diff = a != b
+            assert np.all((d == a) | (d == b))
+            frac.append((d[diff] == b[diff]).mean())
+    assert abs(np.mean(frac) - 0.5) < 0.03
+    for D, pool, _ in offspring_stats(orc, n, 6, xs):  # Best
+        for d, p in zip(D, pool):
+            assert np.array_equal(d, xs[p])
+    ones = [d.mean() for D, _, _ in offspring_stats(orc, n, 7, xs) for d in D]  # Random
+    assert abs(np.mean(ones) - 0.5) < 0.02
+    ones_x = [np.ones(n, np.uint8), np.ones(n, np.uint8)]
+    for D, pool, _ in offspring_stats(orc, n, 5, ones_x):  # IntervalZero
+        for d in D:
+            z = np.nonzero(d == 0)[0]
+            assert 32 <= len(z) <= n // 2
+            # one cyclic segment: at most one 1->0 boundary going around
+            edges = int(((d == 1) & (np.roll(d, -1) == 0)).sum())
+            assert edges == 1
+
+
+def test_adaptive_choice_five_percent(orc):
+    n, S = 64, 256
+    W = wl.dense_qubo(n, -5, 5, 1)
+    so = orc.Solver(W, orc.make_params(searches=S, pools=4, pool_cap=16), seed=5)
+    so.set_pools(*fixed_pools(orc, n, 4, 16, algo=3, op=5))
+    oth_a = oth_o = tot = 0
+    for g in range(60):
+        _, a, o = so.offspring(g)
+        oth_a += int((a != 3).sum())
+        oth_o += int((o != 5).sum())
+        tot += S
+    # 5% uniform choice lands on another value with probability 4/5 resp. 7/8
+    assert abs(oth_a / tot - 0.05 * 4 / 5) < 0.006
+    assert abs(oth_o / tot - 0.05 * 7 / 8) < 0.006
+
+
+def reference_merge(pX, pE, pa, po, rX, rE, ra, ro, P):
+    """Top-C of (pool entries, then results in search order) by energy,
+    earlier first on ties, dropping a later copy of an equal (E, X)."""
+    P_, C, n = pX.shape
+    out = []
+    for p in range(P):
+        items = [(pE[p, k], 0, k, pX[p, k], pa[p, k], po[p, k]) for k in range(C)]
+        items += [(rE[s], 1, s, rX[s], ra[s], ro[s]) for s in range(len(rE)) if s % P == p]
+        seen, uniq = set(), []
+        for it in items:
+            key = (int(it[0]), it[3].tobytes())
+            if key in seen:
+                continue
+            seen.add(key)
+            uniq.append(it)
+        uniq.sort(key=lambda it: (it[0], it[1], it[2]))
+        out.append(uniq[:C])
+    return out
+
+
+def test_pool_merge_is_top_c_of_union(orc):
+    n, S, P, C = 16, 48, 3, 8
+    W = wl.dense_qubo(n, -5, 5, 1)
+    rng = np.random.default_rng(8)
+    so = orc.Solver(W, orc.make_params(searches=S, pools=P, pool_cap=C), seed=1)
+    pX = rng.integers(0, 2, (P, C, n)).astype(np.uint8)
+    pE = np.sort(rng.integers(-20, 20, (P, C)), axis=1).astype(np.int64)
+    pa = rng.integers(0, 5, (P, C)).astype(np.int32)
+    po = rng.integers(0, 8, (P, C)).astype(np.int32)
+    so.set_pools(pX, pE, pa, po)
+    rX = rng.integers(0, 2, (S, n)).astype(np.uint8)
+    rE = rng.integers(-25, 25, S).astype(np.int64)
+    rX[5] = pX[5 % P, 2]; rE[5] = pE[5 % P, 2]            # duplicate of a pool entry
+    rX[7] = rX[4]; rE[7] = rE[4]; rX[10] = rX[4]; rE[10] = rE[4]  # duplicate results
+    ra = rng.integers(0, 5, S).astype(np.int32)
+    ro = rng.integers(0, 8, S).astype(np.int32)
+    so.merge(rX, rE, ra, ro)
+    X, E, a, o = so.pools()
+    ref = reference_merge(pX, pE, pa, po, rX, rE, ra, ro, P)
+    for p in range(P):
+        assert list(E[p]) == [int(it[0]) for it in ref[p]]
+        for k, it in enumerate(ref[p]):
+            assert np.array_equal(X[p, k], it[3]) and a[p, k] == it[4] and o[p, k] == it[5]
+
+
+def test_pool_init_random_with_infinite_energy(orc):
+    n = 300
+    W = wl.dense_qubo(n, -5, 5, 1)
+    so = orc.Solver(W, orc.make_params(searches=8, pools=4, pool_cap=32), seed=3)
+    X, E, a, o = so.pools()
+    assert (E == orc.INT64_MAX).all()
+    assert abs(X.mean() - 0.5) < 0.01
+    assert set(np.unique(a)) == set(range(5)) and set(np.unique(o)) == set(range(8))
+
+
+def test_solver_threads_do_not_change_results(orc):
+    W = wl.dense_qubo(64, -100, 100, 0)
+    p = orc.make_params(searches=32, pools=4, pool_cap=64, max_generations=6)
+    r1 = orc.solve(W, p, budget=2**63, seed=1, threads=1)
+    r4 = orc.solve(W, p, budget=2**63, seed=1, threads=4)
+    assert r1[1] == r4[1] and r1[2] == r4[2] and np.array_equal(r1[0], r4[0])
+    assert r1[1] == orc.energy(W, r1[0])
+
+
+def test_solver_reaches_brute_force_optimum_n20(orc):
+    """Quality sanity on the n = 20 twin of the small dense workload
+    (weights uniform in [-100, 100], seed 0)."""
+    W = wl.dense_qubo(20, -100, 100, 0)
+    emin, _, _ = wl.brute_force_min(W)
+    p = orc.make_params(searches=32, pools=4, pool_cap=64, max_generations=50)
+    X, E, flips, gens = orc.solve(W, p, budget=2**63, seed=0, target=emin)
+    assert E == emin and orc.energy(W, X) == emin
+    assert gens <= 50
+
+
+def test_solver_budget_and_target_stop(orc):
+    W = wl.dense_qubo(64, -100, 100, 0)
+    p = orc.make_params(searches=32, pools=4, pool_cap=64)
+    X, E, flips, gens = orc.solve(W, p, budget=10000, seed=4)
+    assert flips >= 10000 and gens >= 1
+    so = orc.Solver(W, p, seed=4)
+    f = 0
+    for _ in range(gens - 1):
+        f += so.generation()
+    assert f < 10000
+    X2, E2, _, g2 = orc.solve(W, p, budget=2**63, seed=4, target=E)
+    assert E2 <= E and g2 <= gens
