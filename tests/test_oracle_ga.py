@@ -83,6 +83,23 @@ def test_crossover_xrossover_best_random_intervalzero(orc):
             assert edges == 1
 
 
+def test_best_takes_the_first_pool_entry(orc):
+    n, S, P, C = 40, 32, 2, 8
+    W = wl.dense_qubo(n, -5, 5, 1)
+    rng = np.random.default_rng(12)
+    so = orc.Solver(W, orc.make_params(searches=S, pools=P, pool_cap=C), seed=7)
+    pX = rng.integers(0, 2, (P, C, n)).astype(np.uint8)
+    so.set_pools(pX, np.tile(np.arange(C, dtype=np.int64), (P, 1)),
+                 np.zeros((P, C), np.int32), np.full((P, C), 6, np.int32))
+    hits = 0
+    for g in range(10):
+        D, _, o = so.offspring(g)
+        for s in np.nonzero(o == 6)[0]:
+            assert np.array_equal(D[s], pX[s % P, 0])
+            hits += 1
+    assert hits > 100
+
+
 def test_adaptive_choice_five_percent(orc):
     n, S = 64, 256
     W = wl.dense_qubo(n, -5, 5, 1)
@@ -128,11 +145,14 @@ def test_pool_merge_is_top_c_of_union(orc):
     pE = np.sort(rng.integers(-20, 20, (P, C)), axis=1).astype(np.int64)
     pa = rng.integers(0, 5, (P, C)).astype(np.int32)
     po = rng.integers(0, 8, (P, C)).astype(np.int32)
+    pE[2, 0] = -90
     so.set_pools(pX, pE, pa, po)
     rX = rng.integers(0, 2, (S, n)).astype(np.uint8)
     rE = rng.integers(-25, 25, S).astype(np.int64)
-    rX[5] = pX[5 % P, 2]; rE[5] = pE[5 % P, 2]            # duplicate of a pool entry
+    rX[5] = pX[2, 0]; rE[5] = -90                         # duplicate of a pool entry
+    rE[4] = -100
     rX[7] = rX[4]; rE[7] = rE[4]; rX[10] = rX[4]; rE[10] = rE[4]  # duplicate results
+    rE[13] = -100                                          # equal energy, other vector
     ra = rng.integers(0, 5, S).astype(np.int32)
     ro = rng.integers(0, 8, S).astype(np.int32)
     so.merge(rX, rE, ra, ro)

@@ -117,6 +117,28 @@ def test_two_neighbor_finds_every_two_bit_neighbour(orc, a, b):
     assert r["best_E"] == -20 and np.array_equal(r["best_X"], want)
 
 
+def test_ties_go_to_the_lowest_index(orc):
+    """Tie rules of Step 1, Greedy and Straight (lowest index first)."""
+    n = 8
+    W = np.diag([3, -5, 2, -5, -5, 4, 1, 1]).astype(np.int16)
+    z = np.zeros(n, np.uint8)
+    _, _, _, r = run(orc, W, orc.CYCLICMIN, X0=z, D=z, b=(1, 8))
+    assert list(r["trace"][:3]) == [1, 3, 4]  # Greedy: equal Delta = -5, ascending
+    assert r["best_E"] == -15
+    D = np.array([0, 0, 1, 0, 0, 1, 1, 1], np.uint8)
+    _, _, _, r = run(orc, W, orc.CYCLICMIN, X0=z, D=D, b=(1, 8))
+    assert list(r["trace"][:4]) == [6, 7, 2, 5]  # Straight: Delta 1, 1, 2, 4
+    # Step 1 on the first Straight step sees neighbours -5 at bits 1, 3, 4:
+    # BEST must be the lowest one, later replaced only on strict improvement
+    Wb = np.diag([0, -5, 0, 0, 0, 0, 0, 0]).astype(np.int16)
+    D2 = np.array([0, 0, 0, 0, 0, 0, 1, 0], np.uint8)
+    _, _, _, r = run(orc, Wb, orc.TWONEIGHBOR, X0=z, D=D2, b=(1, 8), check=False)
+    assert list(r["trace"]) == [6, 1]
+    # first Step 1 (X = 0) records bit 1; the equal-energy neighbours seen at
+    # X = e6 and X = e1 + e6 must not replace it
+    assert r["best_E"] == -5 and list(np.nonzero(r["best_X"])[0]) == [1]
+
+
 def test_flip_budget_worked_example(orc):
     """Section III-B: Straight 300, Greedy 50, main 600 and b n = 2000 give
     300+50+600+50+600+50+600+50 = 2300 flips and three main searches."""
@@ -194,6 +216,32 @@ def test_selector_rules_on_replay(orc, seed):
                 if pos.size:
                     assert dl[i] <= pos.min()
             seq.append(i)
+
+
+def test_positive_min_pick_is_uniform_over_candidates(orc):
+    """PositiveMin picks one candidate at random (Section III-A): over many
+    iterations the pick's rank among the candidates is uniform."""
+    n, tau = 40, 8
+    ranks = []
+    for seed in range(6):
+        W = wl.dense_qubo(n, -20, 20, seed=seed + 40)
+        p, X0, D, r = run(orc, W, orc.POSITIVEMIN, seed=seed, b=(4, 1), s_f=(1, 1), tabu=tau,
+                          check=False)
+        ph, tr = r["phases"], r["trace"]
+        seq = []
+        for step, (X, dl, i) in enumerate(replay(W, X0, tr)):
+            if ph[step] != orc.PH_MAIN:
+                seq = []
+                continue
+            tabu = set(seq[max(0, len(seq) - tau):])
+            free = np.array([k not in tabu for k in range(n)])
+            pos = dl[free & (dl > 0)]
+            cand = np.nonzero(free & (dl <= pos.min()))[0] if pos.size else np.nonzero(free)[0]
+            assert i in cand
+            if len(cand) > 1:
+                ranks.append(list(cand).index(i) / (len(cand) - 1))
+            seq.append(i)
+    assert len(ranks) > 200 and abs(np.mean(ranks) - 0.5) < 0.06
 
 
 def test_cube21_endpoints_and_monotone(orc):
