@@ -1,0 +1,170 @@
+/*
+ * dabs.h -- C ABI of libdabs.so, a GB300 (sm_103a) implementation of the
+ * bulk local search of Diverse Adaptive Bulk Search (DABS) for QUBO
+ * (Nakano, Takafuji, Ito et al., "Diverse Adaptive Bulk Search: a Framework
+ * for Solving QUBO Problems on Multiple GPUs").
+ *
+ * Problem (Section I-A, Eq. (2)): minimise E(X) = sum_i W_ii x_i +
+ * sum_{i<j} W_ij x_i x_j over X in {0,1}^n, for a symmetric int16 matrix W
+ * (each unordered pair counted once).  A matrix written with every ordered
+ * pair counted converts to this form by W'_ij = W_ij + W_ji (i != j).
+ *
+ * Conventions of every call:
+ *  - Return 0 (DABS_OK) on success, a negative DABS_E_* code on error; no
+ *    call aborts the process.  dabs_strerror() names the code and
+ *    dabs_last_error() gives the context's last message.
+ *  - "host" buffers are ordinary CPU memory owned by the caller; "device"
+ *    buffers are CUDA global memory on the context's device, owned by the
+ *    caller.  The library keeps no pointer to a caller buffer after a call
+ *    returns.  Calls on host buffers are synchronous.  Calls on device
+ *    buffers are enqueued on the context's stream (see dabs_set_stream) and
+ *    return before the GPU work completes.
+ *  - Bit vectors on the device are packed: bit k of a vector is bit (k % 32)
+ *    of 32-bit word k / 32; a vector occupies ceil(n / 32) words and its bits
+ *    >= n must be zero.  On the host, X vectors are n bytes of 0 or 1.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - Energies are int64; Delta values are int32 (exact for n <= 65535).
+ */
+#ifndef DABS_H
+#define DABS_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DABS_OK 0
+#define DABS_E_INVALID_ARG (-1)  /* bad size, pointer, parameter or bit value   */
+#define DABS_E_NOT_SYMMETRIC (-2)/* W is not symmetric                          */
+#define DABS_E_TOO_LARGE (-3)    /* n or a parameter above what the build holds */
+#define DABS_E_OOM (-4)          /* device allocation failed                    */
+#define DABS_E_TIMEOUT (-5)      /* a bounded device wait ran out               */
+#define DABS_E_CUDA (-6)         /* any other CUDA runtime error                */
+#define DABS_E_BUSY (-7)         /* the context is in a state that forbids it   */
+#define DABS_E_NO_DEVICE (-8)    /* no CUDA device of compute capability 10.3   */
+
+#define DABS_N_MAX 8192          /* largest n of the register-resident search   */
+
+enum { DABS_MAXMIN = 0, DABS_CYCLICMIN = 1, DABS_RANDOMMIN = 2, DABS_POSITIVEMIN = 3,
+       DABS_TWONEIGHBOR = 4 };
+enum { DABS_MUTATION = 0, DABS_CROSSOVER = 1, DABS_XROSSOVER = 2, DABS_ZERO = 3, DABS_ONE = 4,
+       DABS_INTERVALZERO = 5, DABS_BEST = 6, DABS_RANDOM = 7 };
+
+/* Solver parameters (Sections III-B and IV).  Defaults (dabs_params_default):
+ * 32 searches, 4 pools, pool_cap 100 and tabu 8 (the paper's experiments),
+ * s = 1/10, b = 1, Straight seeding, no generation limit.                   */
+typedef struct dabs_params {
+    int32_t searches;        /* concurrent batch searches S (1..65535)          */
+    int32_t pools;           /* solution pools P (islands), 1..S                */
+    int32_t pool_cap;        /* packets per pool C, 1..1024                     */
+    int32_t tabu;            /* tabu period, 0..31                              */
+    int32_t s_num, s_den;    /* search flip factor s: T = max(1, floor(n s))    */
+    int32_t b_num, b_den;    /* batch flip factor b: B = ceil(n b)              */
+    int32_t seed_mode;       /* 0: Straight walk to each target (Section III-B);
+                                1: X = target, Delta and E recomputed           */
+    int32_t max_generations; /* 0 = unlimited                                  */
+} dabs_params;
+
+typedef struct dabs_ctx dabs_ctx;
+
+/* Fills *p with the defaults above. */
+int dabs_params_default(dabs_params* p);
+
+/* Creates a context on the current CUDA device: copies W (host, n*n int16,
+ * row-major, symmetric) to device memory once (rows padded to a multiple of
+ * 64 entries) and allocates the solver state for *p.  Errors: INVALID_ARG
+ * (null pointer, n < 1, bad params), NOT_SYMMETRIC, TOO_LARGE (n > DABS_N_MAX
+ * or S / P > 4096), NO_DEVICE, OOM.  On error *out is set to NULL.         */
+int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** out);
+
+/* Frees every device and host resource of ctx (NULL is accepted). */
+void dabs_destroy(dabs_ctx* ctx);
+
+/* Message of a DABS_E_* code, and the context's last error message. */
+const char* dabs_strerror(int code);
+const char* dabs_last_error(const dabs_ctx* ctx);
+
+/* Uses `stream` (a cudaStream_t, NULL = the context's own stream) for all
+ * further device work of ctx. */
+int dabs_set_stream(dabs_ctx* ctx, void* stream);
+
+/* Replaces the weights with another symmetric n x n matrix of the same n
+ * (host buffer), keeping the solver state allocations. */
+int dabs_load_weights(dabs_ctx* ctx, const int16_t* W);
+
+/* Eq. (2): energy of one host vector X (n bytes, each 0 or 1). */
+int dabs_energy(dabs_ctx* ctx, const uint8_t* X, int64_t* E);
+
+/* Eq. (3): Delta_k(X) = E(f_k(X)) - E(X) for all k of one host vector. */
+int dabs_delta(dabs_ctx* ctx, const uint8_t* X, int32_t* delta);
+
+/* Batched Eq. (2)/(3) on device buffers: X (count packed vectors), E
+ * (count int64), delta (count x ld_delta int32, or NULL).  Asynchronous. */
+int dabs_energy_delta_dev(dabs_ctx* ctx, const uint32_t* X, int32_t count, int64_t* E,
+                          int32_t* delta, int32_t ld_delta);
+
+/* Whole solve (Sections III and IV): pools initialised with random vectors,
+ * every search starting at X = 0; generations of (offspring, batch search,
+ * pool merge) until, at a generation boundary, the total number of flips
+ * reaches `budget`, the best energy is <= `target` (INT64_MIN: no target),
+ * or max_generations is reached.  Writes the best vector (host, n bytes),
+ * its energy and the flips made.  Deterministic in (W, params, budget, seed,
+ * target).                                                                   */
+int dabs_solve(dabs_ctx* ctx, uint64_t budget, uint64_t seed, int64_t target, uint8_t* best_X,
+               int64_t* best_E, uint64_t* flips);
+
+/* ---- stepwise form of dabs_solve (device-resident state) ---------------- */
+/* Resets pools, search state and counters for a new solve.  Asynchronous. */
+int dabs_solve_begin(dabs_ctx* ctx, uint64_t seed, uint64_t budget, int64_t target);
+/* Enqueues `count` generations; generations after the stop condition are
+ * no-ops on the device.  Asynchronous. */
+int dabs_solve_generations(dabs_ctx* ctx, int32_t count);
+/* Waits for the stream, then reports the counters. */
+int dabs_solve_status(dabs_ctx* ctx, uint64_t* flips, uint32_t* generations, int64_t* best_E,
+                      int32_t* done);
+/* Waits for the stream, then copies the best vector (host, n bytes) and E. */
+int dabs_solve_best(dabs_ctx* ctx, uint8_t* best_X, int64_t* best_E);
+
+/* ---- one batch search per slot on caller buffers (Section III-B) --------
+ * For slots s < count: state X (packed), delta (ld int32 per slot, see
+ * dabs_info), E; target D (packed); algo (one byte per slot, DABS_MAXMIN..
+ * DABS_TWONEIGHBOR).  Runs seeding (Straight, or nothing when seed_mode = 1:
+ * the state must then already equal the target), Greedy and (main search,
+ * Greedy) rounds until b*n flips, drawing random numbers for generation g
+ * and slot s of `seed`.  Outputs per slot: BEST (packed), E(BEST), flips.
+ * All pointers are device buffers.  Asynchronous.                         */
+int dabs_bulk_search_dev(dabs_ctx* ctx, uint64_t seed, uint32_t g, int32_t count, uint32_t* X,
+                         int32_t* delta, int64_t* E, const uint32_t* D, const uint8_t* algo,
+                         uint32_t* best_X, int64_t* best_E, uint32_t* flips);
+
+/* ---- inspection (host copies; synchronous) ------------------------------ */
+/* n, padded row length ld, packed words per vector, S, P, C, and the
+ * kernel variant (warps per search, 8-bit chunks per thread). */
+int dabs_info(const dabs_ctx* ctx, int32_t* n, int32_t* ld, int32_t* words, int32_t* searches,
+              int32_t* pools, int32_t* pool_cap, int32_t* warps, int32_t* chunks);
+/* Chooses the batch-search variant; returns TOO_LARGE if it cannot hold n. */
+int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
+/* Current pools (the ones the next generation breeds from): X [P][C][words],
+ * E [P][C], algo [P][C], op [P][C].  Any pointer may be NULL. */
+int dabs_read_pools(dabs_ctx* ctx, uint32_t* X, int64_t* E, uint8_t* algo, uint8_t* op);
+int dabs_write_pools(dabs_ctx* ctx, const uint32_t* X, const int64_t* E, const uint8_t* algo,
+                     const uint8_t* op);
+/* Per-search state X [S][words], delta [S][ld], E [S]. */
+int dabs_read_state(dabs_ctx* ctx, uint32_t* X, int32_t* delta, int64_t* E);
+/* Last generation's targets D [S][words], algo, op and results BEST [S][words],
+ * E(BEST) [S], flips [S]. */
+int dabs_read_generation(dabs_ctx* ctx, uint32_t* D, uint8_t* algo, uint8_t* op,
+                         uint32_t* best_X, int64_t* best_E, uint32_t* flips);
+/* Overwrites the results buffers (for a merge-only step). */
+int dabs_write_results(dabs_ctx* ctx, const uint32_t* best_X, const int64_t* best_E,
+                       const uint32_t* flips, const uint8_t* algo, const uint8_t* op);
+/* Runs one stage of the current generation: 0 offspring (+ recompute when
+ * seed_mode = 1), 1 batch search, 2 pool merge, 3 finalise (advances the
+ * generation).  Asynchronous. */
+int dabs_run_stage(dabs_ctx* ctx, int32_t stage);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,568 @@
+// abi.cu -- the C ABI of libdabs.so (declared in include/dabs.h): context
+// lifetime, weight residency, the per-generation launch sequence
+// (offspring -> [recompute] -> batch search -> pool merge -> finalise), the
+// stepwise and whole solve, and inspection calls.  No exception crosses the
+// ABI; every CUDA error becomes a DABS_E_* code with a message in the context.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dabs.h"
+#include "kernels.cuh"
+
+using namespace dabs;
+
+struct dabs_ctx {
+  int dev = 0;
+  int n = 0, ld = 0, nw = 0;
+  dabs_params p{};
+  int T = 1, tau = 0;
+  uint32_t B = 1;
+  int S = 0, P = 0, C = 0, Mmax = 1;
+  size_t merge_smem = 0;
+  cudaStream_t own = nullptr, stream = nullptr;
+  int16_t* W = nullptr;
+  int32_t* diag = nullptr;
+  DevCtrl* ctrl = nullptr;
+  DevCtrl* bulk_ctrl = nullptr;
+  DevCtrl* h_ctrl = nullptr;  // pinned staging
+  uint32_t* poolX[2] = {nullptr, nullptr};
+  int64_t* poolE[2] = {nullptr, nullptr};
+  uint8_t* poolA[2] = {nullptr, nullptr};
+  uint8_t* poolO[2] = {nullptr, nullptr};
+  uint32_t* X = nullptr;
+  int32_t* delta = nullptr;
+  int64_t* E = nullptr;
+  uint32_t* D = nullptr;
+  uint8_t* algo = nullptr;
+  uint8_t* op = nullptr;
+  uint32_t* bestX = nullptr;
+  int64_t* bestE = nullptr;
+  uint32_t* flips = nullptr;
+  uint32_t* gbestX = nullptr;
+  uint32_t* one_X = nullptr;   // single-vector scratch for dabs_energy / dabs_delta
+  int32_t* one_d = nullptr;
+  int64_t* one_E = nullptr;
+  SearchVariant var{};
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace {
+
+int fail(dabs_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? DABS_E_OOM : DABS_E_CUDA,         \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);    \
+  } while (0)
+
+#define CKLAUNCH() CK(cudaGetLastError())
+
+template <class T>
+int dalloc(dabs_ctx* ctx, T** ptr, size_t count) {
+  void* p = nullptr;
+  const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+  CK(cudaMalloc(&p, bytes));
+  ctx->allocs.push_back(p);
+  *ptr = static_cast<T*>(p);
+  return DABS_OK;
+}
+
+bool params_ok(const dabs_params* p) {
+  return p->searches >= 1 && p->searches <= 65535 && p->pools >= 1 && p->pools <= p->searches &&
+         p->pool_cap >= 1 && p->pool_cap <= 1024 && p->tabu >= 0 && p->tabu <= 31 &&
+         p->s_num >= 0 && p->s_den >= 1 && p->b_num >= 0 && p->b_den >= 1 &&
+         (p->seed_mode == 0 || p->seed_mode == 1) && p->max_generations >= 0;
+}
+
+bool default_variant(int n, SearchVariant* v) {
+  static const int order[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 4}, {4, 4}, {8, 4}};
+  for (auto& o : order) {
+    SearchVariant q;
+    if (launch_search(o[0], o[1], nullptr, nullptr, &q) && q.cap >= n) {
+      *v = q;
+      return true;
+    }
+  }
+  return false;
+}
+
+int upload_weights(dabs_ctx* ctx, const int16_t* W) {
+  const int n = ctx->n, ld = ctx->ld;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (W[(size_t)i * n + j] != W[(size_t)j * n + i])
+        return fail(ctx, DABS_E_NOT_SYMMETRIC, "W[%d][%d] != W[%d][%d]", i, j, j, i);
+  std::vector<int16_t> pad((size_t)n * ld, 0);
+  std::vector<int32_t> dg(n);
+  for (int i = 0; i < n; ++i) {
+    memcpy(&pad[(size_t)i * ld], &W[(size_t)i * n], (size_t)n * sizeof(int16_t));
+    dg[i] = W[(size_t)i * n + i];
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(ctx->W, pad.data(), pad.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->diag, dg.data(), dg.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  return DABS_OK;
+}
+
+SearchArgs solve_search_args(dabs_ctx* ctx) {
+  SearchArgs a{};
+  a.W = ctx->W;
+  a.n = ctx->n; a.ld = ctx->ld; a.nw = ctx->nw; a.S = ctx->S;
+  a.T = ctx->T; a.tau = ctx->tau; a.B = ctx->B; a.seed_mode = ctx->p.seed_mode;
+  a.ctrl = ctx->ctrl;
+  a.X = ctx->X; a.delta = ctx->delta; a.E = ctx->E; a.D = ctx->D; a.algo = ctx->algo;
+  a.best_X = ctx->bestX; a.best_E = ctx->bestE; a.flips = ctx->flips;
+  return a;
+}
+
+int stage(dabs_ctx* ctx, int which) {
+  cudaStream_t st = ctx->stream;
+  if (which == 0) {
+    OffArgs o{};
+    o.n = ctx->n; o.nw = ctx->nw; o.S = ctx->S; o.P = ctx->P; o.C = ctx->C; o.ctrl = ctx->ctrl;
+    for (int b = 0; b < 2; ++b) { o.pool_X[b] = ctx->poolX[b]; o.pool_algo[b] = ctx->poolA[b]; o.pool_op[b] = ctx->poolO[b]; }
+    o.D = ctx->D; o.algo = ctx->algo; o.op = ctx->op;
+    k_offspring<<<(ctx->S * 32 + 255) / 256, 256, 0, st>>>(o);
+    CKLAUNCH();
+    if (ctx->p.seed_mode == 1) {
+      const size_t words = (size_t)ctx->S * ctx->nw;
+      k_copy_targets<<<148, 256, 0, st>>>(ctx->D, ctx->X, ctx->E, words, ctx->S, ctx->ctrl);
+      CKLAUNCH();
+      EDArgs e{ctx->W, ctx->n, ctx->ld, ctx->nw, ctx->X, ctx->delta, ctx->ld, ctx->E, ctx->ctrl};
+      k_energy_delta<<<dim3((ctx->n + 255) / 256, ctx->S), 256, 0, st>>>(e);
+      CKLAUNCH();
+    }
+  } else if (which == 1) {
+    const SearchArgs a = solve_search_args(ctx);
+    if (!launch_search(ctx->var.nw, ctx->var.ch, &a, st, nullptr))
+      return fail(ctx, DABS_E_INVALID_ARG, "no batch-search variant %d/%d", ctx->var.nw, ctx->var.ch);
+    CKLAUNCH();
+  } else if (which == 2) {
+    MergeArgs m{};
+    m.nw = ctx->nw; m.S = ctx->S; m.P = ctx->P; m.C = ctx->C; m.Mmax = ctx->Mmax; m.ctrl = ctx->ctrl;
+    for (int b = 0; b < 2; ++b) { m.pool_X[b] = ctx->poolX[b]; m.pool_E[b] = ctx->poolE[b]; m.pool_algo[b] = ctx->poolA[b]; m.pool_op[b] = ctx->poolO[b]; }
+    m.best_X = ctx->bestX; m.best_E = ctx->bestE; m.algo = ctx->algo; m.op = ctx->op;
+    k_merge<<<ctx->P, kMergeThreads, ctx->merge_smem, st>>>(m);
+    CKLAUNCH();
+  } else if (which == 3) {
+    FinArgs f{ctx->nw, ctx->S, ctx->ctrl, ctx->bestX, ctx->bestE, ctx->flips, ctx->gbestX};
+    k_finalize<<<1, 1024, 0, st>>>(f);
+    CKLAUNCH();
+  } else {
+    return fail(ctx, DABS_E_INVALID_ARG, "stage %d", which);
+  }
+  return DABS_OK;
+}
+
+int read_ctrl(dabs_ctx* ctx, DevCtrl* out) {
+  CK(cudaMemcpyAsync(ctx->h_ctrl, ctx->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *out = *ctx->h_ctrl;
+  return DABS_OK;
+}
+
+int check_bits(dabs_ctx* ctx, const uint8_t* X) {
+  for (int k = 0; k < ctx->n; ++k)
+    if (X[k] > 1) return fail(ctx, DABS_E_INVALID_ARG, "X[%d] = %d is not 0 or 1", k, X[k]);
+  return DABS_OK;
+}
+
+}  // namespace
+
+namespace dabs {
+bool launch_search(int nw, int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v) {
+  switch (nw) {
+    case 1: return launch_search_w1(ch, a, st, v);
+    case 2: return launch_search_w2(ch, a, st, v);
+    case 4: return launch_search_w4(ch, a, st, v);
+    case 8: return launch_search_w8(ch, a, st, v);
+    case 16: return launch_search_w16(ch, a, st, v);
+    default: return false;
+  }
+}
+}  // namespace dabs
+
+extern "C" {
+
+int dabs_params_default(dabs_params* p) {
+  if (!p) return DABS_E_INVALID_ARG;
+  *p = dabs_params{32, 4, 100, 8, 1, 10, 1, 1, 0, 0};
+  return DABS_OK;
+}
+
+const char* dabs_strerror(int code) {
+  switch (code) {
+    case DABS_OK: return "ok";
+    case DABS_E_INVALID_ARG: return "invalid argument";
+    case DABS_E_NOT_SYMMETRIC: return "weight matrix is not symmetric";
+    case DABS_E_TOO_LARGE: return "size above the supported maximum";
+    case DABS_E_OOM: return "device memory allocation failed";
+    case DABS_E_TIMEOUT: return "bounded device wait ran out";
+    case DABS_E_CUDA: return "CUDA runtime error";
+    case DABS_E_BUSY: return "context busy";
+    case DABS_E_NO_DEVICE: return "no compute capability 10.3 CUDA device";
+    default: return "unknown error";
+  }
+}
+
+const char* dabs_last_error(const dabs_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+void dabs_destroy(dabs_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
+  if (ctx->own) cudaStreamDestroy(ctx->own);
+  delete ctx;
+}
+
+int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** out) {
+  if (!out) return DABS_E_INVALID_ARG;
+  *out = nullptr;
+  if (!W || !p || n < 1 || !params_ok(p)) return DABS_E_INVALID_ARG;
+  if (n > DABS_N_MAX) return DABS_E_TOO_LARGE;
+  const int R = (p->searches + p->pools - 1) / p->pools;
+  if (R > 4096) return DABS_E_TOO_LARGE;
+  int dev = 0, ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return DABS_E_NO_DEVICE;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DABS_E_NO_DEVICE;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return DABS_E_NO_DEVICE;
+  if (prop.major != 10 || prop.minor != 3) return DABS_E_NO_DEVICE;
+  dabs_ctx* ctx = new (std::nothrow) dabs_ctx;
+  if (!ctx) return DABS_E_OOM;
+  ctx->dev = dev;
+  ctx->n = n;
+  ctx->ld = (n + 63) / 64 * 64;
+  ctx->nw = (n + 31) / 32;
+  ctx->p = *p;
+  uint64_t T = (uint64_t)n * (uint64_t)p->s_num / (uint64_t)p->s_den;
+  ctx->T = (int)(T < 1 ? 1 : (T > (1u << 30) ? (1u << 30) : T));
+  ctx->tau = p->tabu < n - 1 ? p->tabu : n - 1;
+  ctx->B = (uint32_t)(((uint64_t)n * p->b_num + p->b_den - 1) / p->b_den);
+  ctx->S = p->searches; ctx->P = p->pools; ctx->C = p->pool_cap;
+  int M = 1;
+  while (M < R) M <<= 1;
+  ctx->Mmax = M;
+  ctx->merge_smem = (size_t)ctx->C * 16 + (size_t)M * 24;
+  if (!default_variant(n, &ctx->var)) { dabs_destroy(ctx); return DABS_E_TOO_LARGE; }
+  int rc;
+#define TRY(x) do { if ((rc = (x)) != DABS_OK) { *out = nullptr; int r_ = rc; dabs_destroy(ctx); return r_; } } while (0)
+  if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess) {
+    dabs_destroy(ctx);
+    return DABS_E_CUDA;
+  }
+  ctx->stream = ctx->own;
+  const size_t S = ctx->S, PC = (size_t)ctx->P * ctx->C, nw = ctx->nw, ld = ctx->ld;
+  TRY(dalloc(ctx, &ctx->W, (size_t)n * ld));
+  TRY(dalloc(ctx, &ctx->diag, (size_t)n));
+  TRY(dalloc(ctx, &ctx->ctrl, 1));
+  TRY(dalloc(ctx, &ctx->bulk_ctrl, 1));
+  for (int b = 0; b < 2; ++b) {
+    TRY(dalloc(ctx, &ctx->poolX[b], PC * nw));
+    TRY(dalloc(ctx, &ctx->poolE[b], PC));
+    TRY(dalloc(ctx, &ctx->poolA[b], PC));
+    TRY(dalloc(ctx, &ctx->poolO[b], PC));
+  }
+  TRY(dalloc(ctx, &ctx->X, S * nw));
+  TRY(dalloc(ctx, &ctx->delta, S * ld));
+  TRY(dalloc(ctx, &ctx->E, S));
+  TRY(dalloc(ctx, &ctx->D, S * nw));
+  TRY(dalloc(ctx, &ctx->algo, S));
+  TRY(dalloc(ctx, &ctx->op, S));
+  TRY(dalloc(ctx, &ctx->bestX, S * nw));
+  TRY(dalloc(ctx, &ctx->bestE, S));
+  TRY(dalloc(ctx, &ctx->flips, S));
+  TRY(dalloc(ctx, &ctx->gbestX, nw));
+  TRY(dalloc(ctx, &ctx->one_X, nw));
+  TRY(dalloc(ctx, &ctx->one_d, ld));
+  TRY(dalloc(ctx, &ctx->one_E, 1));
+  if (cudaMallocHost(&ctx->h_ctrl, sizeof(DevCtrl)) != cudaSuccess) { dabs_destroy(ctx); return DABS_E_OOM; }
+  if (ctx->merge_smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ctx->merge_smem) != cudaSuccess) {
+      dabs_destroy(ctx);
+      return DABS_E_TOO_LARGE;
+    }
+  }
+  TRY(upload_weights(ctx, W));
+  // a fresh context is a solve with seed 0 that has not run yet
+  TRY(dabs_solve_begin(ctx, 0, UINT64_MAX, INT64_MIN));
+  TRY(cudaStreamSynchronize(ctx->stream) == cudaSuccess ? DABS_OK : DABS_E_CUDA);
+#undef TRY
+  *out = ctx;
+  return DABS_OK;
+}
+
+int dabs_set_stream(dabs_ctx* ctx, void* stream) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->stream = stream ? static_cast<cudaStream_t>(stream) : ctx->own;
+  return DABS_OK;
+}
+
+int dabs_load_weights(dabs_ctx* ctx, const int16_t* W) {
+  if (!ctx || !W) return DABS_E_INVALID_ARG;
+  return upload_weights(ctx, W);
+}
+
+int dabs_energy_delta_dev(dabs_ctx* ctx, const uint32_t* X, int32_t count, int64_t* E,
+                          int32_t* delta, int32_t ld_delta) {
+  if (!ctx || !X || !E || count < 0 || (delta && ld_delta < ctx->n)) return DABS_E_INVALID_ARG;
+  if (count == 0) return DABS_OK;
+  if (count > 65535) return fail(ctx, DABS_E_TOO_LARGE, "count %d > 65535", count);
+  CK(cudaMemsetAsync(E, 0, sizeof(int64_t) * count, ctx->stream));
+  EDArgs e{ctx->W, ctx->n, ctx->ld, ctx->nw, X, delta, ld_delta, E, nullptr};
+  k_energy_delta<<<dim3((ctx->n + 255) / 256, count), 256, 0, ctx->stream>>>(e);
+  CKLAUNCH();
+  return DABS_OK;
+}
+
+static int one_vector(dabs_ctx* ctx, const uint8_t* X, int64_t* E, int32_t* delta) {
+  int rc = check_bits(ctx, X);
+  if (rc) return rc;
+  std::vector<uint32_t> packed(ctx->nw, 0u);
+  for (int k = 0; k < ctx->n; ++k) packed[k >> 5] |= (uint32_t)X[k] << (k & 31);
+  CK(cudaMemcpyAsync(ctx->one_X, packed.data(), packed.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+  rc = dabs_energy_delta_dev(ctx, ctx->one_X, 1, ctx->one_E, delta ? ctx->one_d : nullptr, ctx->ld);
+  if (rc) return rc;
+  int64_t e = 0;
+  CK(cudaMemcpyAsync(&e, ctx->one_E, sizeof e, cudaMemcpyDeviceToHost, ctx->stream));
+  if (delta)
+    CK(cudaMemcpyAsync(delta, ctx->one_d, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (E) *E = e;
+  return DABS_OK;
+}
+
+int dabs_energy(dabs_ctx* ctx, const uint8_t* X, int64_t* E) {
+  if (!ctx || !X || !E) return DABS_E_INVALID_ARG;
+  return one_vector(ctx, X, E, nullptr);
+}
+
+int dabs_delta(dabs_ctx* ctx, const uint8_t* X, int32_t* delta) {
+  if (!ctx || !X || !delta) return DABS_E_INVALID_ARG;
+  return one_vector(ctx, X, nullptr, delta);
+}
+
+int dabs_solve_begin(dabs_ctx* ctx, uint64_t seed, uint64_t budget, int64_t target) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  DevCtrl c{};
+  c.seed = seed;
+  c.g = 0;
+  c.done = 0;
+  c.flips_total = 0;
+  c.budget = budget;
+  c.target = target;
+  c.max_generations = (uint32_t)ctx->p.max_generations;
+  c.best_E = INT64_MAX;
+  *ctx->h_ctrl = c;
+  CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, ctx->stream));
+  StateArgs s{ctx->n, ctx->ld, ctx->nw, ctx->S, ctx->diag, ctx->X, ctx->delta, ctx->E, ctx->gbestX};
+  k_state_init<<<304, 256, 0, ctx->stream>>>(s);
+  CKLAUNCH();
+  PoolArgs pa{};
+  pa.n = ctx->n; pa.nw = ctx->nw; pa.P = ctx->P; pa.C = ctx->C; pa.ctrl = ctx->ctrl;
+  for (int b = 0; b < 2; ++b) { pa.pool_X[b] = ctx->poolX[b]; pa.pool_E[b] = ctx->poolE[b]; pa.pool_algo[b] = ctx->poolA[b]; pa.pool_op[b] = ctx->poolO[b]; }
+  const int entries = ctx->P * ctx->C;
+  k_pool_init<<<(entries * 32 + 255) / 256, 256, 0, ctx->stream>>>(pa);
+  CKLAUNCH();
+  return DABS_OK;
+}
+
+int dabs_run_stage(dabs_ctx* ctx, int32_t which) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  return stage(ctx, which);
+}
+
+int dabs_solve_generations(dabs_ctx* ctx, int32_t count) {
+  if (!ctx || count < 0) return DABS_E_INVALID_ARG;
+  for (int32_t q = 0; q < count; ++q)
+    for (int st = 0; st < 4; ++st) {
+      const int rc = stage(ctx, st);
+      if (rc) return rc;
+    }
+  return DABS_OK;
+}
+
+int dabs_solve_status(dabs_ctx* ctx, uint64_t* flips, uint32_t* generations, int64_t* best_E,
+                      int32_t* done) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  DevCtrl c;
+  const int rc = read_ctrl(ctx, &c);
+  if (rc) return rc;
+  if (flips) *flips = c.flips_total;
+  if (generations) *generations = c.g;
+  if (best_E) *best_E = c.best_E;
+  if (done) *done = (int32_t)c.done;
+  return DABS_OK;
+}
+
+int dabs_solve_best(dabs_ctx* ctx, uint8_t* best_X, int64_t* best_E) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  DevCtrl c;
+  int rc = read_ctrl(ctx, &c);
+  if (rc) return rc;
+  if (best_X) {
+    std::vector<uint32_t> packed(ctx->nw);
+    CK(cudaMemcpy(packed.data(), ctx->gbestX, packed.size() * 4, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < ctx->n; ++k) best_X[k] = (uint8_t)((packed[k >> 5] >> (k & 31)) & 1u);
+  }
+  if (best_E) *best_E = c.best_E;
+  return DABS_OK;
+}
+
+int dabs_solve(dabs_ctx* ctx, uint64_t budget, uint64_t seed, int64_t target, uint8_t* best_X,
+               int64_t* best_E, uint64_t* flips) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  int rc = dabs_solve_begin(ctx, seed, budget, target);
+  if (rc) return rc;
+  int chunk = 1;
+  for (;;) {
+    rc = dabs_solve_generations(ctx, chunk);
+    if (rc) return rc;
+    int32_t done = 0;
+    rc = dabs_solve_status(ctx, flips, nullptr, nullptr, &done);
+    if (rc) return rc;
+    if (done) break;
+    if (chunk < 64) chunk <<= 1;
+  }
+  return dabs_solve_best(ctx, best_X, best_E);
+}
+
+int dabs_bulk_search_dev(dabs_ctx* ctx, uint64_t seed, uint32_t g, int32_t count, uint32_t* X,
+                         int32_t* delta, int64_t* E, const uint32_t* D, const uint8_t* algo,
+                         uint32_t* best_X, int64_t* best_E, uint32_t* flips) {
+  if (!ctx || count < 0 || (count > 0 && (!X || !delta || !E || !D || !algo || !best_X || !best_E || !flips)))
+    return DABS_E_INVALID_ARG;
+  if (count == 0) return DABS_OK;
+  DevCtrl c{};
+  c.seed = seed;
+  c.g = g;
+  CK(cudaMemcpyAsync(ctx->bulk_ctrl, &c, sizeof c, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  SearchArgs a = solve_search_args(ctx);
+  a.S = count;
+  a.ctrl = ctx->bulk_ctrl;
+  a.X = X; a.delta = delta; a.E = E; a.D = D; a.algo = algo;
+  a.best_X = best_X; a.best_E = best_E; a.flips = flips;
+  if (!launch_search(ctx->var.nw, ctx->var.ch, &a, ctx->stream, nullptr))
+    return fail(ctx, DABS_E_INVALID_ARG, "no batch-search variant");
+  CKLAUNCH();
+  return DABS_OK;
+}
+
+int dabs_info(const dabs_ctx* ctx, int32_t* n, int32_t* ld, int32_t* words, int32_t* searches,
+              int32_t* pools, int32_t* pool_cap, int32_t* warps, int32_t* chunks) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  if (n) *n = ctx->n;
+  if (ld) *ld = ctx->ld;
+  if (words) *words = ctx->nw;
+  if (searches) *searches = ctx->S;
+  if (pools) *pools = ctx->P;
+  if (pool_cap) *pool_cap = ctx->C;
+  if (warps) *warps = ctx->var.nw;
+  if (chunks) *chunks = ctx->var.ch;
+  return DABS_OK;
+}
+
+int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  SearchVariant v;
+  if (!launch_search(warps, chunks, nullptr, nullptr, &v))
+    return fail(ctx, DABS_E_INVALID_ARG, "variant %d/%d not built", warps, chunks);
+  if (v.cap < ctx->n) return fail(ctx, DABS_E_TOO_LARGE, "variant holds %d < n", v.cap);
+  ctx->var = v;
+  return DABS_OK;
+}
+
+static int cur_buf(dabs_ctx* ctx, int* b) {
+  DevCtrl c;
+  const int rc = read_ctrl(ctx, &c);
+  if (rc) return rc;
+  *b = (int)(c.g & 1u);
+  return DABS_OK;
+}
+
+int dabs_read_pools(dabs_ctx* ctx, uint32_t* X, int64_t* E, uint8_t* algo, uint8_t* op) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  int b = 0, rc = cur_buf(ctx, &b);
+  if (rc) return rc;
+  const size_t PC = (size_t)ctx->P * ctx->C;
+  if (X) CK(cudaMemcpy(X, ctx->poolX[b], PC * ctx->nw * 4, cudaMemcpyDeviceToHost));
+  if (E) CK(cudaMemcpy(E, ctx->poolE[b], PC * 8, cudaMemcpyDeviceToHost));
+  if (algo) CK(cudaMemcpy(algo, ctx->poolA[b], PC, cudaMemcpyDeviceToHost));
+  if (op) CK(cudaMemcpy(op, ctx->poolO[b], PC, cudaMemcpyDeviceToHost));
+  return DABS_OK;
+}
+
+int dabs_write_pools(dabs_ctx* ctx, const uint32_t* X, const int64_t* E, const uint8_t* algo,
+                     const uint8_t* op) {
+  if (!ctx || !X || !E || !algo || !op) return DABS_E_INVALID_ARG;
+  int b = 0, rc = cur_buf(ctx, &b);
+  if (rc) return rc;
+  const size_t PC = (size_t)ctx->P * ctx->C;
+  CK(cudaMemcpy(ctx->poolX[b], X, PC * ctx->nw * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->poolE[b], E, PC * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->poolA[b], algo, PC, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->poolO[b], op, PC, cudaMemcpyHostToDevice));
+  return DABS_OK;
+}
+
+int dabs_read_state(dabs_ctx* ctx, uint32_t* X, int32_t* delta, int64_t* E) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  const size_t S = ctx->S;
+  if (X) CK(cudaMemcpy(X, ctx->X, S * ctx->nw * 4, cudaMemcpyDeviceToHost));
+  if (delta) CK(cudaMemcpy(delta, ctx->delta, S * ctx->ld * 4, cudaMemcpyDeviceToHost));
+  if (E) CK(cudaMemcpy(E, ctx->E, S * 8, cudaMemcpyDeviceToHost));
+  return DABS_OK;
+}
+
+int dabs_read_generation(dabs_ctx* ctx, uint32_t* D, uint8_t* algo, uint8_t* op, uint32_t* best_X,
+                         int64_t* best_E, uint32_t* flips) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  const size_t S = ctx->S;
+  if (D) CK(cudaMemcpy(D, ctx->D, S * ctx->nw * 4, cudaMemcpyDeviceToHost));
+  if (algo) CK(cudaMemcpy(algo, ctx->algo, S, cudaMemcpyDeviceToHost));
+  if (op) CK(cudaMemcpy(op, ctx->op, S, cudaMemcpyDeviceToHost));
+  if (best_X) CK(cudaMemcpy(best_X, ctx->bestX, S * ctx->nw * 4, cudaMemcpyDeviceToHost));
+  if (best_E) CK(cudaMemcpy(best_E, ctx->bestE, S * 8, cudaMemcpyDeviceToHost));
+  if (flips) CK(cudaMemcpy(flips, ctx->flips, S * 4, cudaMemcpyDeviceToHost));
+  return DABS_OK;
+}
+
+int dabs_write_results(dabs_ctx* ctx, const uint32_t* best_X, const int64_t* best_E,
+                       const uint32_t* flips, const uint8_t* algo, const uint8_t* op) {
+  if (!ctx || !best_X || !best_E || !flips || !algo || !op) return DABS_E_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  const size_t S = ctx->S;
+  CK(cudaMemcpy(ctx->bestX, best_X, S * ctx->nw * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->bestE, best_E, S * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->flips, flips, S * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->algo, algo, S, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->op, op, S, cudaMemcpyHostToDevice));
+  return DABS_OK;
+}
+
+}  // extern "C"

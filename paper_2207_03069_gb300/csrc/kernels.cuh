@@ -1,0 +1,99 @@
+// kernels.cuh -- argument blocks and launch entry points of the DABS device
+// kernels (batch search, genetic layer, bookkeeping, energy/Delta).
+#pragma once
+#include "common.cuh"
+
+namespace dabs {
+
+constexpr unsigned FULLMASK = 0xffffffffu;
+constexpr int kMergeThreads = 512;
+
+// bits of word w that hold bits k < n
+__host__ __device__ __forceinline__ uint32_t valid_mask(int w, int n) {
+  const int rem = n - 32 * w;
+  return rem >= 32 ? 0xffffffffu : (rem <= 0 ? 0u : ((1u << rem) - 1u));
+}
+
+struct PoolArgs {
+  int n, nw, P, C;
+  const DevCtrl* ctrl;
+  uint32_t* pool_X[2];
+  int64_t* pool_E[2];
+  uint8_t* pool_algo[2];
+  uint8_t* pool_op[2];
+};
+
+struct StateArgs {
+  int n, ld, nw, S;
+  const int32_t* diag;
+  uint32_t* X;
+  int32_t* delta;
+  int64_t* E;
+  uint32_t* gbest_X;
+};
+
+struct OffArgs {
+  int n, nw, S, P, C;
+  const DevCtrl* ctrl;
+  const uint32_t* pool_X[2];
+  const uint8_t* pool_algo[2];
+  const uint8_t* pool_op[2];
+  uint32_t* D;
+  uint8_t* algo;
+  uint8_t* op;
+};
+
+struct MergeArgs {
+  int nw, S, P, C, Mmax;
+  const DevCtrl* ctrl;
+  uint32_t* pool_X[2];
+  int64_t* pool_E[2];
+  uint8_t* pool_algo[2];
+  uint8_t* pool_op[2];
+  const uint32_t* best_X;
+  const int64_t* best_E;
+  const uint8_t* algo;
+  const uint8_t* op;
+};
+
+struct FinArgs {
+  int nw, S;
+  DevCtrl* ctrl;
+  const uint32_t* best_X;
+  const int64_t* best_E;
+  const uint32_t* flips;
+  uint32_t* gbest_X;
+};
+
+struct EDArgs {
+  const int16_t* W;
+  int n, ld, nw;
+  const uint32_t* X;   // [count][nw]
+  int32_t* delta;      // [count][ld_delta] or null
+  int ld_delta;
+  int64_t* E;          // [count], zeroed before the launch
+  const DevCtrl* ctrl; // optional: skip when a solve has stopped
+};
+
+__global__ void k_pool_init(const PoolArgs a);
+__global__ void k_state_init(const StateArgs a);
+__global__ void k_offspring(const OffArgs a);
+__global__ void k_merge(const MergeArgs a);
+__global__ void k_finalize(const FinArgs a);
+__global__ void k_energy_delta(const EDArgs a);
+__global__ void k_copy_targets(const uint32_t* D, uint32_t* X, int64_t* E, size_t words, int S,
+                               const DevCtrl* ctrl);
+
+// Batch-search variants: NW warps per search, CH chunks of 8 bits per thread.
+struct SearchVariant {
+  int nw, ch, cap, cta, spc;
+};
+// launches k_batch_search<NW, CH>; returns false if (nw, ch) is not built
+bool launch_search(int nw, int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
+bool launch_search_w1(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
+bool launch_search_w2(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
+bool launch_search_w4(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
+bool launch_search_w8(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
+bool launch_search_w16(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
+
+}  // namespace dabs

@@ -1,0 +1,36 @@
+// search_w1.cu -- batch-search kernel variants with 1 warp(s) per search
+// (one translation unit per warp count so the variants compile in parallel).
+#include "search.cuh"
+#include "kernels.cuh"
+
+namespace dabs {
+
+// a == nullptr: only report the variant; otherwise launch one batch search per slot
+bool launch_search_w1(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v) {
+  switch (ch) {
+    case 1: {
+      using C = Cfg<1, 1>;
+      if (v) *v = SearchVariant{1, 1, C::CAP, C::CTA, C::SPC};
+      if (a && a->S > 0)
+        k_batch_search<1, 1><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      return true;
+    }
+    case 2: {
+      using C = Cfg<1, 2>;
+      if (v) *v = SearchVariant{1, 2, C::CAP, C::CTA, C::SPC};
+      if (a && a->S > 0)
+        k_batch_search<1, 2><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      return true;
+    }
+    case 4: {
+      using C = Cfg<1, 4>;
+      if (v) *v = SearchVariant{1, 4, C::CAP, C::CTA, C::SPC};
+      if (a && a->S > 0)
+        k_batch_search<1, 4><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      return true;
+    }
+    default: return false;
+  }
+}
+
+}  // namespace dabs

@@ -1,0 +1,36 @@
+// search_w2.cu -- batch-search kernel variants with 2 warp(s) per search
+// (one translation unit per warp count so the variants compile in parallel).
+#include "search.cuh"
+#include "kernels.cuh"
+
+namespace dabs {
+
+// a == nullptr: only report the variant; otherwise launch one batch search per slot
+bool launch_search_w2(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v) {
+  switch (ch) {
+    case 1: {
+      using C = Cfg<2, 1>;
+      if (v) *v = SearchVariant{2, 1, C::CAP, C::CTA, C::SPC};
+      if (a && a->S > 0)
+        k_batch_search<2, 1><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      return true;
+    }
+    case 2: {
+      using C = Cfg<2, 2>;
+      if (v) *v = SearchVariant{2, 2, C::CAP, C::CTA, C::SPC};
+      if (a && a->S > 0)
+        k_batch_search<2, 2><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      return true;
+    }
+    case 4: {
+      using C = Cfg<2, 4>;
+      if (v) *v = SearchVariant{2, 4, C::CAP, C::CTA, C::SPC};
+      if (a && a->S > 0)
+        k_batch_search<2, 4><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      return true;
+    }
+    default: return false;
+  }
+}
+
+}  // namespace dabs

@@ -1,0 +1,36 @@
+// search_w4.cu -- batch-search kernel variants with 4 warp(s) per search
+// (one translation unit per warp count so the variants compile in parallel).
+#include "search.cuh"
+#include "kernels.cuh"
+
+namespace dabs {
+
+// a == nullptr: only report the variant; otherwise launch one batch search per slot
+bool launch_search_w4(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v) {
+  switch (ch) {
+    case 1: {
+      using C = Cfg<4, 1>;
+      if (v) *v = SearchVariant{4, 1, C::CAP, C::CTA, C::SPC};
+      if (a && a->S > 0)
+        k_batch_search<4, 1><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      return true;
+    }
+    case 2: {
+      using C = Cfg<4, 2>;
+      if (v) *v = SearchVariant{4, 2, C::CAP, C::CTA, C::SPC};
+      if (a && a->S > 0)
+        k_batch_search<4, 2><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      return true;
+    }
+    case 4: {
+      using C = Cfg<4, 4>;
+      if (v) *v = SearchVariant{4, 4, C::CAP, C::CTA, C::SPC};
+      if (a && a->S > 0)
+        k_batch_search<4, 4><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      return true;
+    }
+    default: return false;
+  }
+}
+
+}  // namespace dabs

@@ -1,0 +1,266 @@
+"""Thin ctypes binding of libdabs.so (include/dabs.h).
+
+Argument marshalling only: every step of the search runs in the CUDA library.
+There is no CPU fallback -- if the library is missing or no sm_103 device is
+present, the calls raise.  Device buffers are passed as torch CUDA tensors
+(their data pointers); host buffers as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdabs.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, E_INVALID_ARG, E_NOT_SYMMETRIC, E_TOO_LARGE, E_OOM, E_TIMEOUT, E_CUDA, E_BUSY, E_NO_DEVICE = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+N_MAX = 8192
+INT64_MAX = np.iinfo(np.int64).max
+INT64_MIN = np.iinfo(np.int64).min
+STAGE_OFFSPRING, STAGE_SEARCH, STAGE_MERGE, STAGE_FINALIZE = range(4)
+
+
+class Params(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in (
+        "searches", "pools", "pool_cap", "tabu", "s_num", "s_den", "b_num", "b_den",
+        "seed_mode", "max_generations")]
+
+
+class DabsError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{code} ({strerror(code)}){': ' + msg if msg else ''}")
+        self.code = code
+
+
+EXPORTS = {
+    "dabs_params_default": (C.c_int, [C.c_void_p]),
+    "dabs_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "dabs_destroy": (None, [C.c_void_p]),
+    "dabs_strerror": (C.c_char_p, [C.c_int]),
+    "dabs_last_error": (C.c_char_p, [C.c_void_p]),
+    "dabs_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dabs_load_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dabs_energy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dabs_delta": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dabs_energy_delta_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                        C.c_void_p, C.c_int32]),
+    "dabs_solve": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int64, C.c_void_p,
+                             C.c_void_p, C.c_void_p]),
+    "dabs_solve_begin": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int64]),
+    "dabs_solve_generations": (C.c_int, [C.c_void_p, C.c_int32]),
+    "dabs_solve_status": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
+    "dabs_solve_best": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dabs_bulk_search_dev": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint32, C.c_int32]
+                             + [C.c_void_p] * 8),
+    "dabs_info": (C.c_int, [C.c_void_p] + [C.c_void_p] * 8),
+    "dabs_set_variant": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "dabs_read_pools": (C.c_int, [C.c_void_p] * 5),
+    "dabs_write_pools": (C.c_int, [C.c_void_p] * 5),
+    "dabs_read_state": (C.c_int, [C.c_void_p] * 4),
+    "dabs_read_generation": (C.c_int, [C.c_void_p] * 7),
+    "dabs_write_results": (C.c_int, [C.c_void_p] * 6),
+    "dabs_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
+}
+
+
+def lib(path: str = LIB_PATH):
+    """Loads libdabs.so (built by build.py / __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"libdabs.so not built ({path}); run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(path)
+            for name, (res, args) in EXPORTS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().dabs_strerror(code).decode()
+    except Exception:
+        return "?"
+
+
+def _ptr(a):
+    """numpy array or torch tensor -> void*"""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    rc = lib().dabs_params_default(C.byref(p))
+    assert rc == OK
+    for k, v in kw.items():
+        if k in ("s", "b"):
+            setattr(p, k + "_num", v[0])
+            setattr(p, k + "_den", v[1])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One solver context: device-resident W, pools and search state."""
+
+    def __init__(self, W: np.ndarray, params: Params | None = None, **kw):
+        W = np.ascontiguousarray(W, dtype=np.int16)
+        if W.ndim != 2 or W.shape[0] != W.shape[1]:
+            raise ValueError("W must be square")
+        self.n = W.shape[0]
+        self.params = params if params is not None else default_params(**kw)
+        h = C.c_void_p()
+        rc = lib().dabs_create(_ptr(W), self.n, C.byref(self.params), C.byref(h))
+        if rc != OK:
+            raise DabsError(rc)
+        self._h = h
+        info = self.info()
+        self.ld, self.words = info["ld"], info["words"]
+        self.S, self.P, self.C = info["searches"], info["pools"], info["pool_cap"]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dabs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, rc):
+        if rc != OK:
+            raise DabsError(rc, lib().dabs_last_error(self._h).decode())
+
+    # ---------------------------------------------------------------- basics
+    def info(self) -> dict:
+        v = [C.c_int32() for _ in range(8)]
+        self._ck(lib().dabs_info(self._h, *[C.byref(x) for x in v]))
+        keys = ("n", "ld", "words", "searches", "pools", "pool_cap", "warps", "chunks")
+        return {k: x.value for k, x in zip(keys, v)}
+
+    def set_variant(self, warps: int, chunks: int):
+        self._ck(lib().dabs_set_variant(self._h, warps, chunks))
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an int handle, or None (own stream)."""
+        handle = None if stream is None else getattr(stream, "cuda_stream", stream)
+        self._ck(lib().dabs_set_stream(self._h, C.c_void_p(handle) if handle else None))
+
+    def load_weights(self, W: np.ndarray):
+        W = np.ascontiguousarray(W, dtype=np.int16)
+        assert W.shape == (self.n, self.n)
+        self._ck(lib().dabs_load_weights(self._h, _ptr(W)))
+
+    def energy(self, X) -> int:
+        X = np.ascontiguousarray(X, dtype=np.uint8)
+        e = C.c_int64()
+        self._ck(lib().dabs_energy(self._h, _ptr(X), C.byref(e)))
+        return int(e.value)
+
+    def delta(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.uint8)
+        out = np.zeros(self.n, np.int32)
+        self._ck(lib().dabs_delta(self._h, _ptr(X), _ptr(out)))
+        return out
+
+    def energy_delta_dev(self, X, E, delta=None, ld_delta: int | None = None):
+        count = X.shape[0]
+        ldd = ld_delta if ld_delta is not None else (delta.shape[-1] if delta is not None else 0)
+        self._ck(lib().dabs_energy_delta_dev(self._h, _ptr(X), count, _ptr(E), _ptr(delta), ldd))
+
+    # ---------------------------------------------------------------- solve
+    def solve(self, budget: int, seed: int, target: int | None = None):
+        X = np.zeros(self.n, np.uint8)
+        e = C.c_int64()
+        f = C.c_uint64()
+        tgt = INT64_MIN if target is None else int(target)
+        self._ck(lib().dabs_solve(self._h, min(int(budget), 2**64 - 1), seed, tgt, _ptr(X),
+                                  C.byref(e), C.byref(f)))
+        return X, int(e.value), int(f.value)
+
+    def solve_begin(self, seed: int, budget: int = 2**64 - 1, target: int | None = None):
+        tgt = INT64_MIN if target is None else int(target)
+        self._ck(lib().dabs_solve_begin(self._h, seed, min(int(budget), 2**64 - 1), tgt))
+
+    def solve_generations(self, count: int):
+        self._ck(lib().dabs_solve_generations(self._h, count))
+
+    def solve_status(self) -> dict:
+        f, g, e, d = C.c_uint64(), C.c_uint32(), C.c_int64(), C.c_int32()
+        self._ck(lib().dabs_solve_status(self._h, C.byref(f), C.byref(g), C.byref(e), C.byref(d)))
+        return dict(flips=int(f.value), generations=int(g.value), best_E=int(e.value),
+                    done=bool(d.value))
+
+    def solve_best(self):
+        X = np.zeros(self.n, np.uint8)
+        e = C.c_int64()
+        self._ck(lib().dabs_solve_best(self._h, _ptr(X), C.byref(e)))
+        return X, int(e.value)
+
+    def run_stage(self, stage: int):
+        self._ck(lib().dabs_run_stage(self._h, stage))
+
+    # ---------------------------------------------------------------- bulk search
+    def bulk_search_dev(self, seed, g, X, delta, E, D, algo, best_X, best_E, flips):
+        self._ck(lib().dabs_bulk_search_dev(self._h, seed, g, X.shape[0], _ptr(X), _ptr(delta),
+                                            _ptr(E), _ptr(D), _ptr(algo), _ptr(best_X),
+                                            _ptr(best_E), _ptr(flips)))
+
+    # ---------------------------------------------------------------- inspection
+    def read_pools(self):
+        X = np.zeros((self.P, self.C, self.words), np.uint32)
+        E = np.zeros((self.P, self.C), np.int64)
+        a = np.zeros((self.P, self.C), np.uint8)
+        o = np.zeros((self.P, self.C), np.uint8)
+        self._ck(lib().dabs_read_pools(self._h, _ptr(X), _ptr(E), _ptr(a), _ptr(o)))
+        return X, E, a, o
+
+    def write_pools(self, X, E, a, o):
+        X = np.ascontiguousarray(X, np.uint32)
+        E = np.ascontiguousarray(E, np.int64)
+        a = np.ascontiguousarray(a, np.uint8)
+        o = np.ascontiguousarray(o, np.uint8)
+        self._ck(lib().dabs_write_pools(self._h, _ptr(X), _ptr(E), _ptr(a), _ptr(o)))
+
+    def read_state(self):
+        X = np.zeros((self.S, self.words), np.uint32)
+        d = np.zeros((self.S, self.ld), np.int32)
+        E = np.zeros(self.S, np.int64)
+        self._ck(lib().dabs_read_state(self._h, _ptr(X), _ptr(d), _ptr(E)))
+        return X, d[:, :self.n], E
+
+    def read_generation(self):
+        S, w = self.S, self.words
+        D = np.zeros((S, w), np.uint32)
+        a = np.zeros(S, np.uint8)
+        o = np.zeros(S, np.uint8)
+        bX = np.zeros((S, w), np.uint32)
+        bE = np.zeros(S, np.int64)
+        f = np.zeros(S, np.uint32)
+        self._ck(lib().dabs_read_generation(self._h, _ptr(D), _ptr(a), _ptr(o), _ptr(bX),
+                                            _ptr(bE), _ptr(f)))
+        return D, a, o, bX, bE, f
+
+    def write_results(self, best_X, best_E, flips, algo, op):
+        args = [np.ascontiguousarray(best_X, np.uint32), np.ascontiguousarray(best_E, np.int64),
+                np.ascontiguousarray(flips, np.uint32), np.ascontiguousarray(algo, np.uint8),
+                np.ascontiguousarray(op, np.uint8)]
+        self._ck(lib().dabs_write_results(self._h, *[_ptr(x) for x in args]))

@@ -17,15 +17,17 @@ import numpy as np
 
 def symmetric_from_upper(U: np.ndarray) -> np.ndarray:
     """Mirror the upper triangle (diagonal included) of U into a symmetric matrix."""
-    up = np.triu(U)
-    return (up + np.triu(up, 1).T).astype(np.int16)
+    up = np.triu(U).astype(np.int16, copy=False)
+    return up + np.triu(up, 1).T
 
 
 def dense_qubo(n: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """Dense symmetric W with i.i.d. integer weights uniform in [lo, hi]
     (upper triangle incl. diagonal drawn, then mirrored)."""
+    if not (-32768 <= lo <= hi <= 32767):
+        raise ValueError("weights must fit int16")
     rng = np.random.default_rng(seed)
-    U = rng.integers(lo, hi + 1, size=(n, n), dtype=np.int64)
+    U = rng.integers(lo, hi + 1, size=(n, n), dtype=np.int32)
     return symmetric_from_upper(U)
 
 

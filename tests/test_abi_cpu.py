@@ -1,0 +1,69 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/dabs.h declares, reports parameter defaults and
+error strings, and refuses to create a context without an sm_103 device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2207_03069_gb300 import build, dabs
+    build.build()
+    return dabs.lib()
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "dabs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dabs_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+    from paper_2207_03069_gb300 import dabs
+    assert set(names) == set(dabs.EXPORTS)
+
+
+def test_params_default_and_strerror(L):
+    from paper_2207_03069_gb300 import dabs
+    p = dabs.default_params()
+    assert (p.searches, p.pools, p.pool_cap, p.tabu) == (32, 4, 100, 8)
+    assert (p.s_num, p.s_den, p.b_num, p.b_den, p.seed_mode) == (1, 10, 1, 1, 0)
+    assert L.dabs_params_default(None) == dabs.E_INVALID_ARG
+    for code in range(0, -9, -1):
+        assert dabs.strerror(code) not in ("", "unknown error")
+
+
+def test_create_rejects_bad_arguments_before_touching_a_device(L):
+    from paper_2207_03069_gb300 import dabs
+    W = np.zeros((4, 4), np.int16)
+    h = C.c_void_p()
+    p = dabs.default_params()
+    assert L.dabs_create(None, 4, C.byref(p), C.byref(h)) == dabs.E_INVALID_ARG
+    assert L.dabs_create(W.ctypes.data_as(C.c_void_p), 0, C.byref(p), C.byref(h)) == dabs.E_INVALID_ARG
+    bad = dabs.default_params(tabu=32)
+    assert L.dabs_create(W.ctypes.data_as(C.c_void_p), 4, C.byref(bad), C.byref(h)) == dabs.E_INVALID_ARG
+    big = np.zeros((1, 1), np.int16)
+    assert L.dabs_create(big.ctypes.data_as(C.c_void_p), dabs.N_MAX + 1, C.byref(p),
+                         C.byref(h)) == dabs.E_TOO_LARGE
+    assert h.value is None
+
+
+def test_create_without_gpu_reports_no_device(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2207_03069_gb300 import dabs
+    W = np.zeros((4, 4), np.int16)
+    h = C.c_void_p()
+    p = dabs.default_params(searches=4, pools=1)
+    assert L.dabs_create(W.ctypes.data_as(C.c_void_p), 4, C.byref(p), C.byref(h)) == dabs.E_NO_DEVICE

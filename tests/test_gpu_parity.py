@@ -1,0 +1,266 @@
+"""GPU parity: the CUDA library against the oracle, bit for bit (all integer
+work).  Covers energy/Delta (Eqs. (2)-(3)), the batch-search kernel for every
+main algorithm and both seeding modes on ragged sizes and every kernel
+variant, offspring and merge in isolation, whole generations and whole solves.
+"""
+import numpy as np
+import pytest
+
+from paper_2207_03069_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_03069_gb300 import build, dabs
+    build.build()
+    return dabs
+
+
+def ctx_for(D, W, **kw):
+    base = dict(searches=8, pools=2, pool_cap=16, tabu=8, s=(1, 4), b=(2, 1), seed_mode=0)
+    base.update(kw)
+    return D.Context(W, **base)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 31, 33, 64, 257, 800, 1000, 2048, 4100, 8192])
+def test_energy_delta(D, orc, n):
+    W = wl.dense_qubo(n, -32768, 32767, seed=n)
+    ctx = ctx_for(D, W, searches=1, pools=1, pool_cap=1)
+    rng = np.random.default_rng(n)
+    for dens in (0.0, 0.5, 1.0, 0.1):
+        X = (rng.random(n) < dens).astype(np.uint8)
+        assert ctx.energy(X) == orc.energy(W, X)
+        assert np.array_equal(ctx.delta(X), orc.delta(W, X))
+    # batched device form
+    cnt = 5
+    Xs = (rng.random((cnt, n)) < 0.5).astype(np.uint8)
+    Xd = torch.from_numpy(wl.pack_bits(Xs).view(np.int32)).cuda()
+    Ed = torch.zeros(cnt, dtype=torch.int64, device="cuda")
+    dd = torch.zeros((cnt, n + 3), dtype=torch.int32, device="cuda")
+    ctx.energy_delta_dev(Xd, Ed, dd)
+    torch.cuda.synchronize()
+    for v in range(cnt):
+        assert int(Ed[v]) == orc.energy(W, Xs[v])
+        assert np.array_equal(dd[v, :n].cpu().numpy(), orc.delta(W, Xs[v]))
+
+
+def test_host_arguments_are_validated(D):
+    W = wl.dense_qubo(8, -5, 5, 0)
+    ctx = ctx_for(D, W)
+    with pytest.raises(D.DabsError):
+        ctx.energy(np.array([0, 1, 2, 0, 0, 0, 0, 0], np.uint8))
+    Wa = W.copy()
+    Wa[0, 1] += 1
+    with pytest.raises(D.DabsError) as e:
+        D.Context(Wa, searches=4, pools=1)
+    assert e.value.code == D.E_NOT_SYMMETRIC
+
+
+def bulk_case(D, orc, W, algos, variant=None, seed=11, g=5, seed_mode=0, s=(1, 4), b=(2, 1),
+              tabu=8, S=None, dflip=None):
+    n = W.shape[0]
+    S = S or len(algos)
+    ctx = ctx_for(D, W, searches=S, pools=1, pool_cap=4, s=s, b=b, tabu=tabu, seed_mode=seed_mode)
+    if variant:
+        ctx.set_variant(*variant)
+    rng = np.random.default_rng(seed + n)
+    X0 = (rng.random((S, n)) < 0.5).astype(np.uint8)
+    Dt = (rng.random((S, n)) < 0.5).astype(np.uint8)
+    if dflip is not None:  # targets near the start: short Straight walks
+        Dt = X0 ^ (rng.random((S, n)) < dflip).astype(np.uint8)
+    if seed_mode == 1:
+        X0 = Dt.copy()
+    d0 = np.stack([orc.delta(W, x) for x in X0])
+    E0 = np.array([orc.energy(W, x) for x in X0], np.int64)
+    dpad = np.zeros((S, ctx.ld), np.int32)
+    dpad[:, :n] = d0
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).view(dt)).cuda()
+    Xd = t(wl.pack_bits(X0), np.int32)
+    Dd = t(wl.pack_bits(Dt), np.int32)
+    dd = t(dpad, np.int32)
+    Ed = t(E0, np.int64)
+    ad = t(np.asarray(algos, np.uint8), np.uint8)
+    bX = torch.zeros((S, ctx.words), dtype=torch.int32, device="cuda")
+    bE = torch.zeros(S, dtype=torch.int64, device="cuda")
+    fl = torch.zeros(S, dtype=torch.int32, device="cuda")
+    ctx.bulk_search_dev(seed, g, Xd, dd, Ed, Dd, ad, bX, bE, fl)
+    torch.cuda.synchronize()
+    p = orc.make_params(searches=1, pools=1, pool_cap=4, tabu=tabu, s=s, b=b, seed_mode=seed_mode)
+    gX = wl.unpack_bits(Xd.cpu().numpy().view(np.uint32), n)
+    gb = wl.unpack_bits(bX.cpu().numpy().view(np.uint32), n)
+    for si in range(S):
+        r = orc.batch_search(W, p, seed, g, si, X0[si], d0[si], int(E0[si]), Dt[si], int(algos[si]))
+        ctx_msg = f"n={n} slot={si} algo={algos[si]} variant={ctx.info()['warps'], ctx.info()['chunks']}"
+        assert int(fl[si]) == r["flips"], ctx_msg
+        assert int(bE[si]) == r["best_E"], ctx_msg
+        assert np.array_equal(gb[si], r["best_X"]), ctx_msg
+        assert np.array_equal(gX[si], r["X"]), ctx_msg
+        assert int(Ed[si]) == r["E"], ctx_msg
+        assert np.array_equal(dd[si, :n].cpu().numpy(), r["delta"]), ctx_msg
+    return ctx
+
+
+ALGOS = [0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 2, 3]
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 31, 33, 64, 100, 257, 800])
+def test_bulk_search_matches_oracle(D, orc, n):
+    W = wl.dense_qubo(n, -100, 100, seed=3 * n)
+    bulk_case(D, orc, W, ALGOS)
+
+
+@pytest.mark.parametrize("variant", [(1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (4, 1),
+                                     (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (16, 1), (16, 2)])
+def test_every_variant_matches_oracle(D, orc, variant):
+    nw, ch = variant
+    cap = 256 * nw * ch
+    for n in sorted({max(1, cap // 3 + 5), cap - 7}):
+        W = wl.dense_qubo(n, -1000, 1000, seed=n + 1)
+        bulk_case(D, orc, W, [0, 1, 2, 3, 4], variant=variant, s=(1, 32), b=(1, 4), dflip=0.02)
+
+
+@pytest.mark.parametrize("n", [33, 300])
+def test_bulk_search_recompute_seeding(D, orc, n):
+    W = wl.dense_qubo(n, -100, 100, seed=n)
+    bulk_case(D, orc, W, ALGOS, seed_mode=1)
+
+
+@pytest.mark.parametrize("tabu,s,b", [(0, (1, 4), (2, 1)), (31, (1, 2), (3, 1)),
+                                      (8, (0, 1), (1, 1)), (8, (1, 4), (0, 1))])
+def test_bulk_search_parameter_edges(D, orc, tabu, s, b):
+    W = wl.dense_qubo(70, -100, 100, seed=9)
+    bulk_case(D, orc, W, ALGOS, tabu=tabu, s=s, b=b)
+
+
+def test_bulk_search_extreme_weights(D, orc):
+    n = 512
+    W = wl.dense_qubo(n, -32768, 32767, seed=1)
+    bulk_case(D, orc, W, ALGOS, s=(1, 8), b=(1, 1))
+    Z = np.zeros((n, n), np.int16)  # all Delta zero: ties everywhere
+    bulk_case(D, orc, Z, ALGOS, s=(1, 8), b=(1, 1))
+
+
+def compare_generation(ctx, so, n, tag):
+    X, E, a, o = ctx.read_pools()
+    oX, oE, oa, oo = so.pools()
+    assert np.array_equal(E, oE), tag
+    assert np.array_equal(wl.unpack_bits(X, n), oX), tag
+    assert np.array_equal(a, oa) and np.array_equal(o, oo), tag
+    Dg, ag, og, bX, bE, fl = ctx.read_generation()
+    rX, rE, rf, ra, ro = so.results()
+    assert np.array_equal(ag, ra) and np.array_equal(og, ro), tag
+    assert np.array_equal(bE, rE) and np.array_equal(fl, rf), tag
+    assert np.array_equal(wl.unpack_bits(bX, n), rX), tag
+    sX, sd, sE = ctx.read_state()
+    oX2, od2, oE2 = so.state()
+    assert np.array_equal(wl.unpack_bits(sX, n), oX2) and np.array_equal(sd, od2), tag
+    assert np.array_equal(sE, oE2), tag
+
+
+@pytest.mark.parametrize("n,S,P,C,seed_mode", [(64, 32, 4, 64, 0), (20, 32, 4, 64, 0),
+                                               (97, 48, 3, 10, 1), (200, 64, 64, 1, 0),
+                                               (33, 16, 1, 8, 0)])
+def test_generations_match_oracle(D, orc, n, S, P, C, seed_mode):
+    W = wl.dense_qubo(n, -100, 100, seed=0)
+    kw = dict(searches=S, pools=P, pool_cap=C, tabu=8, s=(1, 10), b=(1, 1), seed_mode=seed_mode)
+    ctx = D.Context(W, **kw)
+    so = orc.Solver(W, orc.make_params(**kw), 5)
+    ctx.solve_begin(5)
+    X, E, a, o = ctx.read_pools()
+    oX, oE, oa, oo = so.pools()
+    assert np.array_equal(wl.unpack_bits(X, n), oX) and np.array_equal(a, oa)
+    for g in range(6):
+        ctx.solve_generations(1)
+        so.generation()
+        compare_generation(ctx, so, n, f"generation {g}")
+    st = ctx.solve_status()
+    bx, be, bf, bg = so.best()
+    assert (st["best_E"], st["flips"], st["generations"]) == (be, bf, bg)
+    gx, ge = ctx.solve_best()
+    assert ge == be and np.array_equal(gx, bx)
+
+
+def test_offspring_and_merge_on_crafted_pools(D, orc):
+    n, S, P, C = 150, 40, 4, 12
+    W = wl.dense_qubo(n, -50, 50, seed=2)
+    kw = dict(searches=S, pools=P, pool_cap=C)
+    ctx = D.Context(W, **kw)
+    so = orc.Solver(W, orc.make_params(**kw), 9)
+    rng = np.random.default_rng(1)
+    pX = rng.integers(0, 2, (P, C, n)).astype(np.uint8)
+    pE = np.sort(rng.integers(-30, 30, (P, C)), axis=1).astype(np.int64)
+    pa = rng.integers(0, 5, (P, C)).astype(np.int32)
+    po = rng.integers(0, 8, (P, C)).astype(np.int32)
+    ctx.solve_begin(9)
+    ctx.write_pools(wl.pack_bits(pX), pE, pa, po)
+    so.set_pools(pX, pE, pa, po)
+    ctx.run_stage(D.STAGE_OFFSPRING)
+    Dg, ag, og, _, _, _ = ctx.read_generation()
+    oD, oa, oo = so.offspring(0)
+    assert np.array_equal(wl.unpack_bits(Dg, n), oD)
+    assert np.array_equal(ag, oa) and np.array_equal(og, oo)
+    # merge crafted results (duplicates, equal energies, pool copies)
+    rX = rng.integers(0, 2, (S, n)).astype(np.uint8)
+    rE = rng.integers(-40, 40, S).astype(np.int64)
+    rE[4] = -100
+    rX[8] = rX[4]; rE[8] = -100
+    rX[12] = rX[4]; rE[12] = -100
+    rE[16] = -100
+    rX[5] = pX[1, 0]; rE[5] = pE[1, 0]
+    ra = rng.integers(0, 5, S).astype(np.int32)
+    ro = rng.integers(0, 8, S).astype(np.int32)
+    ctx.write_results(wl.pack_bits(rX), rE, np.ones(S, np.uint32), ra, ro)
+    ctx.run_stage(D.STAGE_MERGE)
+    ctx.run_stage(D.STAGE_FINALIZE)
+    so.merge(rX, rE, ra, ro)
+    X, E, a, o = ctx.read_pools()
+    oX, oE, oa, oo = so.pools()
+    assert np.array_equal(E, oE)
+    assert np.array_equal(wl.unpack_bits(X, n), oX)
+    assert np.array_equal(a, oa) and np.array_equal(o, oo)
+    st = ctx.solve_status()
+    assert st["best_E"] == -100 and st["flips"] == S and st["generations"] == 1
+
+
+@pytest.mark.parametrize("n,budget,maxg,target", [(64, 10**9, 12, None), (20, 10**9, 60, "opt"),
+                                                  (128, 30000, 0, None)])
+def test_solve_matches_oracle(D, orc, n, budget, maxg, target):
+    W = wl.dense_qubo(n, -100, 100, seed=0)
+    tgt = wl.brute_force_min(W)[0] if target == "opt" else None
+    kw = dict(searches=32, pools=4, pool_cap=64, tabu=8, s=(1, 10), b=(1, 1), seed_mode=0,
+              max_generations=maxg)
+    ctx = D.Context(W, **kw)
+    gx, ge, gf = ctx.solve(budget, seed=3, target=tgt)
+    ox, oe, of, og = orc.solve(W, orc.make_params(**kw), budget, 3, target=tgt, threads=4)
+    assert (ge, gf) == (oe, of) and np.array_equal(gx, ox)
+    if tgt is not None:
+        assert ge == tgt
+
+
+def test_maxcut_workload_sampled_at_full_size(D, orc):
+    """Sparse Max-Cut n=800, 1024 searches, P=4, C=100, b=10, s=1/10: one full
+    generation on the GPU; 48 sampled searches re-run by the oracle."""
+    n = 800
+    W = wl.maxcut_qubo(n, 0.06, seed=1)
+    kw = dict(searches=1024, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(10, 1), seed_mode=0)
+    ctx = D.Context(W, **kw)
+    so = orc.Solver(W, orc.make_params(**kw), 1)
+    ctx.solve_begin(1)
+    ctx.solve_generations(1)
+    Dg, ag, og, bX, bE, fl = ctx.read_generation()
+    oD, oa, oo = so.offspring(0)
+    assert np.array_equal(wl.unpack_bits(Dg, n), oD) and np.array_equal(ag, oa)
+    p = orc.make_params(**kw)
+    gb = wl.unpack_bits(bX, n)
+    z = np.zeros(n, np.uint8)
+    for s in np.random.default_rng(0).choice(1024, 48, replace=False):
+        r = orc.batch_search(W, p, 1, 0, int(s), z, np.diag(W).astype(np.int32), 0, oD[s], int(oa[s]))
+        assert int(fl[s]) == r["flips"] and int(bE[s]) == r["best_E"]
+        assert np.array_equal(gb[s], r["best_X"])
+    assert (fl >= 8000).all()
