@@ -1,0 +1,355 @@
+"""Benchmark of the DABS bulk local search on GB300.
+
+Default workload: the sparse Max-Cut-shaped QUBO (G(n=800, p=0.06), edge
+weights +-1, seed 1) with 1024 concurrent searches, 4 pools x 100 packets,
+tabu 8, s = 1/10, b = 10, Straight seeding, one instance per launch.  One step
+is one generation: offspring -> batch search (every search flips >= b*n bits)
+-> pool merge -> finalise, all in the CUDA library.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dabs|reference]
+
+Prints one JSON line.  --impl reference times the plain C oracle (the CPU
+restatement of the method) on the host cores, one generation per step.
+Under torchrun (N > 1) every rank runs an independent replica (weak scaling,
+no collective on the data path); rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2207_03069_gb300 import workloads as wl  # noqa: E402
+
+WORKLOADS = {
+    "maxcut800": dict(desc="sparse Max-Cut QUBO G(n=800,p=0.06) w=+-1 seed 1", n=800,
+                      searches=1024, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(10, 1),
+                      seed_mode=0),
+    "dense64": dict(desc="dense QUBO n=64 W~U[-100,100] seed 0", n=64, searches=32, pools=4,
+                    pool_cap=64, tabu=8, s=(1, 10), b=(1, 1), seed_mode=0),
+    "tsp32": dict(desc="TSP one-hot 32 cities (1024 bits) grid 1000 seed 2", n=1024,
+                  searches=2048, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=0),
+}
+
+
+def make_W(name):
+    if name == "maxcut800":
+        return wl.maxcut_qubo(800, 0.06, seed=1)
+    if name == "dense64":
+        return wl.dense_qubo(64, -100, 100, seed=0)
+    if name == "tsp32":
+        return wl.tsp_qubo(32, 1000, seed=2)[0]
+    raise ValueError(name)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def search_profile():
+    """DRAM traffic of the batch-search kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "search_maxcut800.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        prof = json.load(f)
+    h = hashlib.sha256()
+    for fn in ("search.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2207_03069_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    if prof.get("kernel_sha256") != h.hexdigest():
+        return None
+    return prof
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def l2_copy_gbs(torch, dev):
+    """Read+write bandwidth of a 32 MiB device copy that stays in L2 (context)."""
+    a = torch.empty(8 << 20, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    reps = 200
+    for _ in range(reps):
+        b.copy_(a)
+    e1.record()
+    torch.cuda.synchronize()
+    return 2 * a.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
+def oracle_rate(Wm, spec, seed, seconds, threads):
+    """Oracle (plain C, as it stands) on the same workload: whole generations on
+    `threads` host threads until `seconds` have passed.  Returns (flips/s, gens)."""
+    from oracle import oracle as orc
+    p = orc.make_params(searches=spec["searches"], pools=spec["pools"], pool_cap=spec["pool_cap"],
+                        tabu=spec["tabu"], s=spec["s"], b=spec["b"], seed_mode=spec["seed_mode"])
+    so = orc.Solver(Wm, p, seed)
+    t0 = time.perf_counter()
+    flips, gens = 0, 0
+    while True:
+        flips += so.generation(threads)
+        gens += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return flips / (time.perf_counter() - t0), gens
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    return ws, rank, lrank, pg
+
+
+def run_reference(args, ws, rank, pg):
+    spec = WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    Wm = make_W(args.workload)
+    from oracle import oracle as orc
+    threads = os.cpu_count() or 1
+    p = orc.make_params(searches=spec["searches"], pools=spec["pools"], pool_cap=spec["pool_cap"],
+                        tabu=spec["tabu"], s=spec["s"], b=spec["b"], seed_mode=spec["seed_mode"])
+    so = orc.Solver(Wm, p, args.seed)
+    for _ in range(args.warmup):
+        so.generation(threads)
+    t0 = time.perf_counter()
+    flips = 0
+    for _ in range(args.steps):
+        flips += so.generation(threads)
+    dt = time.perf_counter() - t0
+    v = flips / dt
+    line = {"impl": "reference", "metric": "bit flips/s", "value": v, "unit": "flips/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": spec["desc"], "searches": spec["searches"],
+                       "pools": spec["pools"], "pool_cap": spec["pool_cap"],
+                       "parallelism": "host threads"},
+            "cpu_baseline": {"value": v, "unit": "flips/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} whole generations after {args.warmup} "
+                                       f"warm-up generations, {spec['searches']} searches"},
+            "e2e": {"value": v, "unit": "flips/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dabs", choices=["dabs", "reference"])
+    ap.add_argument("--workload", default="maxcut800", choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, lrank, pg = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank, pg)
+        if pg:
+            pg.barrier()
+        return
+
+    import torch
+    from paper_2207_03069_gb300 import build, dabs
+
+    build.build()
+    torch.cuda.set_device(lrank)
+    dev = torch.device("cuda", lrank)
+    spec = WORKLOADS[args.workload]
+    Wm = make_W(args.workload)
+    n = Wm.shape[0]
+    kw = {k: spec[k] for k in ("searches", "pools", "pool_cap", "tabu", "s", "b", "seed_mode")}
+    ctx = dabs.Context(Wm, **kw)
+    stream = torch.cuda.Stream(device=dev)
+    ctx.set_stream(stream)
+    seed = args.seed + 1000 * rank
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    # ---------------- device-resident timing: one generation per step
+    ctx.solve_begin(seed)
+    for _ in range(args.warmup):
+        ctx.solve_generations(1)
+    st0 = ctx.solve_status()
+    sampler = ClockSampler(lrank)
+    sampler.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)  # untimed: evict L2 between timed steps
+        e = ev[k]
+        e[0].record(stream)
+        ctx.run_stage(dabs.STAGE_OFFSPRING)
+        e[1].record(stream)
+        ctx.run_stage(dabs.STAGE_SEARCH)
+        e[2].record(stream)
+        ctx.run_stage(dabs.STAGE_MERGE)
+        ctx.run_stage(dabs.STAGE_FINALIZE)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = sampler.stop()
+    st1 = ctx.solve_status()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    search_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    total_s = sum(step_ms) * 1e-3
+    flips = st1["flips"] - st0["flips"]
+    if pg:
+        t = torch.tensor([total_s, flips], dtype=torch.float64)
+        tmax = t.clone()
+        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+        pg.all_reduce(t, op=pg.ReduceOp.SUM)
+        total_s, flips = float(tmax[0]), float(t[1])
+    value = flips / total_s
+    flips_rank = st1["flips"] - st0["flips"]
+
+    # ---------------- roofline of the batch-search kernel
+    hbm, peak_kind = peaks()
+    algo_bytes = flips_rank * 2 * n / args.steps  # int16 row of W per flip, per launch
+    launch_s = sum(search_ms) * 1e-3 / args.steps
+    achieved = algo_bytes / launch_s / 1e9
+    prof = search_profile()
+    l2 = l2_copy_gbs(torch, dev)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_kind": f"{peak_kind} HBM copy",
+                "traffic": prof["dram_bytes_per_launch"] if prof else None,
+                "kernel": "k_batch_search", "algorithmic_bytes_per_launch": algo_bytes,
+                "launch_ms": launch_s * 1e3, "search_share_of_step": sum(search_ms) / sum(step_ms),
+                "l2_copy_gbs_measured": l2, "frac_of_l2_copy": achieved / l2}
+
+    # ---------------- end to end through the C ABI with host buffers
+    Wpin = torch.empty((n, n), dtype=torch.int16, pin_memory=True).numpy()
+    Wpin[:] = Wm
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    ctx.set_stream(None)
+    ctx.solve(1, seed=seed)  # warm
+    t0 = time.perf_counter()
+    e2e_flips = 0
+    for k in range(e2e_steps):
+        ctx.load_weights(Wpin)              # H2D of the step's input
+        X, E, f = ctx.solve(1, seed=seed + k)  # one generation, best X/E back to the host
+        e2e_flips += f
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": e2e_flips / e2e_s, "unit": "flips/s", "h2d_bytes_per_step": 2 * n * n,
+           "d2h_bytes_per_step": n + 8,
+           "call": "dabs_load_weights + dabs_solve(budget=1 generation) per step"}
+
+    # ---------------- CPU baseline: the oracle as it stands, bounded sample
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, gens = oracle_rate(Wm, spec, seed, args.cpu_seconds, threads)
+        cpu = {"value": rate, "unit": "flips/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {gens} generation(s) of the same workload ({spec['searches']} "
+                         f"searches), about {args.cpu_seconds:.0f} s"}
+
+    if rank == 0:
+        line = {"metric": "bit flips/s", "value": value, "unit": "flips/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": sum(step_ms) / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": spec["desc"], "n": n, "searches": spec["searches"],
+                           "pools": spec["pools"], "pool_cap": spec["pool_cap"],
+                           "tabu": spec["tabu"], "s": "%d/%d" % spec["s"],
+                           "b": "%d/%d" % spec["b"],
+                           "seeding": "straight" if spec["seed_mode"] == 0 else "recompute",
+                           "variant": "%d warp(s) x %d chunk(s)" % (ctx.info()["warps"],
+                                                                    ctx.info()["chunks"]),
+                           "l2": "flushed (256 MiB write) between timed steps",
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "delta_updates_per_s": value * n, "gpu_launches": 4 * args.steps,
+                "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.barrier()
+
+
+if __name__ == "__main__":
+    main()

@@ -263,4 +263,5 @@ def test_maxcut_workload_sampled_at_full_size(D, orc):
         r = orc.batch_search(W, p, 1, 0, int(s), z, np.diag(W).astype(np.int32), 0, oD[s], int(oa[s]))
         assert int(fl[s]) == r["flips"] and int(bE[s]) == r["best_E"]
         assert np.array_equal(gb[s], r["best_X"])
-    assert (fl >= 8000).all()
+    # b*n = 8000 flips, except TwoNeighbor, which runs once (Section III-B)
+    assert (fl[ag != 4] >= 8000).all() and (fl[ag == 4] >= 2 * n - 1).all()
