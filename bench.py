@@ -222,6 +222,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--variant", default="", help="force warps x chunks, e.g. 4x1")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, lrank, pg = dist_setup()
@@ -244,6 +246,12 @@ def main():
     ctx = dabs.Context(Wm, **kw)
     stream = torch.cuda.Stream(device=dev)
     ctx.set_stream(stream)
+    sweep = {}
+    if args.variant:
+        ctx.set_variant(*[int(x) for x in args.variant.split("x")])
+    elif not args.no_autotune:
+        tuned = ctx.autotune(2)  # untimed: picks warps x chunks for this workload
+        sweep = {"chosen": "%dx%d" % tuned[:2], "ns_per_flip": tuned[3]}
     seed = args.seed + 1000 * rank
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
@@ -343,7 +351,7 @@ def main():
                                                                     ctx.info()["chunks"]),
                            "l2": "flushed (256 MiB write) between timed steps",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
-                "delta_updates_per_s": value * n, "gpu_launches": 4 * args.steps,
+                "delta_updates_per_s": value * n, "autotune": sweep, "gpu_launches": 4 * args.steps,
                 "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -145,6 +145,16 @@ int dabs_info(const dabs_ctx* ctx, int32_t* n, int32_t* ld, int32_t* words, int3
               int32_t* pools, int32_t* pool_cap, int32_t* warps, int32_t* chunks);
 /* Chooses the batch-search variant; returns TOO_LARGE if it cannot hold n. */
 int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
+/* Times the batch-search stage of every built variant that holds n over
+ * `generations` generations of a throwaway solve on the context's workload
+ * and keeps the fastest per flip (results never depend on the variant).
+ * table (may be NULL) receives DABS_N_VARIANTS nanoseconds-per-flip entries
+ * in the order (warps x chunks) 1x1 1x2 1x4 2x1 2x2 2x4 4x1 4x2 4x4 8x1 8x2
+ * 8x4 16x1 16x2, 0 where a variant cannot hold n.  Resets the solve state;
+ * call before dabs_solve_begin.  Synchronous. */
+#define DABS_N_VARIANTS 14
+int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* chunks,
+                  float* ns_per_flip, float* table);
 /* Current pools (the ones the next generation breeds from): X [P][C][words],
  * E [P][C], algo [P][C], op [P][C].  Any pointer may be NULL. */
 int dabs_read_pools(dabs_ctx* ctx, uint32_t* X, int64_t* E, uint8_t* algo, uint8_t* op);

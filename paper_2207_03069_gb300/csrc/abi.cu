@@ -495,6 +495,60 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks) {
   return DABS_OK;
 }
 
+int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* chunks,
+                  float* ns_per_flip, float* table) {
+  if (!ctx || generations < 1) return DABS_E_INVALID_ARG;
+  static const int cand[DABS_N_VARIANTS][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4},
+                                               {4, 1}, {4, 2}, {4, 4}, {8, 1}, {8, 2}, {8, 4},
+                                               {16, 1}, {16, 2}};
+  if (table)
+    for (int q = 0; q < DABS_N_VARIANTS; ++q) table[q] = 0.f;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const SearchVariant keep = ctx->var;
+  SearchVariant best = keep;
+  float best_ns = 0.f;
+  int rc = DABS_OK;
+  for (int ci = 0; ci < DABS_N_VARIANTS; ++ci) {
+    const int* c = cand[ci];
+    SearchVariant v;
+    if (!launch_search(c[0], c[1], nullptr, nullptr, &v) || v.cap < ctx->n) continue;
+    ctx->var = v;
+    // a throwaway solve: results never depend on the variant
+    if ((rc = dabs_solve_begin(ctx, 0x5eed, UINT64_MAX, INT64_MIN)) != DABS_OK) break;
+    if ((rc = dabs_solve_generations(ctx, 1)) != DABS_OK) break;
+    float ms_total = 0.f;
+    DevCtrl c0, c1;
+    if ((rc = read_ctrl(ctx, &c0)) != DABS_OK) break;
+    for (int q = 0; q < generations; ++q) {
+      if ((rc = stage(ctx, 0)) != DABS_OK) break;
+      CK(cudaEventRecord(e0, ctx->stream));
+      if ((rc = stage(ctx, 1)) != DABS_OK) break;
+      CK(cudaEventRecord(e1, ctx->stream));
+      if ((rc = stage(ctx, 2)) != DABS_OK || (rc = stage(ctx, 3)) != DABS_OK) break;
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      ms_total += ms;
+    }
+    if (rc != DABS_OK) break;
+    if ((rc = read_ctrl(ctx, &c1)) != DABS_OK) break;
+    const double fl = (double)(c1.flips_total - c0.flips_total);
+    const float ns = fl > 0 ? (float)(ms_total * 1e6 / fl) : 1e30f;
+    if (table) table[ci] = ns;
+    if (best_ns == 0.f || ns < best_ns) { best_ns = ns; best = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != DABS_OK) { ctx->var = keep; return rc; }
+  ctx->var = best;
+  if (warps) *warps = best.nw;
+  if (chunks) *chunks = best.ch;
+  if (ns_per_flip) *ns_per_flip = best_ns;
+  return dabs_solve_begin(ctx, 0, UINT64_MAX, INT64_MIN);
+}
+
 static int cur_buf(dabs_ctx* ctx, int* b) {
   DevCtrl c;
   const int rc = read_ctrl(ctx, &c);

@@ -5,16 +5,20 @@
 // phase's selector), Step 3 (E += Delta_i, Delta_k += W_ik sigma(x_i) sigma(x_k)
 // for k != i by Eq. (4), Delta_i = -Delta_i by Eq. (5)).
 //
+// The phases (Straight, Greedy, main search) run in one loop with a single
+// reduction site for Step 1 and a single flip site, which keeps the kernel's
+// code small (instruction-cache friendly) whatever the algorithm mix.
+//
 // Register layout: thread t of a group (NT = 32 NW threads) owns, for chunk
 // c = 0..CH-1, the eight consecutive bits k = c*8*NT + 8t + e (e = 0..7).  One
 // 128-bit load per chunk brings the thread's eight int16 weights of row i, so
 // a whole row is read with fully coalesced 16-byte accesses.  Bit k lives at
 // local position p = 8c + e of the thread's Delta array and bit masks.
 //
-// Reductions use the sm_80+ warp reduce instructions and, for NW > 1, one
+// Reductions use the warp reduce instructions and, for NW > 1, one
 // shared-memory slot round per reduction (double-buffered, one barrier).
-// Ties always resolve to the lowest bit index (for CyclicMin: the first bit in
-// cyclic order from the window start).
+// Ties resolve to the lowest bit index (CyclicMin: the first bit in cyclic
+// order from the window start).
 #pragma once
 #include "common.cuh"
 
@@ -33,6 +37,8 @@ struct Cfg {
 };
 
 constexpr unsigned FULL = 0xffffffffu;
+enum Phase : int { PH_STRAIGHT = 0, PH_GREEDY = 1, PH_MAIN = 2 };
+enum Selector : int { SEL_STRAIGHT = 8, SEL_GREEDY = 9 };
 
 __device__ __forceinline__ int sext_lo(uint32_t w) { return (int)(w << 16) >> 16; }
 __device__ __forceinline__ int sext_hi(uint32_t w) { return (int)w >> 16; }
@@ -43,6 +49,11 @@ __device__ __forceinline__ int w16(const uint4& v, int e) {
 __device__ __forceinline__ uint32_t u32of(const uint4& v, int q) {
   return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
 }
+// bits [lo, hi) of the 8-bit run starting at b0, as an 8-bit mask
+__device__ __forceinline__ uint32_t run_mask(int b0, int lo, int hi) {
+  const int a = max(lo, b0), b = min(hi, b0 + 8);
+  return a < b ? (((1u << (b - a)) - 1u) << (a - b0)) : 0u;
+}
 
 template <class C>
 struct SmemSearch {
@@ -52,10 +63,16 @@ struct SmemSearch {
   int ring[C::NW][32];       // tabu list (one copy per warp: warp-synchronous updates)
 };
 
+#define DABS_CASES(X)                                                                      \
+  X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15)    \
+  X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29)      \
+  X(30) X(31)
+
 template <class C>
 struct Searcher {
   static constexpr int NW = C::NW, CH = C::CH, NT = C::NT, EPT = C::EPT, SPAN = C::SPAN,
                        NMW = C::NMW;
+  static_assert(EPT <= 32, "register-resident variants hold at most 32 bits per thread");
   // --- state (registers) ---
   int d[EPT];          // Delta (INT_MAX for bits >= n)
   uint32_t xb[NMW];    // X bits
@@ -66,61 +83,56 @@ struct Searcher {
   int64_t E, Ebest;
   uint32_t flips;
   // --- context ---
-  const SearchArgs a;
   SmemSearch<C>* sm;
   int t, lane, warp, buf;
   uint32_t s, g;
   uint64_t seed;
   const int16_t* W;
   int n, ld;
-  // tabu ring (uniform): flipped bits of the last tau main iterations
-  int ring_len, ring_head;
+  int ring_len, ring_head;  // tabu ring (uniform)
 
-  __device__ __forceinline__ Searcher(const SearchArgs& args, SmemSearch<C>* smem, int tid, uint32_t sidx,
-                      uint32_t gen, uint64_t sd)
-      : a(args), sm(smem), t(tid), lane(tid & 31), warp(tid >> 5), buf(0), s(sidx), g(gen),
-        seed(sd), W(args.W), n(args.n), ld(args.ld) {}
+  __device__ __forceinline__ Searcher(const SearchArgs& a, SmemSearch<C>* smem, int tid,
+                                      uint32_t sidx, uint32_t gen, uint64_t sd)
+      : sm(smem), t(tid), lane(tid & 31), warp(tid >> 5), buf(0), s(sidx), g(gen), seed(sd),
+        W(a.W), n(a.n), ld(a.ld), ring_len(0), ring_head(0) {}
 
   // ------------------------------------------------------------ bit helpers
-  __device__ __forceinline__ static bool bit(const uint32_t (&m)[NMW], int p) {
-    return (m[p >> 5] >> (p & 31)) & 1u;
-  }
-  // same for a run-time position (no dynamic register-array indexing)
   __device__ __forceinline__ static bool bit_at(const uint32_t (&m)[NMW], int p) {
-    uint32_t w = 0;
-#pragma unroll
-    for (int q = 0; q < NMW; ++q)
-      if (q == (p >> 5)) w = m[q];
-    return (w >> (p & 31)) & 1u;
+    return (m[0] >> (p & 31)) & 1u;  // NMW == 1
   }
   __device__ __forceinline__ int kidx(int p) const { return (p >> 3) * SPAN + 8 * t + (p & 7); }
   __device__ __forceinline__ static int owner_t(int i) { return (i >> 3) & (NT - 1); }
   __device__ __forceinline__ static int local_p(int i) { return ((i >> 3) / NT) * 8 + (i & 7); }
-  __device__ __forceinline__ void toggle(uint32_t (&m)[NMW], int p) {
-#pragma unroll
-    for (int q = 0; q < NMW; ++q)
-      if (q == (p >> 5)) m[q] ^= 1u << (p & 31);
+  __device__ __forceinline__ uint32_t key_of(int lp) const {
+    return lp < 0 ? UINT_MAX : (((uint32_t)kidx(lp) << 1) | (uint32_t)bit_at(xb, lp));
   }
-  // value of d at a run-time position p (same p in all threads of the group)
+  // value of d at a run-time position (a switch, no local memory)
   __device__ __forceinline__ int get_at(int p) const {
     int v = 0;
-#pragma unroll
-    for (int q = 0; q < EPT; ++q)
-      if (q == p) v = d[q];
+    switch (p) {
+#define DABS_GET(q) \
+  case q:           \
+    if constexpr (q < EPT) v = d[q < EPT ? q : 0]; \
+    break;
+      DABS_CASES(DABS_GET)
+#undef DABS_GET
+      default: break;
+    }
     return v;
   }
   __device__ __forceinline__ void set_at(int p, int v) {
-#pragma unroll
-    for (int q = 0; q < EPT; ++q)
-      if (q == p) d[q] = v;
+    switch (p) {
+#define DABS_SET(q) \
+  case q:           \
+    if constexpr (q < EPT) d[q < EPT ? q : 0] = v; \
+    break;
+      DABS_CASES(DABS_SET)
+#undef DABS_SET
+      default: break;
+    }
   }
 
   // ------------------------------------------------------------ reductions
-  __device__ __forceinline__ void gsync() {
-    if constexpr (NW == 1) __syncwarp();
-    else __syncthreads();
-  }
-  // group min of up to three int values (warp reduce, then a slot round)
   template <int K>
   __device__ __forceinline__ void gmin(int (&v)[K]) {
 #pragma unroll
@@ -169,36 +181,38 @@ struct Searcher {
     for (int p = 0; p < EPT; ++p) m = min(m, d[p]);
     return m;
   }
-  __device__ __forceinline__ int tmin_mask(const uint32_t (&M)[NMW]) const {
+  __device__ __forceinline__ int tmin_mask(uint32_t M) const {
     int m = INT_MAX;
 #pragma unroll
-    for (int p = 0; p < EPT; ++p)
-      if (bit(M, p)) m = min(m, d[p]);
+    for (int p = 0; p < EPT; ++p) m = min(m, ((M >> p) & 1u) ? d[p] : INT_MAX);
     return m;
   }
-  // key = (k << 1) | x_k of the lowest k with d == v (UINT_MAX if none)
-  __device__ __forceinline__ uint32_t tkey_eq(int v) const {
-    uint32_t key = UINT_MAX;
+  __device__ __forceinline__ int tmax_mask(uint32_t M) const {
+    int m = INT_MIN;
 #pragma unroll
-    for (int p = EPT - 1; p >= 0; --p)
-      if (d[p] == v) key = ((uint32_t)kidx(p) << 1) | (uint32_t)bit(xb, p);
-    return key;
+    for (int p = 0; p < EPT; ++p) m = max(m, ((M >> p) & 1u) ? d[p] : INT_MIN);
+    return m;
   }
-  __device__ __forceinline__ uint32_t tkey_eq_mask(int v, const uint32_t (&M)[NMW]) const {
-    uint32_t key = UINT_MAX;
+  // lowest local position with d == v (inside M), -1 if none
+  __device__ __forceinline__ int tlow_eq(int v) const {
+    int lp = -1;
 #pragma unroll
-    for (int p = EPT - 1; p >= 0; --p)
-      if (bit(M, p) && d[p] == v) key = ((uint32_t)kidx(p) << 1) | (uint32_t)bit(xb, p);
-    return key;
+    for (int p = EPT - 1; p >= 0; --p) lp = d[p] == v ? p : lp;
+    return lp;
+  }
+  __device__ __forceinline__ int tlow_eq_mask(int v, uint32_t M) const {
+    int lp = -1;
+#pragma unroll
+    for (int p = EPT - 1; p >= 0; --p) lp = (((M >> p) & 1u) && d[p] == v) ? p : lp;
+    return lp;
   }
 
   // ------------------------------------------------------------ Step 1 / Step 3
   // BEST <- f_j(X) for j = key >> 1 (Step 1 on strict improvement)
   __device__ __forceinline__ void take_best(uint32_t keyj, int m) {
     const int j = (int)(keyj >> 1);
-#pragma unroll
-    for (int q = 0; q < NMW; ++q) bb[q] = xb[q];
-    if (t == owner_t(j)) toggle(bb, local_p(j));
+    bb[0] = xb[0];
+    if (t == owner_t(j)) bb[0] ^= 1u << local_p(j);
     Ebest = E + m;
   }
 
@@ -214,22 +228,21 @@ struct Searcher {
       const int off = c * SPAN + 8 * t;
       rv[c] = off < ld ? __ldg(reinterpret_cast<const uint4*>(row + off)) : make_uint4(0, 0, 0, 0);
     }
-    const uint32_t xim = xi ? FULL : 0u;
+    // bit p of xs is set where x_k != x_i, i.e. sigma(x_i) sigma(x_k) = -1
+    const uint32_t xs = xb[0] ^ (xi ? FULL : 0u);
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int p = 8 * c + e;
-        // -1 where x_k != x_i: sigma(x_i) sigma(x_k) = (m | 1)
-        const int m = -(int)(((xb[p >> 5] ^ xim) >> (p & 31)) & 1u);
+        const int m = (int)(xs << (31 - p)) >> 31;  // 0 or -1
         d[p] += w16(rv[c], e) * (m | 1);
       }
     }
-    const int pi = local_p(i);
-    const bool own = (t == owner_t(i));
-    if (own) {
+    if (t == owner_t(i)) {
+      const int pi = local_p(i);
       set_at(pi, -di);  // Eq. (5)
-      toggle(xb, pi);
+      xb[0] ^= 1u << pi;
     }
     E += di;
     ++flips;
@@ -238,11 +251,11 @@ struct Searcher {
   // ------------------------------------------------------------ k-th pick
   // The ((u * count) >> 32)-th set bit of the group-wide candidate mask Cm, in
   // ascending bit order.  Returns key = (i << 1) | x_i and Delta_i via *di.
-  __device__ __forceinline__ uint32_t kth(const uint32_t (&Cm)[NMW], uint32_t u, int* di) {
+  __device__ __forceinline__ uint32_t kth(uint32_t Cm, uint32_t u, int* di) {
     int cnt[CH], wt[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
-      cnt[c] = __popc((Cm[(8 * c) >> 5] >> ((8 * c) & 31)) & 0xFFu);
+      cnt[c] = __popc((Cm >> (8 * c)) & 0xFFu);
       wt[c] = (int)__reduce_add_sync(FULL, (unsigned)cnt[c]);
     }
     int csel = 0, wsel = 0, rel = 0;
@@ -294,25 +307,15 @@ struct Searcher {
       }
       const int excl = incl - mycnt;
       const bool mine = excl <= rel && rel < incl;
+      uint32_t byte = (Cm >> (8 * csel)) & 0xFFu;
+      for (int r = rel - excl; r > 0 && byte; --r) byte &= byte - 1;  // drop r lowest set bits
+      const int p = 8 * csel + (byte ? __ffs(byte) - 1 : 0);
       if (mine) {
-        uint32_t byte = 0;
-#pragma unroll
-        for (int c = 0; c < CH; ++c)
-          if (c == csel) byte = (Cm[(8 * c) >> 5] >> ((8 * c) & 31)) & 0xFFu;
-        int r = rel - excl;
-        int e = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if ((byte >> q) & 1u) {
-            if (r == 0) e = q;
-            --r;
-          }
-        const int p = 8 * csel + e;
-        key = ((uint32_t)kidx(p) << 1) | (uint32_t)bit_at(xb, p);
+        key = key_of(p);
         dv = get_at(p);
       }
       const unsigned bal = __ballot_sync(FULL, mine);
-      const int src = __ffs(bal) - 1;
+      const int src = bal ? __ffs(bal) - 1 : 0;
       key = __shfl_sync(FULL, key, src);
       dv = __shfl_sync(FULL, dv, src);
       if constexpr (NW > 1) {
@@ -347,60 +350,14 @@ struct Searcher {
     return ((uint32_t)i << 1) | x;
   }
 
-  // ------------------------------------------------------------ phases
-  // Greedy (Section III-A): Step 1, stop at a local minimum, else flip argmin.
-  __device__ __forceinline__ void greedy() {
-    for (;;) {
-      int v[1] = {tmin_all()};
-      gmin(v);
-      const int m = v[0];
-      const bool improve = E + m < Ebest;
-      if (m >= 0 && !improve) break;
-      uint32_t k[1] = {tkey_eq(m)};
-      gminu(k);
-      if (improve) take_best(k[0], m);
-      if (m >= 0) break;
-      flip((int)(k[0] >> 1), (int)(k[0] & 1u), m);
-    }
-  }
-
-  // Straight (Section III-A): walk to D flipping the argmin over x_k != d_k.
-  __device__ __forceinline__ void straight() {
-    for (;;) {
-      uint32_t M[NMW];
-#pragma unroll
-      for (int q = 0; q < NMW; ++q) M[q] = (xb[q] ^ db[q]) & vb[q];
-      int v[2] = {tmin_all(), tmin_mask(M)};
-      gmin(v);
-      if (v[1] == INT_MAX) break;  // X == D
-      const int m = v[0], ms = v[1];
-      const bool improve = E + m < Ebest;
-      uint32_t k[2] = {improve ? tkey_eq(m) : UINT_MAX, tkey_eq_mask(ms, M)};
-      gminu(k);
-      if (improve) take_best(k[0], m);
-      flip((int)(k[1] >> 1), (int)(k[1] & 1u), ms);
-    }
-  }
-
-  __device__ __forceinline__ void step1_only(int m) {
-    if (E + m < Ebest) {
-      uint32_t k[1] = {tkey_eq(m)};
-      gminu(k);
-      take_best(k[0], m);
-    }
-  }
-
-  __device__ __forceinline__ void tabu_free(uint32_t (&F)[NMW]) const {
-#pragma unroll
-    for (int q = 0; q < NMW; ++q) F[q] = vb[q] & ~tb[q];
-  }
+  // ------------------------------------------------------------ tabu
   // bit i flipped at this iteration becomes tabu for the next tau iterations
   __device__ __forceinline__ void tabu_push(int i, int tau) {
     if (tau <= 0) return;
     int* ring = sm->ring[warp];
     if (ring_len == tau) {
       const int old = ring[ring_head];
-      if (t == owner_t(old)) toggle(tb, local_p(old));
+      if (t == owner_t(old)) tb[0] ^= 1u << local_p(old);
     } else {
       ++ring_len;
     }
@@ -408,165 +365,183 @@ struct Searcher {
     if (lane == 0) ring[ring_head] = i;
     __syncwarp();
     ring_head = ring_head + 1 == tau ? 0 : ring_head + 1;
-    if (t == owner_t(i)) toggle(tb, local_p(i));
+    if (t == owner_t(i)) tb[0] ^= 1u << local_p(i);
   }
 
-  __device__ __forceinline__ void main_search(int algo, int T, int tau) {
-    if (algo == TWONEIGHBOR) {
-      for (int q = 0; q < 2 * n - 1; ++q) {
-        const int i = q == 0 ? 0 : ((q & 1) ? (q + 1) >> 1 : (q >> 1) - 1);
-        int v[1] = {tmin_all()};
-        gmin(v);
-        step1_only(v[0]);
-        int di;
-        const uint32_t key = fetch(i, &di);
-        flip(i, (int)(key & 1u), di);
-      }
-      return;
-    }
-#pragma unroll
-    for (int q = 0; q < NMW; ++q) tb[q] = 0;
-    ring_len = 0;
-    ring_head = 0;
+  // ------------------------------------------------------------ the batch search
+  // Section III-B: seeding (Straight, unless X was set to D already), Greedy,
+  // then (main search, Greedy) rounds until at least B flips; TwoNeighbor at
+  // most once.  Every iteration first runs Step 1 over all n bits.
+  __device__ __forceinline__ void run(int algo, int seed_mode, int T, int tau, uint32_t B) {
+    int phase = seed_mode == 0 ? PH_STRAIGHT : PH_GREEDY;
+    int runs = 0, it = 0, ws = 0;
+    const int Tmain = algo == TWONEIGHBOR ? 2 * n - 1 : T;
     const int cwin = n < 32 ? n : 32;
     const uint32_t c16 = ((1u << 21) + (uint32_t)n - 1) / (uint32_t)n;
-    int ws = 0;  // CyclicMin window start
-    for (int it = 1; it <= T; ++it) {
-      uint32_t F[NMW];
-      tabu_free(F);
-      int i = 0, xi = 0, di = 0;
-      if (algo == MAXMIN) {
-        int mx = INT_MIN;
-#pragma unroll
-        for (int p = 0; p < EPT; ++p)
-          if (bit(F, p)) mx = max(mx, d[p]);
-        int v[3] = {tmin_all(), tmin_mask(F), ~mx};
-        gmin(v);
-        step1_only(v[0]);
-        const int mn = v[1];
-        const int mxg = ~v[2];
-        const uint64_t q = cube21((uint64_t)(T - it), (uint64_t)T);
-        const uint64_t span = (uint64_t)((int64_t)mxg - (int64_t)mn);
-        const uint64_t R = (q * span) >> 32;
-        const uint4 u = draw(seed, flips, g, s, RNG_MAXMIN);
-        const int64_t thr = (int64_t)mn + (int64_t)(((uint64_t)u.x * (R + 1)) >> 32);
-        uint32_t Cm[NMW];
-#pragma unroll
-        for (int w = 0; w < NMW; ++w) Cm[w] = 0;
-#pragma unroll
-        for (int p = 0; p < EPT; ++p)
-          if (bit(F, p) && (int64_t)d[p] <= thr) Cm[p >> 5] |= 1u << (p & 31);
-        const uint32_t key = kth(Cm, u.y, &di);
-        i = (int)(key >> 1);
-        xi = (int)(key & 1u);
-      } else if (algo == POSITIVEMIN) {
+    for (;;) {
+      const int sel = phase == PH_MAIN ? algo : (phase == PH_STRAIGHT ? SEL_STRAIGHT : SEL_GREEDY);
+      const uint32_t F = vb[0] & ~tb[0];  // free (non-tabu) bits
+      uint32_t Msel = 0, Mw2 = 0;
+      int wsz = 0;
+      int v[3] = {tmin_all(), INT_MAX, INT_MAX};
+      if (sel == SEL_STRAIGHT) {
+        Msel = (xb[0] ^ db[0]) & vb[0];
+        v[1] = tmin_mask(Msel);
+      } else if (sel == MAXMIN) {
+        v[1] = tmin_mask(F);
+        v[2] = ~tmax_mask(F);
+      } else if (sel == POSITIVEMIN) {
         int pm = INT_MAX;
 #pragma unroll
-        for (int p = 0; p < EPT; ++p)
-          if (bit(F, p) && d[p] > 0) pm = min(pm, d[p]);
-        int v[2] = {tmin_all(), pm};
-        gmin(v);
-        step1_only(v[0]);
-        const int pmg = v[1];
-        uint32_t Cm[NMW];
+        for (int p = 0; p < EPT; ++p) pm = min(pm, (((F >> p) & 1u) && d[p] > 0) ? d[p] : INT_MAX);
+        v[1] = pm;
+      } else if (sel == CYCLICMIN) {
+        uint64_t wl = (cube21((uint64_t)(it + 1), (uint64_t)T) * (uint64_t)n) >> 32;
+        wsz = (int)(wl < (uint64_t)cwin ? (uint64_t)cwin : (wl > (uint64_t)n ? (uint64_t)n : wl));
+        // window [ws, ws + wsz) cyclically: [ws, min(ws+wsz, n)) and [0, ws+wsz-n)
+        const int hi1 = min(ws + wsz, n), hi2 = ws + wsz - n;
 #pragma unroll
-        for (int w = 0; w < NMW; ++w) Cm[w] = 0;
-#pragma unroll
-        for (int p = 0; p < EPT; ++p)
-          if (bit(F, p) && (pmg == INT_MAX || d[p] <= pmg)) Cm[p >> 5] |= 1u << (p & 31);
-        const uint4 u = draw(seed, flips, g, s, RNG_POSMIN);
-        const uint32_t key = kth(Cm, u.x, &di);
-        i = (int)(key >> 1);
-        xi = (int)(key & 1u);
-      } else if (algo == CYCLICMIN) {
-        uint64_t wl = (cube21((uint64_t)it, (uint64_t)T) * (uint64_t)n) >> 32;
-        if (wl < (uint64_t)cwin) wl = (uint64_t)cwin;
-        if (wl > (uint64_t)n) wl = (uint64_t)n;
-        const int wsz = (int)wl;
-        int bm = INT_MAX;
-        uint32_t Wm[NMW];
-#pragma unroll
-        for (int w = 0; w < NMW; ++w) Wm[w] = 0;
-#pragma unroll
-        for (int p = 0; p < EPT; ++p) {
-          int r = kidx(p) - ws;
-          if (r < 0) r += n;
-          if (bit(F, p) && r < wsz) {
-            Wm[p >> 5] |= 1u << (p & 31);
-            bm = min(bm, d[p]);
-          }
+        for (int c = 0; c < CH; ++c) {
+          const int b0 = c * SPAN + 8 * t;
+          Msel |= run_mask(b0, ws, hi1) << (8 * c);
+          Mw2 |= run_mask(b0, 0, hi2) << (8 * c);
         }
-        int v[2] = {tmin_all(), bm};
-        gmin(v);
-        const int m = v[0], mw = v[1];
-        const bool improve = E + m < Ebest;
-        // selection key: (cyclic offset from the window start << 1) | x
-        uint32_t kc = UINT_MAX;
-#pragma unroll
-        for (int p = EPT - 1; p >= 0; --p) {
-          int r = kidx(p) - ws;
-          if (r < 0) r += n;
-          if (bit(Wm, p) && d[p] == mw) kc = min(kc, ((uint32_t)r << 1) | (uint32_t)bit(xb, p));
-        }
-        uint32_t k[2] = {improve ? tkey_eq(m) : UINT_MAX, kc};
-        gminu(k);
-        if (improve) take_best(k[0], m);
-        int sel = ws + (int)(k[1] >> 1);
-        if (sel >= n) sel -= n;
-        i = sel;
-        xi = (int)(k[1] & 1u);
-        di = mw;
-        ws += wsz;
-        if (ws >= n) ws -= n;
-      } else {  // RANDOMMIN
-        uint64_t thr = cube21((uint64_t)it, (uint64_t)T) >> 16;
-        if (thr < c16) thr = c16;
-        if (thr > 65536u) thr = 65536u;
-        uint32_t Cm[NMW];
-#pragma unroll
-        for (int w = 0; w < NMW; ++w) Cm[w] = 0;
-        int bc = INT_MAX;
+        Msel &= F;
+        Mw2 &= F;
+        v[1] = tmin_mask(Msel | Mw2);
+      } else if (sel == RANDOMMIN) {
+        uint64_t thr = cube21((uint64_t)(it + 1), (uint64_t)T) >> 16;
+        thr = thr < c16 ? c16 : (thr > 65536u ? 65536u : thr);
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
           const uint4 u = draw(seed, flips, g, s, RNG_RANDMIN | (uint32_t)(c * NT + t));
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const int p = 8 * c + e;
             const uint32_t u16 = (u32of(u, e >> 1) >> (16 * (e & 1))) & 0xFFFFu;
-            if (bit(F, p) && u16 < (uint32_t)thr) {
-              Cm[p >> 5] |= 1u << (p & 31);
-              bc = min(bc, d[p]);
-            }
+            Msel |= (uint32_t)(u16 < (uint32_t)thr) << (8 * c + e);
           }
         }
-        int v[3] = {tmin_all(), bc, tmin_mask(F)};
-        gmin(v);
-        const int m = v[0];
-        const bool improve = E + m < Ebest;
-        const bool have = v[1] != INT_MAX;
-        const int ms = have ? v[1] : v[2];
-        uint32_t k[2] = {improve ? tkey_eq(m) : UINT_MAX, have ? tkey_eq_mask(ms, Cm) : tkey_eq_mask(ms, F)};
-        gminu(k);
-        if (improve) take_best(k[0], m);
-        i = (int)(k[1] >> 1);
-        xi = (int)(k[1] & 1u);
-        di = ms;
+        Msel &= F;
+        v[1] = tmin_mask(Msel);
+        v[2] = tmin_mask(F);
       }
-      flip(i, xi, di);
-      tabu_push(i, tau);
-    }
+      gmin(v);  // round 1: Step 1 minimum and the selector's statistics
+      const int m = v[0];
+      if (sel == SEL_STRAIGHT && v[1] == INT_MAX) {  // X == D: Straight ends
+        phase = PH_GREEDY;
+        continue;
+      }
+      const bool improve = E + m < Ebest;
+      if (sel == SEL_GREEDY && m >= 0) {  // local minimum: Greedy ends after Step 1
+        if (improve) {
+          uint32_t k[1] = {key_of(tlow_eq(m))};
+          gminu(k);
+          take_best(k[0], m);
+        }
+        if (flips < B && !(algo == TWONEIGHBOR && runs >= 1)) {
+          phase = PH_MAIN;
+          it = 0;
+          ws = 0;
+          tb[0] = 0;
+          ring_len = 0;
+          ring_head = 0;
+          continue;
+        }
+        break;
+      }
+      int i = 0, xi = 0, di = 0;
+      uint32_t kj = UINT_MAX;
+      if (sel == SEL_GREEDY || sel == SEL_STRAIGHT || sel == CYCLICMIN || sel == RANDOMMIN) {
+        uint32_t k[2];
+        k[0] = (improve && sel != SEL_GREEDY) ? key_of(tlow_eq(m)) : UINT_MAX;
+        if (sel == SEL_GREEDY) {
+          k[1] = key_of(tlow_eq(m));
+          di = m;
+        } else if (sel == SEL_STRAIGHT) {
+          k[1] = key_of(tlow_eq_mask(v[1], Msel));
+          di = v[1];
+        } else if (sel == CYCLICMIN) {
+          // first in cyclic order from ws: [ws, n) before [0, ws + wsz - n)
+          const int l1 = tlow_eq_mask(v[1], Msel), l2 = tlow_eq_mask(v[1], Mw2);
+          const uint32_t r1 = l1 < 0 ? UINT_MAX : ((uint32_t)(kidx(l1) - ws) << 1) | (uint32_t)bit_at(xb, l1);
+          const uint32_t r2 = l2 < 0 ? UINT_MAX : ((uint32_t)(kidx(l2) + n - ws) << 1) | (uint32_t)bit_at(xb, l2);
+          k[1] = min(r1, r2);
+          di = v[1];
+        } else {  // RANDOMMIN: argmin over candidates, else over free bits
+          const bool have = v[1] != INT_MAX;
+          di = have ? v[1] : v[2];
+          k[1] = key_of(tlow_eq_mask(di, have ? Msel : F));
+        }
+        gminu(k);  // round 2: BEST key and selection key
+        kj = sel == SEL_GREEDY ? k[1] : k[0];
+        if (sel == CYCLICMIN) {
+          const int sb = ws + (int)(k[1] >> 1);
+          i = sb >= n ? sb - n : sb;
+        } else {
+          i = (int)(k[1] >> 1);
+        }
+        xi = (int)(k[1] & 1u);
+      } else {
+        if (improve) {
+          uint32_t k[1] = {key_of(tlow_eq(m))};
+          gminu(k);
+          kj = k[0];
+        }
+        if (sel == TWONEIGHBOR) {
+          i = it == 0 ? 0 : ((it & 1) ? (it + 1) >> 1 : (it >> 1) - 1);
+          xi = (int)(fetch(i, &di) & 1u);
+        } else if (sel == MAXMIN) {
+          const int mn = v[1], mx = ~v[2];
+          const uint64_t q = cube21((uint64_t)(T - (it + 1)), (uint64_t)T);
+          const uint64_t span = (uint64_t)((int64_t)mx - (int64_t)mn);
+          const uint64_t R = (q * span) >> 32;
+          const uint4 u = draw(seed, flips, g, s, RNG_MAXMIN);
+          const int64_t thr = (int64_t)mn + (int64_t)(((uint64_t)u.x * (R + 1)) >> 32);
+          uint32_t Cm = 0;
 #pragma unroll
-    for (int q = 0; q < NMW; ++q) tb[q] = 0;
+          for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)((int64_t)d[p] <= thr) << p;
+          const uint32_t key = kth(Cm & F, u.y, &di);
+          i = (int)(key >> 1);
+          xi = (int)(key & 1u);
+        } else {  // POSITIVEMIN
+          const int pm = v[1];
+          uint32_t Cm = F;
+          if (pm != INT_MAX) {
+            Cm = 0;
+#pragma unroll
+            for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)(d[p] <= pm) << p;
+            Cm &= F;
+          }
+          const uint4 u = draw(seed, flips, g, s, RNG_POSMIN);
+          const uint32_t key = kth(Cm, u.x, &di);
+          i = (int)(key >> 1);
+          xi = (int)(key & 1u);
+        }
+      }
+      if (improve) take_best(kj, m);
+      flip(i, xi, di);
+      if (phase == PH_MAIN) {
+        if (algo != TWONEIGHBOR) tabu_push(i, tau);
+        if (algo == CYCLICMIN) {
+          ws += wsz;
+          if (ws >= n) ws -= n;
+        }
+        if (++it == Tmain) {
+          phase = PH_GREEDY;
+          ++runs;
+          tb[0] = 0;
+        }
+      }
+    }
   }
 
   // ------------------------------------------------------------ state I/O
-  __device__ __forceinline__ void load() {
+  __device__ __forceinline__ void load(const SearchArgs& a) {
     const uint8_t* xbytes = reinterpret_cast<const uint8_t*>(a.X + (size_t)s * a.nw);
     const uint8_t* dbytes = reinterpret_cast<const uint8_t*>(a.D + (size_t)s * a.nw);
     const int32_t* dl = a.delta + (size_t)s * ld;
     const int nbytes = 4 * a.nw;
-#pragma unroll
-    for (int q = 0; q < NMW; ++q) { xb[q] = 0; db[q] = 0; vb[q] = 0; bb[q] = 0; tb[q] = 0; }
+    xb[0] = 0; db[0] = 0; vb[0] = 0; bb[0] = 0; tb[0] = 0;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
       const int base = c * SPAN + 8 * t;
@@ -585,9 +560,9 @@ struct Searcher {
         const bool valid = base + e < n;
         d[p] = valid ? vals[e] : INT_MAX;
         if (valid) {
-          vb[p >> 5] |= 1u << (p & 31);
-          xb[p >> 5] |= ((xbyte >> e) & 1u) << (p & 31);
-          db[p >> 5] |= ((dbyte >> e) & 1u) << (p & 31);
+          vb[0] |= 1u << p;
+          xb[0] |= ((xbyte >> e) & 1u) << p;
+          db[0] |= ((dbyte >> e) & 1u) << p;
         }
       }
     }
@@ -596,7 +571,7 @@ struct Searcher {
     flips = 0;
   }
 
-  __device__ __forceinline__ void store() {
+  __device__ __forceinline__ void store(const SearchArgs& a) {
     uint8_t* xbytes = reinterpret_cast<uint8_t*>(a.X + (size_t)s * a.nw);
     uint8_t* bbytes = reinterpret_cast<uint8_t*>(a.best_X + (size_t)s * a.nw);
     int32_t* dl = a.delta + (size_t)s * ld;
@@ -613,8 +588,8 @@ struct Searcher {
       }
       const int bi = c * NT + t;
       if (bi < nbytes) {
-        xbytes[bi] = (uint8_t)((xb[(8 * c) >> 5] >> ((8 * c) & 31)) & 0xFFu);
-        bbytes[bi] = (uint8_t)((bb[(8 * c) >> 5] >> ((8 * c) & 31)) & 0xFFu);
+        xbytes[bi] = (uint8_t)((xb[0] >> (8 * c)) & 0xFFu);
+        bbytes[bi] = (uint8_t)((bb[0] >> (8 * c)) & 0xFFu);
       }
     }
     if (t == 0) {
@@ -635,19 +610,9 @@ __global__ void __launch_bounds__(Cfg<NW, CH>::CTA) k_batch_search(const SearchA
   const DevCtrl* ctrl = a.ctrl;
   if (ctrl->done) return;
   Searcher<C> sr(a, &smem[sl], threadIdx.x % C::NT, s, ctrl->g, ctrl->seed);
-  sr.load();
-  if (a.seed_mode == 0) sr.straight();
-  sr.greedy();
-  const int algo = a.algo[s];
-  int runs = 0;
-  // Section III-B: (main search, Greedy) rounds until at least b*n flips;
-  // TwoNeighbor at most once.
-  while (sr.flips < a.B && !(algo == TWONEIGHBOR && runs >= 1)) {
-    sr.main_search(algo, a.T, a.tau);
-    ++runs;
-    sr.greedy();
-  }
-  sr.store();
+  sr.load(a);
+  sr.run(a.algo[s], a.seed_mode, a.T, a.tau, a.B);
+  sr.store(a);
 }
 
 }  // namespace dabs

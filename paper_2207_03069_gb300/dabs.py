@@ -61,6 +61,7 @@ EXPORTS = {
                              + [C.c_void_p] * 8),
     "dabs_info": (C.c_int, [C.c_void_p] + [C.c_void_p] * 8),
     "dabs_set_variant": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "dabs_autotune": (C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 4),
     "dabs_read_pools": (C.c_int, [C.c_void_p] * 5),
     "dabs_write_pools": (C.c_int, [C.c_void_p] * 5),
     "dabs_read_state": (C.c_int, [C.c_void_p] * 4),
@@ -158,6 +159,19 @@ class Context:
 
     def set_variant(self, warps: int, chunks: int):
         self._ck(lib().dabs_set_variant(self._h, warps, chunks))
+
+    VARIANTS = ((1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (4, 1), (4, 2), (4, 4), (8, 1),
+                (8, 2), (8, 4), (16, 1), (16, 2))
+
+    def autotune(self, generations: int = 2):
+        """Picks the fastest batch-search variant; resets the solve state.
+        Returns (warps, chunks, ns_per_flip, {"WxC": ns_per_flip})."""
+        w, c, ns = C.c_int32(), C.c_int32(), C.c_float()
+        table = np.zeros(len(self.VARIANTS), np.float32)
+        self._ck(lib().dabs_autotune(self._h, generations, C.byref(w), C.byref(c), C.byref(ns),
+                                     _ptr(table)))
+        per = {"%dx%d" % v: round(float(x), 4) for v, x in zip(self.VARIANTS, table) if x > 0}
+        return int(w.value), int(c.value), float(ns.value), per
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, an int handle, or None (own stream)."""

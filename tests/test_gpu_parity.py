@@ -265,3 +265,16 @@ def test_maxcut_workload_sampled_at_full_size(D, orc):
         assert np.array_equal(gb[s], r["best_X"])
     # b*n = 8000 flips, except TwoNeighbor, which runs once (Section III-B)
     assert (fl[ag != 4] >= 8000).all() and (fl[ag == 4] >= 2 * n - 1).all()
+
+
+def test_autotune_keeps_results(D, orc):
+    n = 300
+    W = wl.dense_qubo(n, -100, 100, seed=4)
+    kw = dict(searches=64, pools=4, pool_cap=16, tabu=8, s=(1, 10), b=(2, 1), seed_mode=0,
+              max_generations=3)
+    ctx = D.Context(W, **kw)
+    w, c, ns, table = ctx.autotune(1)
+    assert 256 * w * c >= n and ns > 0 and table["%dx%d" % (w, c)] == min(table.values())
+    gx, ge, gf = ctx.solve(10**9, seed=2)
+    ox, oe, of, _ = orc.solve(W, orc.make_params(**kw), 10**9, 2, threads=4)
+    assert (ge, gf) == (oe, of) and np.array_equal(gx, ox)
