@@ -6,7 +6,7 @@
  *
  * Problem (Section I-A, Eq. (2)): minimise E(X) = sum_i W_ii x_i +
  * sum_{i<j} W_ij x_i x_j over X in {0,1}^n, for a symmetric int16 matrix W
- * (each unordered pair counted once).  A matrix written with every ordered
+ * with entries in [-32767, 32767] (each unordered pair counted once).  A matrix written with every ordered
  * pair counted converts to this form by W'_ij = W_ij + W_ji (i != j).
  *
  * Conventions of every call:
@@ -75,7 +75,8 @@ int dabs_params_default(dabs_params* p);
  * row-major, symmetric) to device memory once (rows padded to a multiple of
  * 64 entries) and allocates the solver state for *p.  Errors: INVALID_ARG
  * (null pointer, n < 1, bad params), NOT_SYMMETRIC, TOO_LARGE (n > DABS_N_MAX
- * or S / P > 4096), NO_DEVICE, OOM.  On error *out is set to NULL.         */
+ * or S / P > 4096), NO_DEVICE, OOM; INVALID_ARG also when an entry is
+ * -32768 (the library keeps -W on the device).  On error *out is NULL.     */
 int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** out);
 
 /* Frees every device and host resource of ctx (NULL is accepted). */

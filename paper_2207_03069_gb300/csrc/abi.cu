@@ -25,6 +25,7 @@ struct dabs_ctx {
   size_t merge_smem = 0;
   cudaStream_t own = nullptr, stream = nullptr;
   int16_t* W = nullptr;
+  int16_t* Wneg = nullptr;  // -W: lets the flip kernel read row i of sigma(x_i) W
   int32_t* diag = nullptr;
   DevCtrl* ctrl = nullptr;
   DevCtrl* bulk_ctrl = nullptr;
@@ -107,17 +108,24 @@ bool default_variant(int n, SearchVariant* v) {
 int upload_weights(dabs_ctx* ctx, const int16_t* W) {
   const int n = ctx->n, ld = ctx->ld;
   for (int i = 0; i < n; ++i)
-    for (int j = i + 1; j < n; ++j)
+    for (int j = i; j < n; ++j) {
       if (W[(size_t)i * n + j] != W[(size_t)j * n + i])
         return fail(ctx, DABS_E_NOT_SYMMETRIC, "W[%d][%d] != W[%d][%d]", i, j, j, i);
-  std::vector<int16_t> pad((size_t)n * ld, 0);
+      if (W[(size_t)i * n + j] == INT16_MIN)
+        return fail(ctx, DABS_E_INVALID_ARG, "W[%d][%d] = -32768 (weights must lie in [-32767, 32767])", i, j);
+    }
+  std::vector<int16_t> pad((size_t)n * ld, 0), neg((size_t)n * ld, 0);
   std::vector<int32_t> dg(n);
   for (int i = 0; i < n; ++i) {
-    memcpy(&pad[(size_t)i * ld], &W[(size_t)i * n], (size_t)n * sizeof(int16_t));
+    for (int j = 0; j < n; ++j) {
+      pad[(size_t)i * ld + j] = W[(size_t)i * n + j];
+      neg[(size_t)i * ld + j] = (int16_t)-W[(size_t)i * n + j];
+    }
     dg[i] = W[(size_t)i * n + i];
   }
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaMemcpy(ctx->W, pad.data(), pad.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->Wneg, neg.data(), neg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->diag, dg.data(), dg.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   return DABS_OK;
 }
@@ -125,6 +133,7 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
 SearchArgs solve_search_args(dabs_ctx* ctx) {
   SearchArgs a{};
   a.W = ctx->W;
+  a.Wneg = ctx->Wneg;
   a.n = ctx->n; a.ld = ctx->ld; a.nw = ctx->nw; a.S = ctx->S;
   a.T = ctx->T; a.tau = ctx->tau; a.B = ctx->B; a.seed_mode = ctx->p.seed_mode;
   a.ctrl = ctx->ctrl;
@@ -273,6 +282,7 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
   ctx->stream = ctx->own;
   const size_t S = ctx->S, PC = (size_t)ctx->P * ctx->C, nw = ctx->nw, ld = ctx->ld;
   TRY(dalloc(ctx, &ctx->W, (size_t)n * ld));
+  TRY(dalloc(ctx, &ctx->Wneg, (size_t)n * ld));
   TRY(dalloc(ctx, &ctx->diag, (size_t)n));
   TRY(dalloc(ctx, &ctx->ctrl, 1));
   TRY(dalloc(ctx, &ctx->bulk_ctrl, 1));

@@ -98,7 +98,8 @@ struct DevCtrl {
 
 // Arguments of the batch-search kernel (one launch = one batch search per search slot).
 struct SearchArgs {
-  const int16_t* W;  // [n][ld] row-major, zero padded
+  const int16_t* W;     // [n][ld] row-major, zero padded
+  const int16_t* Wneg;  // -W, same layout
   int32_t n, ld, nw; // nw = 32-bit words of a bit vector
   int32_t S;         // search slots in this launch
   int32_t T;         // flips per main search

@@ -49,6 +49,11 @@ __device__ __forceinline__ int w16(const uint4& v, int e) {
 __device__ __forceinline__ uint32_t u32of(const uint4& v, int q) {
   return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
 }
+// f^3 >> 31 for a 21-bit fixed-point ratio f (the cube21 schedule helper)
+__device__ __forceinline__ uint64_t cube_of(uint32_t f) {
+  const uint64_t f2 = (uint64_t)f * f;
+  return (f2 * f) >> 31;
+}
 // bits [lo, hi) of the 8-bit run starting at b0, as an 8-bit mask
 __device__ __forceinline__ uint32_t run_mask(int b0, int lo, int hi) {
   const int a = max(lo, b0), b = min(hi, b0 + 8);
@@ -57,7 +62,7 @@ __device__ __forceinline__ uint32_t run_mask(int b0, int lo, int hi) {
 
 template <class C>
 struct SmemSearch {
-  int red[2][C::NW][4];      // reduction slots (double buffered)
+  int4 red[2][C::NW];        // reduction slots (double buffered)
   int tot[C::CH][C::NW];     // per chunk, per warp candidate counts (k-th pick)
   int pick[4];               // broadcast of a pick made by one thread
   int ring[C::NW][32];       // tabu list (one copy per warp: warp-synchronous updates)
@@ -75,6 +80,7 @@ struct Searcher {
   static_assert(EPT <= 32, "register-resident variants hold at most 32 bits per thread");
   // --- state (registers) ---
   int d[EPT];          // Delta (INT_MAX for bits >= n)
+  int sg[EPT];         // sigma(x_k) = 2 x_k - 1
   uint32_t xb[NMW];    // X bits
   uint32_t bb[NMW];    // BEST bits
   uint32_t vb[NMW];    // valid bits (k < n)
@@ -87,14 +93,15 @@ struct Searcher {
   int t, lane, warp, buf;
   uint32_t s, g;
   uint64_t seed;
-  const int16_t* W;
+  const int16_t* W;     // W, and Wneg = -W: row i of sigma(x_i) W is read directly
+  const int16_t* Wneg;
   int n, ld;
   int ring_len, ring_head;  // tabu ring (uniform)
 
   __device__ __forceinline__ Searcher(const SearchArgs& a, SmemSearch<C>* smem, int tid,
                                       uint32_t sidx, uint32_t gen, uint64_t sd)
       : sm(smem), t(tid), lane(tid & 31), warp(tid >> 5), buf(0), s(sidx), g(gen), seed(sd),
-        W(a.W), n(a.n), ld(a.ld), ring_len(0), ring_head(0) {}
+        W(a.W), Wneg(a.Wneg), n(a.n), ld(a.ld), ring_len(0), ring_head(0) {}
 
   // ------------------------------------------------------------ bit helpers
   __device__ __forceinline__ static bool bit_at(const uint32_t (&m)[NMW], int p) {
@@ -120,11 +127,15 @@ struct Searcher {
     }
     return v;
   }
-  __device__ __forceinline__ void set_at(int p, int v) {
+  // Eq. (5) at a run-time position: Delta_i = -Delta_i (given), sigma flips
+  __device__ __forceinline__ void set_flipped(int p, int v) {
     switch (p) {
-#define DABS_SET(q) \
-  case q:           \
-    if constexpr (q < EPT) d[q < EPT ? q : 0] = v; \
+#define DABS_SET(q)                         \
+  case q:                                   \
+    if constexpr (q < EPT) {                \
+      d[q < EPT ? q : 0] = v;               \
+      sg[q < EPT ? q : 0] = -sg[q < EPT ? q : 0]; \
+    }                                       \
     break;
       DABS_CASES(DABS_SET)
 #undef DABS_SET
@@ -138,18 +149,18 @@ struct Searcher {
 #pragma unroll
     for (int q = 0; q < K; ++q) v[q] = __reduce_min_sync(FULL, v[q]);
     if constexpr (NW > 1) {
-      if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < K; ++q) sm->red[buf][warp][q] = v[q];
-      }
+      if (lane == 0)
+        sm->red[buf][warp] = make_int4(v[0], K > 1 ? v[K > 1 ? 1 : 0] : 0, K > 2 ? v[K > 2 ? 2 : 0] : 0, 0);
       __syncthreads();
+      int4 r = sm->red[buf][0];
 #pragma unroll
-      for (int q = 0; q < K; ++q) {
-        int r = sm->red[buf][0][q];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) r = min(r, sm->red[buf][w][q]);
-        v[q] = r;
+      for (int w = 1; w < NW; ++w) {
+        const int4 o = sm->red[buf][w];
+        r.x = min(r.x, o.x); r.y = min(r.y, o.y); r.z = min(r.z, o.z);
       }
+      v[0] = r.x;
+      if constexpr (K > 1) v[K > 1 ? 1 : 0] = r.y;
+      if constexpr (K > 2) v[K > 2 ? 2 : 0] = r.z;
       buf ^= 1;
     }
   }
@@ -158,18 +169,18 @@ struct Searcher {
 #pragma unroll
     for (int q = 0; q < K; ++q) v[q] = __reduce_min_sync(FULL, v[q]);
     if constexpr (NW > 1) {
-      if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < K; ++q) sm->red[buf][warp][q] = (int)v[q];
-      }
+      if (lane == 0)
+        sm->red[buf][warp] = make_int4((int)v[0], K > 1 ? (int)v[K > 1 ? 1 : 0] : 0, 0, 0);
       __syncthreads();
+      uint32_t r0 = (uint32_t)sm->red[buf][0].x, r1 = (uint32_t)sm->red[buf][0].y;
 #pragma unroll
-      for (int q = 0; q < K; ++q) {
-        uint32_t r = (uint32_t)sm->red[buf][0][q];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) r = min(r, (uint32_t)sm->red[buf][w][q]);
-        v[q] = r;
+      for (int w = 1; w < NW; ++w) {
+        const int4 o = sm->red[buf][w];
+        r0 = min(r0, (uint32_t)o.x);
+        r1 = min(r1, (uint32_t)o.y);
       }
+      v[0] = r0;
+      if constexpr (K > 1) v[K > 1 ? 1 : 0] = r1;
       buf ^= 1;
     }
   }
@@ -221,27 +232,25 @@ struct Searcher {
     // every selector yields 0 <= i < n; the clamp only keeps a logic error
     // from turning into an out-of-bounds read (parity tests would flag it)
     i = min(max(i, 0), n - 1);
-    const int16_t* row = W + (size_t)i * ld;
+    // row i of sigma(x_i) W, so that Eq. (4) is Delta_k += row_k * sigma(x_k)
+    const int16_t* row = (xi ? W : Wneg) + (size_t)i * ld;
     uint4 rv[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
       const int off = c * SPAN + 8 * t;
       rv[c] = off < ld ? __ldg(reinterpret_cast<const uint4*>(row + off)) : make_uint4(0, 0, 0, 0);
     }
-    // bit p of xs is set where x_k != x_i, i.e. sigma(x_i) sigma(x_k) = -1
-    const uint32_t xs = xb[0] ^ (xi ? FULL : 0u);
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int p = 8 * c + e;
-        const int m = (int)(xs << (31 - p)) >> 31;  // 0 or -1
-        d[p] += w16(rv[c], e) * (m | 1);
+        d[p] += w16(rv[c], e) * sg[p];
       }
     }
     if (t == owner_t(i)) {
       const int pi = local_p(i);
-      set_at(pi, -di);  // Eq. (5)
+      set_flipped(pi, -di);  // Eq. (5)
       xb[0] ^= 1u << pi;
     }
     E += di;
@@ -376,6 +385,12 @@ struct Searcher {
     int phase = seed_mode == 0 ? PH_STRAIGHT : PH_GREEDY;
     int runs = 0, it = 0, ws = 0;
     const int Tmain = algo == TWONEIGHBOR ? 2 * n - 1 : T;
+    // exact floor(a * 2^21 / T) for a = t (rising) and a = T - t (falling),
+    // advanced incrementally instead of a 64-bit division per iteration
+    const uint32_t Kq = (1u << 21) / (uint32_t)T, Kr = (1u << 21) % (uint32_t)T;
+    uint32_t fup = 0, rup = 0, fdn = 1u << 21;
+    int rdn = 0;
+    uint32_t rnd0 = 0, rnd1 = 0;  // 32 MaxMin/PositiveMin draws, one per lane
     const int cwin = n < 32 ? n : 32;
     const uint32_t c16 = ((1u << 21) + (uint32_t)n - 1) / (uint32_t)n;
     for (;;) {
@@ -383,6 +398,21 @@ struct Searcher {
       const uint32_t F = vb[0] & ~tb[0];  // free (non-tabu) bits
       uint32_t Msel = 0, Mw2 = 0;
       int wsz = 0;
+      if (phase == PH_MAIN) {
+        fup += Kq;
+        rup += Kr;
+        if (rup >= (uint32_t)T) { ++fup; rup -= (uint32_t)T; }
+        fdn -= Kq;
+        rdn -= (int)Kr;
+        if (rdn < 0) { --fdn; rdn += T; }
+        if ((sel == MAXMIN || sel == POSITIVEMIN) && (it & 31) == 0) {
+          // the flips of iterations it .. it+31 are flips .. flips+31
+          const uint4 u = draw(seed, flips + (uint32_t)lane, g, s,
+                               sel == MAXMIN ? RNG_MAXMIN : RNG_POSMIN);
+          rnd0 = u.x;
+          rnd1 = u.y;
+        }
+      }
       int v[3] = {tmin_all(), INT_MAX, INT_MAX};
       if (sel == SEL_STRAIGHT) {
         Msel = (xb[0] ^ db[0]) & vb[0];
@@ -396,7 +426,7 @@ struct Searcher {
         for (int p = 0; p < EPT; ++p) pm = min(pm, (((F >> p) & 1u) && d[p] > 0) ? d[p] : INT_MAX);
         v[1] = pm;
       } else if (sel == CYCLICMIN) {
-        uint64_t wl = (cube21((uint64_t)(it + 1), (uint64_t)T) * (uint64_t)n) >> 32;
+        uint64_t wl = (cube_of(fup) * (uint64_t)n) >> 32;
         wsz = (int)(wl < (uint64_t)cwin ? (uint64_t)cwin : (wl > (uint64_t)n ? (uint64_t)n : wl));
         // window [ws, ws + wsz) cyclically: [ws, min(ws+wsz, n)) and [0, ws+wsz-n)
         const int hi1 = min(ws + wsz, n), hi2 = ws + wsz - n;
@@ -410,7 +440,7 @@ struct Searcher {
         Mw2 &= F;
         v[1] = tmin_mask(Msel | Mw2);
       } else if (sel == RANDOMMIN) {
-        uint64_t thr = cube21((uint64_t)(it + 1), (uint64_t)T) >> 16;
+        uint64_t thr = cube_of(fup) >> 16;
         thr = thr < c16 ? c16 : (thr > 65536u ? 65536u : thr);
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
@@ -442,6 +472,10 @@ struct Searcher {
           phase = PH_MAIN;
           it = 0;
           ws = 0;
+          fup = 0;
+          rup = 0;
+          fdn = 1u << 21;
+          rdn = 0;
           tb[0] = 0;
           ring_len = 0;
           ring_head = 0;
@@ -492,15 +526,15 @@ struct Searcher {
           xi = (int)(fetch(i, &di) & 1u);
         } else if (sel == MAXMIN) {
           const int mn = v[1], mx = ~v[2];
-          const uint64_t q = cube21((uint64_t)(T - (it + 1)), (uint64_t)T);
+          const uint64_t q = cube_of(fdn);
           const uint64_t span = (uint64_t)((int64_t)mx - (int64_t)mn);
           const uint64_t R = (q * span) >> 32;
-          const uint4 u = draw(seed, flips, g, s, RNG_MAXMIN);
-          const int64_t thr = (int64_t)mn + (int64_t)(((uint64_t)u.x * (R + 1)) >> 32);
+          const uint32_t u0 = __shfl_sync(FULL, rnd0, it & 31), u1 = __shfl_sync(FULL, rnd1, it & 31);
+          const int64_t thr = (int64_t)mn + (int64_t)(((uint64_t)u0 * (R + 1)) >> 32);
           uint32_t Cm = 0;
 #pragma unroll
           for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)((int64_t)d[p] <= thr) << p;
-          const uint32_t key = kth(Cm & F, u.y, &di);
+          const uint32_t key = kth(Cm & F, u1, &di);
           i = (int)(key >> 1);
           xi = (int)(key & 1u);
         } else {  // POSITIVEMIN
@@ -512,8 +546,8 @@ struct Searcher {
             for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)(d[p] <= pm) << p;
             Cm &= F;
           }
-          const uint4 u = draw(seed, flips, g, s, RNG_POSMIN);
-          const uint32_t key = kth(Cm, u.x, &di);
+          const uint32_t u0 = __shfl_sync(FULL, rnd0, it & 31);
+          const uint32_t key = kth(Cm, u0, &di);
           i = (int)(key >> 1);
           xi = (int)(key & 1u);
         }
@@ -559,6 +593,7 @@ struct Searcher {
         const int p = 8 * c + e;
         const bool valid = base + e < n;
         d[p] = valid ? vals[e] : INT_MAX;
+        sg[p] = ((xbyte >> e) & 1u) && valid ? 1 : -1;
         if (valid) {
           vb[0] |= 1u << p;
           xb[0] |= ((xbyte >> e) & 1u) << p;

@@ -30,7 +30,7 @@ def ctx_for(D, W, **kw):
 
 @pytest.mark.parametrize("n", [1, 2, 5, 31, 33, 64, 257, 800, 1000, 2048, 4100, 8192])
 def test_energy_delta(D, orc, n):
-    W = wl.dense_qubo(n, -32768, 32767, seed=n)
+    W = wl.dense_qubo(n, -32767, 32767, seed=n)
     ctx = ctx_for(D, W, searches=1, pools=1, pool_cap=1)
     rng = np.random.default_rng(n)
     for dens in (0.0, 0.5, 1.0, 0.1):
@@ -55,6 +55,11 @@ def test_host_arguments_are_validated(D):
     ctx = ctx_for(D, W)
     with pytest.raises(D.DabsError):
         ctx.energy(np.array([0, 1, 2, 0, 0, 0, 0, 0], np.uint8))
+    Wm = W.copy()
+    Wm[2, 3] = Wm[3, 2] = -32768
+    with pytest.raises(D.DabsError) as e:
+        D.Context(Wm, searches=4, pools=1)
+    assert e.value.code == D.E_INVALID_ARG
     Wa = W.copy()
     Wa[0, 1] += 1
     with pytest.raises(D.DabsError) as e:
@@ -140,7 +145,7 @@ def test_bulk_search_parameter_edges(D, orc, tabu, s, b):
 
 def test_bulk_search_extreme_weights(D, orc):
     n = 512
-    W = wl.dense_qubo(n, -32768, 32767, seed=1)
+    W = wl.dense_qubo(n, -32767, 32767, seed=1)
     bulk_case(D, orc, W, ALGOS, s=(1, 8), b=(1, 1))
     Z = np.zeros((n, n), np.int16)  # all Delta zero: ties everywhere
     bulk_case(D, orc, Z, ALGOS, s=(1, 8), b=(1, 1))
