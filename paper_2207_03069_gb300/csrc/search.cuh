@@ -186,24 +186,6 @@ struct Searcher {
   }
 
   // ------------------------------------------------------------ per-thread scans
-  __device__ __forceinline__ int tmin_all() const {
-    int m = INT_MAX;
-#pragma unroll
-    for (int p = 0; p < EPT; ++p) m = min(m, d[p]);
-    return m;
-  }
-  __device__ __forceinline__ int tmin_mask(uint32_t M) const {
-    int m = INT_MAX;
-#pragma unroll
-    for (int p = 0; p < EPT; ++p) m = min(m, ((M >> p) & 1u) ? d[p] : INT_MAX);
-    return m;
-  }
-  __device__ __forceinline__ int tmax_mask(uint32_t M) const {
-    int m = INT_MIN;
-#pragma unroll
-    for (int p = 0; p < EPT; ++p) m = max(m, ((M >> p) & 1u) ? d[p] : INT_MIN);
-    return m;
-  }
   // lowest local position with d == v (inside M), -1 if none
   __device__ __forceinline__ int tlow_eq(int v) const {
     int lp = -1;
@@ -377,14 +359,45 @@ struct Searcher {
     if (t == owner_t(i)) tb[0] ^= 1u << local_p(i);
   }
 
+  // ------------------------------------------------------------ tree reductions
+  // balanced trees (depth log2 EPT) instead of serial chains: more ILP
+  __device__ __forceinline__ static int tree_min(int (&v)[EPT]) {
+#pragma unroll
+    for (int h = EPT / 2; h > 0; h >>= 1)
+#pragma unroll
+      for (int p = 0; p < h; ++p) v[p] = min(v[p], v[p + h]);
+    return v[0];
+  }
+  __device__ __forceinline__ static int tree_max(int (&v)[EPT]) {
+#pragma unroll
+    for (int h = EPT / 2; h > 0; h >>= 1)
+#pragma unroll
+      for (int p = 0; p < h; ++p) v[p] = max(v[p], v[p + h]);
+    return v[0];
+  }
+  __device__ __forceinline__ int min_all() const {
+    int v[EPT];
+#pragma unroll
+    for (int p = 0; p < EPT; ++p) v[p] = d[p];
+    return tree_min(v);
+  }
+  __device__ __forceinline__ int min_mask(uint32_t M) const {
+    int v[EPT];
+#pragma unroll
+    for (int p = 0; p < EPT; ++p) v[p] = ((M >> p) & 1u) ? d[p] : INT_MAX;
+    return tree_min(v);
+  }
+
   // ------------------------------------------------------------ the batch search
   // Section III-B: seeding (Straight, unless X was set to D already), Greedy,
   // then (main search, Greedy) rounds until at least B flips; TwoNeighbor at
-  // most once.  Every iteration first runs Step 1 over all n bits.
-  __device__ __forceinline__ void run(int algo, int seed_mode, int T, int tau, uint32_t B) {
+  // most once.  Every iteration first runs Step 1 over all n bits.  The loop
+  // is specialised per main algorithm (ALGO) so each body is lean.
+  template <int ALGO>
+  __device__ __forceinline__ void run_algo(int seed_mode, int T, int tau, uint32_t B) {
     int phase = seed_mode == 0 ? PH_STRAIGHT : PH_GREEDY;
     int runs = 0, it = 0, ws = 0;
-    const int Tmain = algo == TWONEIGHBOR ? 2 * n - 1 : T;
+    const int Tmain = ALGO == TWONEIGHBOR ? 2 * n - 1 : T;
     // exact floor(a * 2^21 / T) for a = t (rising) and a = T - t (falling),
     // advanced incrementally instead of a 64-bit division per iteration
     const uint32_t Kq = (1u << 21) / (uint32_t)T, Kr = (1u << 21) % (uint32_t)T;
@@ -394,178 +407,216 @@ struct Searcher {
     const int cwin = n < 32 ? n : 32;
     const uint32_t c16 = ((1u << 21) + (uint32_t)n - 1) / (uint32_t)n;
     for (;;) {
-      const int sel = phase == PH_MAIN ? algo : (phase == PH_STRAIGHT ? SEL_STRAIGHT : SEL_GREEDY);
-      const uint32_t F = vb[0] & ~tb[0];  // free (non-tabu) bits
-      uint32_t Msel = 0, Mw2 = 0;
-      int wsz = 0;
-      if (phase == PH_MAIN) {
+      int i = 0, xi = 0, di = 0;
+      uint32_t kj = UINT_MAX;
+      bool improve;
+      int m;
+      if (phase != PH_MAIN) {
+        // ---------------- Straight / Greedy
+        const bool st = phase == PH_STRAIGHT;
+        const uint32_t Msel = (xb[0] ^ db[0]) & vb[0];
+        int v[2] = {min_all(), st ? min_mask(Msel) : INT_MAX};
+        gmin(v);
+        m = v[0];
+        if (st && v[1] == INT_MAX) {  // X == D: Straight ends
+          phase = PH_GREEDY;
+          continue;
+        }
+        improve = E + m < Ebest;
+        if (!st && m >= 0) {  // local minimum: Greedy ends after Step 1
+          if (improve) {
+            uint32_t k[1] = {key_of(tlow_eq(m))};
+            gminu(k);
+            take_best(k[0], m);
+          }
+          if (flips < B && !(ALGO == TWONEIGHBOR && runs >= 1)) {
+            phase = PH_MAIN;
+            it = 0;
+            ws = 0;
+            fup = 0;
+            rup = 0;
+            fdn = 1u << 21;
+            rdn = 0;
+            tb[0] = 0;
+            ring_len = 0;
+            ring_head = 0;
+            continue;
+          }
+          break;
+        }
+        if (st) {
+          uint32_t k[2] = {improve ? key_of(tlow_eq(m)) : UINT_MAX,
+                           key_of(tlow_eq_mask(v[1], Msel))};
+          gminu(k);
+          kj = k[0];
+          i = (int)(k[1] >> 1);
+          xi = (int)(k[1] & 1u);
+          di = v[1];
+        } else {
+          uint32_t k[1] = {key_of(tlow_eq(m))};
+          gminu(k);
+          kj = k[0];
+          i = (int)(k[0] >> 1);
+          xi = (int)(k[0] & 1u);
+          di = m;
+        }
+      } else {
+        // ---------------- main search iteration t = it + 1
         fup += Kq;
         rup += Kr;
         if (rup >= (uint32_t)T) { ++fup; rup -= (uint32_t)T; }
         fdn -= Kq;
         rdn -= (int)Kr;
         if (rdn < 0) { --fdn; rdn += T; }
-        if ((sel == MAXMIN || sel == POSITIVEMIN) && (it & 31) == 0) {
-          // the flips of iterations it .. it+31 are flips .. flips+31
-          const uint4 u = draw(seed, flips + (uint32_t)lane, g, s,
-                               sel == MAXMIN ? RNG_MAXMIN : RNG_POSMIN);
-          rnd0 = u.x;
-          rnd1 = u.y;
-        }
-      }
-      int v[3] = {tmin_all(), INT_MAX, INT_MAX};
-      if (sel == SEL_STRAIGHT) {
-        Msel = (xb[0] ^ db[0]) & vb[0];
-        v[1] = tmin_mask(Msel);
-      } else if (sel == MAXMIN) {
-        v[1] = tmin_mask(F);
-        v[2] = ~tmax_mask(F);
-      } else if (sel == POSITIVEMIN) {
-        int pm = INT_MAX;
-#pragma unroll
-        for (int p = 0; p < EPT; ++p) pm = min(pm, (((F >> p) & 1u) && d[p] > 0) ? d[p] : INT_MAX);
-        v[1] = pm;
-      } else if (sel == CYCLICMIN) {
-        uint64_t wl = (cube_of(fup) * (uint64_t)n) >> 32;
-        wsz = (int)(wl < (uint64_t)cwin ? (uint64_t)cwin : (wl > (uint64_t)n ? (uint64_t)n : wl));
-        // window [ws, ws + wsz) cyclically: [ws, min(ws+wsz, n)) and [0, ws+wsz-n)
-        const int hi1 = min(ws + wsz, n), hi2 = ws + wsz - n;
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-          const int b0 = c * SPAN + 8 * t;
-          Msel |= run_mask(b0, ws, hi1) << (8 * c);
-          Mw2 |= run_mask(b0, 0, hi2) << (8 * c);
-        }
-        Msel &= F;
-        Mw2 &= F;
-        v[1] = tmin_mask(Msel | Mw2);
-      } else if (sel == RANDOMMIN) {
-        uint64_t thr = cube_of(fup) >> 16;
-        thr = thr < c16 ? c16 : (thr > 65536u ? 65536u : thr);
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-          const uint4 u = draw(seed, flips, g, s, RNG_RANDMIN | (uint32_t)(c * NT + t));
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const uint32_t u16 = (u32of(u, e >> 1) >> (16 * (e & 1))) & 0xFFFFu;
-            Msel |= (uint32_t)(u16 < (uint32_t)thr) << (8 * c + e);
+        const uint32_t F = vb[0] & ~tb[0];  // free (non-tabu) bits
+        if (ALGO == TWONEIGHBOR) {
+          int v[1] = {min_all()};
+          gmin(v);
+          m = v[0];
+          improve = E + m < Ebest;
+          if (improve) {
+            uint32_t k[1] = {key_of(tlow_eq(m))};
+            gminu(k);
+            kj = k[0];
           }
-        }
-        Msel &= F;
-        v[1] = tmin_mask(Msel);
-        v[2] = tmin_mask(F);
-      }
-      gmin(v);  // round 1: Step 1 minimum and the selector's statistics
-      const int m = v[0];
-      if (sel == SEL_STRAIGHT && v[1] == INT_MAX) {  // X == D: Straight ends
-        phase = PH_GREEDY;
-        continue;
-      }
-      const bool improve = E + m < Ebest;
-      if (sel == SEL_GREEDY && m >= 0) {  // local minimum: Greedy ends after Step 1
-        if (improve) {
-          uint32_t k[1] = {key_of(tlow_eq(m))};
-          gminu(k);
-          take_best(k[0], m);
-        }
-        if (flips < B && !(algo == TWONEIGHBOR && runs >= 1)) {
-          phase = PH_MAIN;
-          it = 0;
-          ws = 0;
-          fup = 0;
-          rup = 0;
-          fdn = 1u << 21;
-          rdn = 0;
-          tb[0] = 0;
-          ring_len = 0;
-          ring_head = 0;
-          continue;
-        }
-        break;
-      }
-      int i = 0, xi = 0, di = 0;
-      uint32_t kj = UINT_MAX;
-      if (sel == SEL_GREEDY || sel == SEL_STRAIGHT || sel == CYCLICMIN || sel == RANDOMMIN) {
-        uint32_t k[2];
-        k[0] = (improve && sel != SEL_GREEDY) ? key_of(tlow_eq(m)) : UINT_MAX;
-        if (sel == SEL_GREEDY) {
-          k[1] = key_of(tlow_eq(m));
-          di = m;
-        } else if (sel == SEL_STRAIGHT) {
-          k[1] = key_of(tlow_eq_mask(v[1], Msel));
-          di = v[1];
-        } else if (sel == CYCLICMIN) {
-          // first in cyclic order from ws: [ws, n) before [0, ws + wsz - n)
-          const int l1 = tlow_eq_mask(v[1], Msel), l2 = tlow_eq_mask(v[1], Mw2);
-          const uint32_t r1 = l1 < 0 ? UINT_MAX : ((uint32_t)(kidx(l1) - ws) << 1) | (uint32_t)bit_at(xb, l1);
-          const uint32_t r2 = l2 < 0 ? UINT_MAX : ((uint32_t)(kidx(l2) + n - ws) << 1) | (uint32_t)bit_at(xb, l2);
-          k[1] = min(r1, r2);
-          di = v[1];
-        } else {  // RANDOMMIN: argmin over candidates, else over free bits
-          const bool have = v[1] != INT_MAX;
-          di = have ? v[1] : v[2];
-          k[1] = key_of(tlow_eq_mask(di, have ? Msel : F));
-        }
-        gminu(k);  // round 2: BEST key and selection key
-        kj = sel == SEL_GREEDY ? k[1] : k[0];
-        if (sel == CYCLICMIN) {
-          const int sb = ws + (int)(k[1] >> 1);
-          i = sb >= n ? sb - n : sb;
-        } else {
-          i = (int)(k[1] >> 1);
-        }
-        xi = (int)(k[1] & 1u);
-      } else {
-        if (improve) {
-          uint32_t k[1] = {key_of(tlow_eq(m))};
-          gminu(k);
-          kj = k[0];
-        }
-        if (sel == TWONEIGHBOR) {
           i = it == 0 ? 0 : ((it & 1) ? (it + 1) >> 1 : (it >> 1) - 1);
           xi = (int)(fetch(i, &di) & 1u);
-        } else if (sel == MAXMIN) {
-          const int mn = v[1], mx = ~v[2];
-          const uint64_t q = cube_of(fdn);
-          const uint64_t span = (uint64_t)((int64_t)mx - (int64_t)mn);
-          const uint64_t R = (q * span) >> 32;
-          const uint32_t u0 = __shfl_sync(FULL, rnd0, it & 31), u1 = __shfl_sync(FULL, rnd1, it & 31);
-          const int64_t thr = (int64_t)mn + (int64_t)(((uint64_t)u0 * (R + 1)) >> 32);
-          uint32_t Cm = 0;
-#pragma unroll
-          for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)((int64_t)d[p] <= thr) << p;
-          const uint32_t key = kth(Cm & F, u1, &di);
-          i = (int)(key >> 1);
-          xi = (int)(key & 1u);
-        } else {  // POSITIVEMIN
-          const int pm = v[1];
-          uint32_t Cm = F;
-          if (pm != INT_MAX) {
-            Cm = 0;
-#pragma unroll
-            for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)(d[p] <= pm) << p;
-            Cm &= F;
+        } else if (ALGO == MAXMIN || ALGO == POSITIVEMIN) {
+          if ((it & 31) == 0) {
+            // the flips of iterations it .. it+31 are flips .. flips+31
+            const uint4 u = draw(seed, flips + (uint32_t)lane, g, s,
+                                 ALGO == MAXMIN ? RNG_MAXMIN : RNG_POSMIN);
+            rnd0 = u.x;
+            rnd1 = u.y;
           }
           const uint32_t u0 = __shfl_sync(FULL, rnd0, it & 31);
-          const uint32_t key = kth(Cm, u0, &di);
+          uint32_t Cm = 0, ukth = 0;
+          if (ALGO == MAXMIN) {
+            int vmin[EPT], vmax[EPT];
+#pragma unroll
+            for (int p = 0; p < EPT; ++p) {
+              const bool f = (F >> p) & 1u;
+              vmin[p] = f ? d[p] : INT_MAX;
+              vmax[p] = f ? d[p] : INT_MIN;
+            }
+            int v[3] = {min_all(), tree_min(vmin), ~tree_max(vmax)};
+            gmin(v);
+            m = v[0];
+            const int mn = v[1], mx = ~v[2];
+            const uint64_t q = cube_of(fdn);
+            const uint64_t span = (uint64_t)((int64_t)mx - (int64_t)mn);
+            const uint64_t R = (q * span) >> 32;
+            // threshold in [mn, mx]: fits int32
+            const int thr = (int)((int64_t)mn + (int64_t)(((uint64_t)u0 * (R + 1)) >> 32));
+#pragma unroll
+            for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)(d[p] <= thr) << p;
+            Cm &= F;
+            ukth = __shfl_sync(FULL, rnd1, it & 31);
+          } else {
+            int vpos[EPT];
+#pragma unroll
+            for (int p = 0; p < EPT; ++p) vpos[p] = (((F >> p) & 1u) && d[p] > 0) ? d[p] : INT_MAX;
+            int v[2] = {min_all(), tree_min(vpos)};
+            gmin(v);
+            m = v[0];
+            const int pm = v[1];
+            if (pm != INT_MAX) {
+#pragma unroll
+              for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)(d[p] <= pm) << p;
+              Cm &= F;
+            } else {
+              Cm = F;
+            }
+            ukth = u0;
+          }
+          improve = E + m < Ebest;
+          if (improve) {
+            uint32_t k[1] = {key_of(tlow_eq(m))};
+            gminu(k);
+            kj = k[0];
+          }
+          const uint32_t key = kth(Cm, ukth, &di);
           i = (int)(key >> 1);
           xi = (int)(key & 1u);
+        } else if (ALGO == CYCLICMIN) {
+          const uint64_t wl = (cube_of(fup) * (uint64_t)n) >> 32;
+          const int wsz = (int)(wl < (uint64_t)cwin ? (uint64_t)cwin : (wl > (uint64_t)n ? (uint64_t)n : wl));
+          // window [ws, ws + wsz) cyclically: [ws, min(ws+wsz, n)) and [0, ws+wsz-n)
+          const int hi1 = min(ws + wsz, n), hi2 = ws + wsz - n;
+          uint32_t M1 = 0, M2 = 0;
+#pragma unroll
+          for (int c = 0; c < CH; ++c) {
+            const int b0 = c * SPAN + 8 * t;
+            M1 |= run_mask(b0, ws, hi1) << (8 * c);
+            M2 |= run_mask(b0, 0, hi2) << (8 * c);
+          }
+          M1 &= F;
+          M2 &= F;
+          int v[2] = {min_all(), min_mask(M1 | M2)};
+          gmin(v);
+          m = v[0];
+          improve = E + m < Ebest;
+          // first in cyclic order from ws: [ws, n) before [0, ws + wsz - n)
+          const int l1 = tlow_eq_mask(v[1], M1), l2 = tlow_eq_mask(v[1], M2);
+          const uint32_t r1 = l1 < 0 ? UINT_MAX : ((uint32_t)(kidx(l1) - ws) << 1) | (uint32_t)bit_at(xb, l1);
+          const uint32_t r2 = l2 < 0 ? UINT_MAX : ((uint32_t)(kidx(l2) + n - ws) << 1) | (uint32_t)bit_at(xb, l2);
+          uint32_t k[2] = {improve ? key_of(tlow_eq(m)) : UINT_MAX, min(r1, r2)};
+          gminu(k);
+          kj = k[0];
+          const int sb = ws + (int)(k[1] >> 1);
+          i = sb >= n ? sb - n : sb;
+          xi = (int)(k[1] & 1u);
+          di = v[1];
+          ws += wsz;
+          if (ws >= n) ws -= n;
+        } else {  // RANDOMMIN
+          uint32_t thr = (uint32_t)(cube_of(fup) >> 16);
+          thr = thr < c16 ? c16 : (thr > 65536u ? 65536u : thr);
+          uint32_t Cm = 0;
+#pragma unroll
+          for (int c = 0; c < CH; ++c) {
+            const uint4 u = draw(seed, flips, g, s, RNG_RANDMIN | (uint32_t)(c * NT + t));
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const uint32_t u16 = (u32of(u, e >> 1) >> (16 * (e & 1))) & 0xFFFFu;
+              Cm |= (uint32_t)(u16 < thr) << (8 * c + e);
+            }
+          }
+          Cm &= F;
+          int v[3] = {min_all(), min_mask(Cm), min_mask(F)};
+          gmin(v);
+          m = v[0];
+          improve = E + m < Ebest;
+          const bool have = v[1] != INT_MAX;  // no candidate: argmin over free bits
+          di = have ? v[1] : v[2];
+          uint32_t k[2] = {improve ? key_of(tlow_eq(m)) : UINT_MAX,
+                           key_of(tlow_eq_mask(di, have ? Cm : F))};
+          gminu(k);
+          kj = k[0];
+          i = (int)(k[1] >> 1);
+          xi = (int)(k[1] & 1u);
         }
       }
       if (improve) take_best(kj, m);
       flip(i, xi, di);
       if (phase == PH_MAIN) {
-        if (algo != TWONEIGHBOR) tabu_push(i, tau);
-        if (algo == CYCLICMIN) {
-          ws += wsz;
-          if (ws >= n) ws -= n;
-        }
+        if (ALGO != TWONEIGHBOR) tabu_push(i, tau);
         if (++it == Tmain) {
           phase = PH_GREEDY;
           ++runs;
           tb[0] = 0;
         }
       }
+    }
+  }
+
+  __device__ __forceinline__ void run(int algo, int seed_mode, int T, int tau, uint32_t B) {
+    switch (algo) {
+      case MAXMIN: run_algo<MAXMIN>(seed_mode, T, tau, B); break;
+      case CYCLICMIN: run_algo<CYCLICMIN>(seed_mode, T, tau, B); break;
+      case RANDOMMIN: run_algo<RANDOMMIN>(seed_mode, T, tau, B); break;
+      case POSITIVEMIN: run_algo<POSITIVEMIN>(seed_mode, T, tau, B); break;
+      default: run_algo<TWONEIGHBOR>(seed_mode, T, tau, B); break;
     }
   }
 
