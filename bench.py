@@ -351,7 +351,7 @@ def main():
                                                                     ctx.info()["chunks"]),
                            "l2": "flushed (256 MiB write) between timed steps",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
-                "delta_updates_per_s": value * n, "autotune": sweep, "gpu_launches": 4 * args.steps,
+                "delta_updates_per_s": value * n, "autotune": sweep, "gpu_launches": 5 * args.steps,
                 "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()

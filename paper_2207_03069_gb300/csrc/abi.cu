@@ -43,6 +43,7 @@ struct dabs_ctx {
   uint32_t* bestX = nullptr;
   int64_t* bestE = nullptr;
   uint32_t* flips = nullptr;
+  int32_t* order = nullptr;   // slot launch order grouped by algorithm
   uint32_t* gbestX = nullptr;
   uint32_t* one_X = nullptr;   // single-vector scratch for dabs_energy / dabs_delta
   int32_t* one_d = nullptr;
@@ -139,6 +140,7 @@ SearchArgs solve_search_args(dabs_ctx* ctx) {
   a.ctrl = ctx->ctrl;
   a.X = ctx->X; a.delta = ctx->delta; a.E = ctx->E; a.D = ctx->D; a.algo = ctx->algo;
   a.best_X = ctx->bestX; a.best_E = ctx->bestE; a.flips = ctx->flips;
+  a.order = ctx->order;
   return a;
 }
 
@@ -160,6 +162,8 @@ int stage(dabs_ctx* ctx, int which) {
       CKLAUNCH();
     }
   } else if (which == 1) {
+    k_order_by_algo<<<1, 1024, 0, st>>>(ctx->algo, ctx->S, ctx->order, ctx->ctrl);
+    CKLAUNCH();
     const SearchArgs a = solve_search_args(ctx);
     if (!launch_search(ctx->var.nw, ctx->var.ch, &a, st, nullptr))
       return fail(ctx, DABS_E_INVALID_ARG, "no batch-search variant %d/%d", ctx->var.nw, ctx->var.ch);
@@ -301,6 +305,7 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
   TRY(dalloc(ctx, &ctx->bestX, S * nw));
   TRY(dalloc(ctx, &ctx->bestE, S));
   TRY(dalloc(ctx, &ctx->flips, S));
+  TRY(dalloc(ctx, &ctx->order, S));
   TRY(dalloc(ctx, &ctx->gbestX, nw));
   TRY(dalloc(ctx, &ctx->one_X, nw));
   TRY(dalloc(ctx, &ctx->one_d, ld));
@@ -473,6 +478,12 @@ int dabs_bulk_search_dev(dabs_ctx* ctx, uint64_t seed, uint32_t g, int32_t count
   SearchArgs a = solve_search_args(ctx);
   a.S = count;
   a.ctrl = ctx->bulk_ctrl;
+  a.order = nullptr;
+  if (count <= ctx->S) {
+    k_order_by_algo<<<1, 1024, 0, ctx->stream>>>(algo, count, ctx->order, ctx->bulk_ctrl);
+    CKLAUNCH();
+    a.order = ctx->order;
+  }
   a.X = X; a.delta = delta; a.E = E; a.D = D; a.algo = algo;
   a.best_X = best_X; a.best_E = best_E; a.flips = flips;
   if (!launch_search(ctx->var.nw, ctx->var.ch, &a, ctx->stream, nullptr))

@@ -115,6 +115,7 @@ struct SearchArgs {
   uint32_t* best_X;  // [S][nw]
   int64_t* best_E;   // [S]
   uint32_t* flips;   // [S]
+  const int32_t* order; // launch order of the slots (grouped by algorithm), or null
 };
 
 }  // namespace dabs

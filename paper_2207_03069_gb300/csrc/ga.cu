@@ -383,6 +383,25 @@ __global__ void __launch_bounds__(256) k_energy_delta(const EDArgs a) {
   }
 }
 
+// Launch order of the search slots grouped by main algorithm (any order inside
+// a group: it only decides which CTA runs which search, never a result).
+__global__ void __launch_bounds__(1024) k_order_by_algo(const uint8_t* algo, int S, int32_t* order,
+                                                        const DevCtrl* ctrl) {
+  if (ctrl && ctrl->done) return;
+  __shared__ int cnt[N_ALGOS], off[N_ALGOS];
+  if (threadIdx.x < N_ALGOS) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < S; s += blockDim.x) atomicAdd(&cnt[min((int)algo[s], N_ALGOS - 1)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int q = 0; q < N_ALGOS; ++q) { off[q] = acc; acc += cnt[q]; }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < S; s += blockDim.x)
+    order[atomicAdd(&off[min((int)algo[s], N_ALGOS - 1)], 1)] = s;
+}
+
 // X <- D and Delta, E from scratch for every search slot (recompute seeding);
 // the energy accumulators must be zero before the launch.
 __global__ void k_copy_targets(const uint32_t* D, uint32_t* X, int64_t* E, size_t words, int S,

@@ -81,6 +81,7 @@ __global__ void k_offspring(const OffArgs a);
 __global__ void k_merge(const MergeArgs a);
 __global__ void k_finalize(const FinArgs a);
 __global__ void k_energy_delta(const EDArgs a);
+__global__ void k_order_by_algo(const uint8_t* algo, int S, int32_t* order, const DevCtrl* ctrl);
 __global__ void k_copy_targets(const uint32_t* D, uint32_t* X, int64_t* E, size_t words, int S,
                                const DevCtrl* ctrl);
 

@@ -691,8 +691,11 @@ __global__ void __launch_bounds__(Cfg<NW, CH>::CTA) k_batch_search(const SearchA
   using C = Cfg<NW, CH>;
   __shared__ SmemSearch<C> smem[C::SPC];
   const int sl = threadIdx.x / C::NT;
-  const uint32_t s = blockIdx.x * C::SPC + sl;
-  if (s >= (uint32_t)a.S) return;
+  const uint32_t slot = blockIdx.x * C::SPC + sl;
+  if (slot >= (uint32_t)a.S) return;
+  // slots grouped by algorithm keep each SM on one loop body (instruction
+  // cache); the search index s, and with it every result, is unchanged
+  const uint32_t s = a.order ? (uint32_t)a.order[slot] : slot;
   const DevCtrl* ctrl = a.ctrl;
   if (ctrl->done) return;
   Searcher<C> sr(a, &smem[sl], threadIdx.x % C::NT, s, ctrl->g, ctrl->seed);
