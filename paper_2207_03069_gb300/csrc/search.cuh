@@ -65,7 +65,6 @@ struct SmemSearch {
   int4 red[2][C::NW];        // reduction slots (double buffered)
   int tot[C::CH][C::NW];     // per chunk, per warp candidate counts (k-th pick)
   int pick[4];               // broadcast of a pick made by one thread
-  int ring[C::NW][32];       // tabu list (one copy per warp: warp-synchronous updates)
 };
 
 #define DABS_CASES(X)                                                                      \
@@ -96,12 +95,13 @@ struct Searcher {
   const int16_t* W;     // W, and Wneg = -W: row i of sigma(x_i) W is read directly
   const int16_t* Wneg;
   int n, ld;
-  int ring_len, ring_head;  // tabu ring (uniform)
+  int ring_len, ring_head;  // tabu ring (uniform); entry j lives in lane j's ringv
+  int ringv;
 
   __device__ __forceinline__ Searcher(const SearchArgs& a, SmemSearch<C>* smem, int tid,
                                       uint32_t sidx, uint32_t gen, uint64_t sd)
       : sm(smem), t(tid), lane(tid & 31), warp(tid >> 5), buf(0), s(sidx), g(gen), seed(sd),
-        W(a.W), Wneg(a.Wneg), n(a.n), ld(a.ld), ring_len(0), ring_head(0) {}
+        W(a.W), Wneg(a.Wneg), n(a.n), ld(a.ld), ring_len(0), ring_head(0), ringv(0) {}
 
   // ------------------------------------------------------------ bit helpers
   __device__ __forceinline__ static bool bit_at(const uint32_t (&m)[NMW], int p) {
@@ -186,20 +186,6 @@ struct Searcher {
   }
 
   // ------------------------------------------------------------ per-thread scans
-  // lowest local position with d == v (inside M), -1 if none
-  __device__ __forceinline__ int tlow_eq(int v) const {
-    int lp = -1;
-#pragma unroll
-    for (int p = EPT - 1; p >= 0; --p) lp = d[p] == v ? p : lp;
-    return lp;
-  }
-  __device__ __forceinline__ int tlow_eq_mask(int v, uint32_t M) const {
-    int lp = -1;
-#pragma unroll
-    for (int p = EPT - 1; p >= 0; --p) lp = (((M >> p) & 1u) && d[p] == v) ? p : lp;
-    return lp;
-  }
-
   // ------------------------------------------------------------ Step 1 / Step 3
   // BEST <- f_j(X) for j = key >> 1 (Step 1 on strict improvement)
   __device__ __forceinline__ void take_best(uint32_t keyj, int m) {
@@ -342,50 +328,77 @@ struct Searcher {
   }
 
   // ------------------------------------------------------------ tabu
-  // bit i flipped at this iteration becomes tabu for the next tau iterations
+  // bit i flipped at this iteration becomes tabu for the next tau iterations;
+  // the ring of the last tau flips is spread over the lanes (entry j in lane j)
   __device__ __forceinline__ void tabu_push(int i, int tau) {
     if (tau <= 0) return;
-    int* ring = sm->ring[warp];
     if (ring_len == tau) {
-      const int old = ring[ring_head];
+      const int old = __shfl_sync(FULL, ringv, ring_head);
       if (t == owner_t(old)) tb[0] ^= 1u << local_p(old);
     } else {
       ++ring_len;
     }
-    __syncwarp();
-    if (lane == 0) ring[ring_head] = i;
-    __syncwarp();
+    if (lane == ring_head) ringv = i;
     ring_head = ring_head + 1 == tau ? 0 : ring_head + 1;
     if (t == owner_t(i)) tb[0] ^= 1u << local_p(i);
   }
 
-  // ------------------------------------------------------------ tree reductions
-  // balanced trees (depth log2 EPT) instead of serial chains: more ILP
-  __device__ __forceinline__ static int tree_min(int (&v)[EPT]) {
-#pragma unroll
-    for (int h = EPT / 2; h > 0; h >>= 1)
-#pragma unroll
-      for (int p = 0; p < h; ++p) v[p] = min(v[p], v[p + h]);
-    return v[0];
+  // ------------------------------------------------------------ chunk minima
+  // three-input min/max (DPX) trees: per 8-bit chunk, then across chunks
+  __device__ __forceinline__ static int min8(const int (&v)[8]) {
+    return __vimin3_s32(__vimin3_s32(v[0], v[1], v[2]), __vimin3_s32(v[3], v[4], v[5]),
+                        min(v[6], v[7]));
   }
-  __device__ __forceinline__ static int tree_max(int (&v)[EPT]) {
-#pragma unroll
-    for (int h = EPT / 2; h > 0; h >>= 1)
-#pragma unroll
-      for (int p = 0; p < h; ++p) v[p] = max(v[p], v[p + h]);
-    return v[0];
+  __device__ __forceinline__ static int max8(const int (&v)[8]) {
+    return __vimax3_s32(__vimax3_s32(v[0], v[1], v[2]), __vimax3_s32(v[3], v[4], v[5]),
+                        max(v[6], v[7]));
   }
-  __device__ __forceinline__ int min_all() const {
-    int v[EPT];
-#pragma unroll
-    for (int p = 0; p < EPT; ++p) v[p] = d[p];
-    return tree_min(v);
+  __device__ __forceinline__ static int min_of(const int (&cm)[CH]) {
+    if constexpr (CH == 1) return cm[0];
+    else if constexpr (CH == 2) return min(cm[0], cm[CH > 1 ? 1 : 0]);
+    else return min(min(cm[0], cm[CH > 1 ? 1 : 0]), min(cm[CH > 2 ? 2 : 0], cm[CH > 3 ? 3 : 0]));
   }
-  __device__ __forceinline__ int min_mask(uint32_t M) const {
-    int v[EPT];
+  // per-chunk minima of d over the bits of M (INT_MAX where none)
+  __device__ __forceinline__ void chunk_min(uint32_t M, int (&cm)[CH]) const {
 #pragma unroll
-    for (int p = 0; p < EPT; ++p) v[p] = ((M >> p) & 1u) ? d[p] : INT_MAX;
-    return tree_min(v);
+    for (int c = 0; c < CH; ++c) {
+      int v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = ((M >> (8 * c + e)) & 1u) ? d[8 * c + e] : INT_MAX;
+      cm[c] = min8(v);
+    }
+  }
+  __device__ __forceinline__ void chunk_min_all(int (&cm)[CH]) const {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      int v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = d[8 * c + e];
+      cm[c] = min8(v);
+    }
+  }
+  // key (k << 1 | x_k) of this warp's lowest bit k in M with d == target, found
+  // chunk by chunk with a ballot over the chunk minima (UINT_MAX if none)
+  __device__ __forceinline__ uint32_t warp_key(uint32_t M, const int (&cm)[CH], int target) const {
+    uint32_t key = UINT_MAX;
+    bool found = false;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      if (!found) {
+        const unsigned bal = __ballot_sync(FULL, cm[c] == target);
+        if (bal) {
+          found = true;
+          int e0 = 0;
+#pragma unroll
+          for (int e = 7; e >= 0; --e)
+            if (((M >> (8 * c + e)) & 1u) && d[8 * c + e] == target) e0 = e;
+          const int p = 8 * c + e0;
+          const uint32_t kk = ((uint32_t)kidx(p) << 1) | ((xb[0] >> p) & 1u);
+          key = __shfl_sync(FULL, kk, __ffs(bal) - 1);
+        }
+      }
+    }
+    return key;
   }
 
   // ------------------------------------------------------------ the batch search
@@ -409,13 +422,17 @@ struct Searcher {
     for (;;) {
       int i = 0, xi = 0, di = 0;
       uint32_t kj = UINT_MAX;
-      bool improve;
+      int cma[CH];
+      chunk_min_all(cma);  // Step 1: every one-bit neighbour
       int m;
+      bool improve;
       if (phase != PH_MAIN) {
         // ---------------- Straight / Greedy
         const bool st = phase == PH_STRAIGHT;
-        const uint32_t Msel = (xb[0] ^ db[0]) & vb[0];
-        int v[2] = {min_all(), st ? min_mask(Msel) : INT_MAX};
+        const uint32_t Ms = (xb[0] ^ db[0]) & vb[0];
+        int cms[CH];
+        if (st) chunk_min(Ms, cms);
+        int v[2] = {min_of(cma), st ? min_of(cms) : INT_MAX};
         gmin(v);
         m = v[0];
         if (st && v[1] == INT_MAX) {  // X == D: Straight ends
@@ -425,7 +442,7 @@ struct Searcher {
         improve = E + m < Ebest;
         if (!st && m >= 0) {  // local minimum: Greedy ends after Step 1
           if (improve) {
-            uint32_t k[1] = {key_of(tlow_eq(m))};
+            uint32_t k[1] = {warp_key(FULL, cma, m)};
             gminu(k);
             take_best(k[0], m);
           }
@@ -445,15 +462,14 @@ struct Searcher {
           break;
         }
         if (st) {
-          uint32_t k[2] = {improve ? key_of(tlow_eq(m)) : UINT_MAX,
-                           key_of(tlow_eq_mask(v[1], Msel))};
+          uint32_t k[2] = {improve ? warp_key(FULL, cma, m) : UINT_MAX, warp_key(Ms, cms, v[1])};
           gminu(k);
           kj = k[0];
           i = (int)(k[1] >> 1);
           xi = (int)(k[1] & 1u);
           di = v[1];
         } else {
-          uint32_t k[1] = {key_of(tlow_eq(m))};
+          uint32_t k[1] = {warp_key(FULL, cma, m)};
           gminu(k);
           kj = k[0];
           i = (int)(k[0] >> 1);
@@ -470,12 +486,12 @@ struct Searcher {
         if (rdn < 0) { --fdn; rdn += T; }
         const uint32_t F = vb[0] & ~tb[0];  // free (non-tabu) bits
         if (ALGO == TWONEIGHBOR) {
-          int v[1] = {min_all()};
+          int v[1] = {min_of(cma)};
           gmin(v);
           m = v[0];
           improve = E + m < Ebest;
           if (improve) {
-            uint32_t k[1] = {key_of(tlow_eq(m))};
+            uint32_t k[1] = {warp_key(FULL, cma, m)};
             gminu(k);
             kj = k[0];
           }
@@ -492,14 +508,20 @@ struct Searcher {
           const uint32_t u0 = __shfl_sync(FULL, rnd0, it & 31);
           uint32_t Cm = 0, ukth = 0;
           if (ALGO == MAXMIN) {
-            int vmin[EPT], vmax[EPT];
+            int cmn[CH], cmx[CH];
 #pragma unroll
-            for (int p = 0; p < EPT; ++p) {
-              const bool f = (F >> p) & 1u;
-              vmin[p] = f ? d[p] : INT_MAX;
-              vmax[p] = f ? d[p] : INT_MIN;
+            for (int c = 0; c < CH; ++c) {
+              int vn[8], vx[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const bool f = (F >> (8 * c + e)) & 1u;
+                vn[e] = f ? d[8 * c + e] : INT_MAX;
+                vx[e] = f ? d[8 * c + e] : INT_MIN;
+              }
+              cmn[c] = min8(vn);
+              cmx[c] = ~max8(vx);
             }
-            int v[3] = {min_all(), tree_min(vmin), ~tree_max(vmax)};
+            int v[3] = {min_of(cma), min_of(cmn), min_of(cmx)};
             gmin(v);
             m = v[0];
             const int mn = v[1], mx = ~v[2];
@@ -513,10 +535,16 @@ struct Searcher {
             Cm &= F;
             ukth = __shfl_sync(FULL, rnd1, it & 31);
           } else {
-            int vpos[EPT];
+            int cmp[CH];
 #pragma unroll
-            for (int p = 0; p < EPT; ++p) vpos[p] = (((F >> p) & 1u) && d[p] > 0) ? d[p] : INT_MAX;
-            int v[2] = {min_all(), tree_min(vpos)};
+            for (int c = 0; c < CH; ++c) {
+              int vp[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e)
+                vp[e] = (((F >> (8 * c + e)) & 1u) && d[8 * c + e] > 0) ? d[8 * c + e] : INT_MAX;
+              cmp[c] = min8(vp);
+            }
+            int v[2] = {min_of(cma), min_of(cmp)};
             gmin(v);
             m = v[0];
             const int pm = v[1];
@@ -531,7 +559,7 @@ struct Searcher {
           }
           improve = E + m < Ebest;
           if (improve) {
-            uint32_t k[1] = {key_of(tlow_eq(m))};
+            uint32_t k[1] = {warp_key(FULL, cma, m)};
             gminu(k);
             kj = k[0];
           }
@@ -552,15 +580,18 @@ struct Searcher {
           }
           M1 &= F;
           M2 &= F;
-          int v[2] = {min_all(), min_mask(M1 | M2)};
+          int cm1[CH], cm2[CH];
+          chunk_min(M1, cm1);
+          chunk_min(M2, cm2);
+          int v[2] = {min_of(cma), min(min_of(cm1), min_of(cm2))};
           gmin(v);
           m = v[0];
           improve = E + m < Ebest;
           // first in cyclic order from ws: [ws, n) before [0, ws + wsz - n)
-          const int l1 = tlow_eq_mask(v[1], M1), l2 = tlow_eq_mask(v[1], M2);
-          const uint32_t r1 = l1 < 0 ? UINT_MAX : ((uint32_t)(kidx(l1) - ws) << 1) | (uint32_t)bit_at(xb, l1);
-          const uint32_t r2 = l2 < 0 ? UINT_MAX : ((uint32_t)(kidx(l2) + n - ws) << 1) | (uint32_t)bit_at(xb, l2);
-          uint32_t k[2] = {improve ? key_of(tlow_eq(m)) : UINT_MAX, min(r1, r2)};
+          const uint32_t k1 = warp_key(M1, cm1, v[1]), k2 = warp_key(M2, cm2, v[1]);
+          const uint32_t r1 = k1 == UINT_MAX ? UINT_MAX : k1 - ((uint32_t)ws << 1);
+          const uint32_t r2 = k2 == UINT_MAX ? UINT_MAX : k2 + ((uint32_t)(n - ws) << 1);
+          uint32_t k[2] = {improve ? warp_key(FULL, cma, m) : UINT_MAX, min(r1, r2)};
           gminu(k);
           kj = k[0];
           const int sb = ws + (int)(k[1] >> 1);
@@ -583,14 +614,17 @@ struct Searcher {
             }
           }
           Cm &= F;
-          int v[3] = {min_all(), min_mask(Cm), min_mask(F)};
+          int cmc[CH], cmf[CH];
+          chunk_min(Cm, cmc);
+          chunk_min(F, cmf);
+          int v[3] = {min_of(cma), min_of(cmc), min_of(cmf)};
           gmin(v);
           m = v[0];
           improve = E + m < Ebest;
           const bool have = v[1] != INT_MAX;  // no candidate: argmin over free bits
           di = have ? v[1] : v[2];
-          uint32_t k[2] = {improve ? key_of(tlow_eq(m)) : UINT_MAX,
-                           key_of(tlow_eq_mask(di, have ? Cm : F))};
+          uint32_t k[2] = {improve ? warp_key(FULL, cma, m) : UINT_MAX,
+                           have ? warp_key(Cm, cmc, di) : warp_key(F, cmf, di)};
           gminu(k);
           kj = k[0];
           i = (int)(k[1] >> 1);
