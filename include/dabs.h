@@ -139,6 +139,33 @@ int dabs_bulk_search_dev(dabs_ctx* ctx, uint64_t seed, uint32_t g, int32_t count
                          int32_t* delta, int64_t* E, const uint32_t* D, const uint8_t* algo,
                          uint32_t* best_X, int64_t* best_E, uint32_t* flips);
 
+/* ---- the batch search without device allocation -------------------------
+ * No counterpart in the paper: an engineering entry point.  It runs the same
+ * batch search as dabs_bulk_search_dev (identical results) for callers that
+ * cannot allocate device memory -- e.g. code whose device memory is owned by
+ * another allocator (a framework's caching allocator or a fixed arena) that
+ * must not see cudaMalloc/cudaFree, which may synchronise the device and
+ * fragment the arena.  No context is needed and nothing is allocated: the
+ * negated weight copy, the slot launch order and the control block live in
+ * one file-scope device array of 2 MiB + 64 KiB + 256 B that every GPU which
+ * loads the library keeps until the process exits.
+ *   W      device, n x ld int16 row-major, 16-byte aligned, ld a multiple of
+ *          8, columns >= n zero, entries in [-32767, 32767]
+ *   p      tabu, s_num/s_den, b_num/b_den and seed_mode are used
+ *   X, delta (count x ld int32, 16-byte aligned), E, D, algo, best_X, best_E,
+ *   flips  as in dabs_bulk_search_dev (device buffers of the caller)
+ *   stream the cudaStream_t to enqueue on (NULL = default stream)
+ * Limits: n * ld <= 1048576 and count <= 16384, else DABS_E_TOO_LARGE.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (each call rewrites the parts it reads), so calls whose GPU work overlaps
+ * race: order them on one stream.  Asynchronous.                            */
+int dabs_bulk_search_noalloc(const int16_t* W, int32_t n, int32_t ld, const dabs_params* p,
+                             uint64_t seed, uint32_t g, int32_t count, uint32_t* X,
+                             int32_t* delta, int64_t* E, const uint32_t* D, const uint8_t* algo,
+                             uint32_t* best_X, int64_t* best_E, uint32_t* flips, void* stream);
+
 /* ---- inspection (host copies; synchronous) ------------------------------ */
 /* n, padded row length ld, packed words per vector, S, P, C, and the
  * kernel variant (warps per search, 8-bit chunks per thread). */

@@ -68,6 +68,8 @@ EXPORTS = {
     "dabs_read_generation": (C.c_int, [C.c_void_p] * 7),
     "dabs_write_results": (C.c_int, [C.c_void_p] * 6),
     "dabs_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
+    "dabs_bulk_search_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                           C.c_uint64, C.c_uint32, C.c_int32] + [C.c_void_p] * 9),
 }
 
 
@@ -115,6 +117,18 @@ def default_params(**kw) -> Params:
         else:
             setattr(p, k, v)
     return p
+
+
+def bulk_search_noalloc(W, n, ld, params, seed, g, X, delta, E, D, algo, best_X, best_E, flips,
+                        stream=None):
+    """dabs_bulk_search_noalloc on caller tensors (W: device int16 [n][ld])."""
+    handle = None if stream is None else getattr(stream, "cuda_stream", stream)
+    rc = lib().dabs_bulk_search_noalloc(
+        _ptr(W), n, ld, C.byref(params), seed, g, X.shape[0], _ptr(X), _ptr(delta), _ptr(E),
+        _ptr(D), _ptr(algo), _ptr(best_X), _ptr(best_E), _ptr(flips),
+        C.c_void_p(handle) if handle else None)
+    if rc != OK:
+        raise DabsError(rc)
 
 
 class Context:
