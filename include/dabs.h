@@ -105,6 +105,20 @@ int dabs_delta(dabs_ctx* ctx, const uint8_t* X, int32_t* delta);
 int dabs_energy_delta_dev(dabs_ctx* ctx, const uint32_t* X, int32_t count, int64_t* E,
                           int32_t* delta, int32_t ld_delta);
 
+/* Eq. (2)/(3) for `count` packed device vectors on the tensor cores
+ * (tcgen05 MMA on bf16 limbs: W = 256 hi + lo, 8-bit limbs, fp32 accumulation
+ * exact for n <= 65,793), same outputs as dabs_energy_delta_dev.  count must
+ * not exceed the context's searches rounded up to 128.  Asynchronous; a
+ * bounded device wait that ran out is reported by dabs_kernel_status. */
+int dabs_recompute_dev(dabs_ctx* ctx, const uint32_t* X, int32_t count, int64_t* E,
+                       int32_t* delta, int32_t ld_delta);
+/* Recompute seeding (seed_mode = 1) on 0 = CUDA cores, 1 = tensor cores (the
+ * default for contexts created with seed_mode = 1). */
+int dabs_set_recompute(dabs_ctx* ctx, int32_t mode);
+/* Waits for the context's stream; DABS_E_TIMEOUT if a kernel's bounded wait
+ * ran out since the last call (the flag is then cleared). */
+int dabs_kernel_status(dabs_ctx* ctx);
+
 /* Whole solve (Sections III and IV): pools initialised with random vectors,
  * every search starting at X = 0; generations of (offspring, batch search,
  * pool merge) until, at a generation boundary, the total number of flips

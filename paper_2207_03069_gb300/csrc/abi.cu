@@ -5,6 +5,7 @@
 // ABI; every CUDA error becomes a DABS_E_* code with a message in the context.
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -12,6 +13,7 @@
 
 #include "dabs.h"
 #include "kernels.cuh"
+#include "umma.cuh"
 
 using namespace dabs;
 
@@ -49,6 +51,16 @@ struct dabs_ctx {
   int32_t* one_d = nullptr;
   int64_t* one_E = nullptr;
   SearchVariant var{};
+  // tensor-core recompute (tcgen05): W limbs, bf16 copy of the vectors, maps
+  int recompute_mode = 0;     // 0 = CUDA cores, 1 = tensor cores
+  bool tc_ready = false;
+  int n_pad = 0, rows_pad = 0;
+  uint16_t* Whi = nullptr;
+  uint16_t* Wlo = nullptr;
+  uint16_t* Abf = nullptr;
+  int64_t* E2 = nullptr;
+  int* kerr = nullptr;
+  CUtensorMap mapA{}, mapHi{}, mapLo{};
   std::vector<void*> allocs;
   std::string err;
 };
@@ -106,6 +118,8 @@ bool default_variant(int n, SearchVariant* v) {
   return false;
 }
 
+int tc_limbs(dabs_ctx* ctx);
+
 int upload_weights(dabs_ctx* ctx, const int16_t* W) {
   const int n = ctx->n, ld = ctx->ld;
   for (int i = 0; i < n; ++i)
@@ -128,6 +142,57 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
   CK(cudaMemcpy(ctx->W, pad.data(), pad.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->Wneg, neg.data(), neg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->diag, dg.data(), dg.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (ctx->tc_ready) return tc_limbs(ctx);
+  return DABS_OK;
+}
+
+int tc_limbs(dabs_ctx* ctx) {
+  const size_t total = (size_t)ctx->n_pad * ctx->n_pad;
+  k_limbs<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+      ctx->W, ctx->n, ctx->ld, ctx->n_pad, ctx->Whi, ctx->Wlo);
+  CKLAUNCH();
+  return DABS_OK;
+}
+
+// allocates the tensor-core recompute buffers and builds the TMA maps (once)
+int tc_setup(dabs_ctx* ctx) {
+  if (ctx->tc_ready) return DABS_OK;
+  const int bm = umma_tile_m(), bn = umma_tile_n();
+  ctx->n_pad = (ctx->n + bn - 1) / bn * bn;
+  ctx->rows_pad = (std::max(ctx->S, 1) + bm - 1) / bm * bm;
+  int rc;
+  if ((rc = dalloc(ctx, &ctx->Whi, (size_t)ctx->n_pad * ctx->n_pad)) != DABS_OK) return rc;
+  if ((rc = dalloc(ctx, &ctx->Wlo, (size_t)ctx->n_pad * ctx->n_pad)) != DABS_OK) return rc;
+  if ((rc = dalloc(ctx, &ctx->Abf, (size_t)ctx->rows_pad * ctx->n_pad)) != DABS_OK) return rc;
+  if ((rc = dalloc(ctx, &ctx->E2, (size_t)ctx->rows_pad)) != DABS_OK) return rc;
+  if ((rc = dalloc(ctx, &ctx->kerr, 1)) != DABS_OK) return rc;
+  CK(cudaMemsetAsync(ctx->kerr, 0, sizeof(int), ctx->stream));
+  if (!make_tmap_bf16(&ctx->mapA, ctx->Abf, ctx->rows_pad, ctx->n_pad) ||
+      !make_tmap_bf16(&ctx->mapHi, ctx->Whi, ctx->n_pad, ctx->n_pad) ||
+      !make_tmap_bf16(&ctx->mapLo, ctx->Wlo, ctx->n_pad, ctx->n_pad))
+    return fail(ctx, DABS_E_CUDA, "cuTensorMapEncodeTiled failed");
+  CK(cudaFuncSetAttribute(k_recompute_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)umma_smem_bytes()));
+  if ((rc = tc_limbs(ctx)) != DABS_OK) return rc;
+  ctx->tc_ready = true;
+  return DABS_OK;
+}
+
+// Eq. (2)/(3) for `count` packed vectors on the tensor cores
+int tc_recompute(dabs_ctx* ctx, const uint32_t* X, int count, int64_t* E, int32_t* delta,
+                 int ld_delta, const DevCtrl* ctrl) {
+  cudaStream_t st = ctx->stream;
+  const size_t pairs = (size_t)ctx->rows_pad * (ctx->n_pad / 2);
+  k_bits_to_bf16<<<(unsigned)std::min<size_t>((pairs + 255) / 256, 4096), 256, 0, st>>>(
+      X, count, ctx->n, ctx->nw, ctx->rows_pad, ctx->n_pad, ctx->Abf, ctrl);
+  CKLAUNCH();
+  CK(cudaMemsetAsync(ctx->E2, 0, sizeof(int64_t) * ctx->rows_pad, st));
+  UmmaArgs u{count, ctx->n, ctx->n_pad, ctx->nw, ld_delta, X, ctx->diag, delta, ctx->E2, ctx->kerr, ctrl};
+  const dim3 grid(ctx->n_pad / umma_tile_n(), (count + umma_tile_m() - 1) / umma_tile_m());
+  k_recompute_umma<<<grid, 128, umma_smem_bytes(), st>>>(ctx->mapA, ctx->mapHi, ctx->mapLo, u);
+  CKLAUNCH();
+  k_halve<<<(count + 255) / 256, 256, 0, st>>>(E, ctx->E2, count, ctrl);
+  CKLAUNCH();
   return DABS_OK;
 }
 
@@ -157,9 +222,14 @@ int stage(dabs_ctx* ctx, int which) {
       const size_t words = (size_t)ctx->S * ctx->nw;
       k_copy_targets<<<148, 256, 0, st>>>(ctx->D, ctx->X, ctx->E, words, ctx->S, ctx->ctrl);
       CKLAUNCH();
-      EDArgs e{ctx->W, ctx->n, ctx->ld, ctx->nw, ctx->X, ctx->delta, ctx->ld, ctx->E, ctx->ctrl};
-      k_energy_delta<<<dim3((ctx->n + 255) / 256, ctx->S), 256, 0, st>>>(e);
-      CKLAUNCH();
+      if (ctx->recompute_mode == 1) {
+        const int rc = tc_recompute(ctx, ctx->D, ctx->S, ctx->E, ctx->delta, ctx->ld, ctx->ctrl);
+        if (rc) return rc;
+      } else {
+        EDArgs e{ctx->W, ctx->n, ctx->ld, ctx->nw, ctx->X, ctx->delta, ctx->ld, ctx->E, ctx->ctrl};
+        k_energy_delta<<<dim3((ctx->n + 255) / 256, ctx->S), 256, 0, st>>>(e);
+        CKLAUNCH();
+      }
     }
   } else if (which == 1) {
     k_order_by_algo<<<1, 1024, 0, st>>>(ctx->algo, ctx->S, ctx->order, ctx->ctrl);
@@ -319,6 +389,10 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
     }
   }
   TRY(upload_weights(ctx, W));
+  if (p->seed_mode == 1) {  // recompute seeding runs on the tensor cores by default
+    TRY(tc_setup(ctx));
+    ctx->recompute_mode = 1;
+  }
   // a fresh context is a solve with seed 0 that has not run yet
   TRY(dabs_solve_begin(ctx, 0, UINT64_MAX, INT64_MIN));
   TRY(cudaStreamSynchronize(ctx->stream) == cudaSuccess ? DABS_OK : DABS_E_CUDA);
@@ -568,6 +642,40 @@ int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* c
   if (chunks) *chunks = best.ch;
   if (ns_per_flip) *ns_per_flip = best_ns;
   return dabs_solve_begin(ctx, 0, UINT64_MAX, INT64_MIN);
+}
+
+int dabs_set_recompute(dabs_ctx* ctx, int32_t mode) {
+  if (!ctx || (mode != 0 && mode != 1)) return DABS_E_INVALID_ARG;
+  if (mode == 1) {
+    const int rc = tc_setup(ctx);
+    if (rc) return rc;
+  }
+  ctx->recompute_mode = mode;
+  return DABS_OK;
+}
+
+int dabs_recompute_dev(dabs_ctx* ctx, const uint32_t* X, int32_t count, int64_t* E,
+                       int32_t* delta, int32_t ld_delta) {
+  if (!ctx || !X || !E || count < 0 || (delta && ld_delta < ctx->n)) return DABS_E_INVALID_ARG;
+  int rc = tc_setup(ctx);
+  if (rc) return rc;
+  if (count > ctx->rows_pad)
+    return fail(ctx, DABS_E_TOO_LARGE, "count %d > %d rows of the recompute buffer", count, ctx->rows_pad);
+  if (count == 0) return DABS_OK;
+  return tc_recompute(ctx, X, count, E, delta, ld_delta, nullptr);
+}
+
+int dabs_kernel_status(dabs_ctx* ctx) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (!ctx->kerr) return DABS_OK;
+  int e = 0;
+  CK(cudaMemcpy(&e, ctx->kerr, sizeof e, cudaMemcpyDeviceToHost));
+  if (e) {
+    CK(cudaMemset(ctx->kerr, 0, sizeof(int)));
+    return fail(ctx, DABS_E_TIMEOUT, "a device wait ran out (kernel error %d)", e);
+  }
+  return DABS_OK;
 }
 
 static int cur_buf(dabs_ctx* ctx, int* b) {

@@ -1,0 +1,312 @@
+// umma.cu -- from-scratch Delta and energy of a batch of vectors on the
+// tensor cores (5th-generation, tcgen05): F = D * W for D in {0,1}^{S x n},
+// then Eq. (3) Delta_k = -sigma(d_k) F_k + W_kk (1 - d_k) and Eq. (2)
+// E = (sum_k d_k F_k + sum_k d_k W_kk) / 2.
+//
+// Exactness: W (int16 in [-32767, 32767]) is split into two 8-bit limbs,
+// W = 256 * hi + lo with lo in [0, 255] and hi in [-128, 127]; both limbs and
+// the 0/1 entries of D are exact in bf16, every product is an integer, and the
+// fp32 accumulator stays exact while |partial sum| < 2^24, i.e. for
+// n <= 65,793 (n * 255 < 2^24).  F = 256 * F_hi + F_lo is then exact in int32.
+//
+// Kernel: one CTA per 128 x 128 output tile, 4 warps.  Thread 0 streams
+// K-blocks of 64 (128 bytes) of D and of both limbs into a 4-stage
+// shared-memory ring with TMA (128-byte swizzle) and issues
+// tcgen05.mma.kind::f16 (M = 128, N = 128, K = 16) into two fp32 TMEM
+// accumulators (hi, lo); each stage is released by tcgen05.commit.  All four
+// warps then read their 32 TMEM lanes (rows) with tcgen05.ld and write Delta
+// and the energy partial sums.  Every mbarrier wait is bounded; on expiry the
+// kernel records an error code and returns after releasing its TMEM.
+#include <cuda.h>
+
+#include "kernels.cuh"
+#include "umma.cuh"
+
+namespace dabs {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr uint32_t TILE_BYTES = BM * BK * 2;           // 16 KiB per operand tile
+constexpr uint32_t STAGE_BYTES = 3 * TILE_BYTES;       // D, W_hi, W_lo
+constexpr uint32_t TMEM_COLS = 256;                    // hi: [0,128), lo: [128,256)
+constexpr uint64_t WAIT_NS = 2000000000ull;            // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase of the given parity; false on timeout or abort
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_test(bar, parity)) return true;
+    if (*abort) return false;
+    if ((it & 63) == 63) {
+      if (global_ns() - t0 > WAIT_NS) return false;
+      __nanosleep(128);
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// of 1024 bytes (stride byte offset), descriptor version 1
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // version
+  d |= (uint64_t)2 << 61;              // 128-byte swizzle
+  return d;
+}
+// instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+}  // namespace
+
+// D bits [count][nw] -> bf16 0/1 matrix [rows_pad][n_pad] (zero padding)
+__global__ void k_bits_to_bf16(const uint32_t* D, int count, int n, int nw, int rows_pad,
+                               int n_pad, uint16_t* A, const DevCtrl* ctrl) {
+  if (ctrl && ctrl->done) return;
+  const size_t total = (size_t)rows_pad * (n_pad / 2);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(q / (n_pad / 2)), k = 2 * (int)(q % (n_pad / 2));
+    uint32_t v = 0;
+    if (r < count && k < n) {
+      const uint32_t w = D[(size_t)r * nw + (k >> 5)];
+      const uint32_t b0 = (w >> (k & 31)) & 1u, b1 = (k + 1 < n) ? ((w >> ((k + 1) & 31)) & 1u) : 0u;
+      v = (b0 ? 0x3F80u : 0u) | ((b1 ? 0x3F80u : 0u) << 16);  // bf16 1.0 = 0x3F80
+    }
+    reinterpret_cast<uint32_t*>(A)[q] = v;
+  }
+}
+
+// W [n][ld] int16 -> limbs hi = W >> 8 (arithmetic), lo = W & 255 as bf16 [n_pad][n_pad]
+__global__ void k_limbs(const int16_t* W, int n, int ld, int n_pad, uint16_t* Whi, uint16_t* Wlo) {
+  const size_t total = (size_t)n_pad * n_pad;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(q / n_pad), c = (int)(q % n_pad);
+    const int w = (r < n && c < n) ? (int)W[(size_t)r * ld + c] : 0;
+    // |limb| <= 255 needs at most 8 significant bits, so the upper half of the
+    // fp32 encoding is the exact bf16 encoding
+    Whi[q] = (uint16_t)(__float_as_uint((float)(w >> 8)) >> 16);
+    Wlo[q] = (uint16_t)(__float_as_uint((float)(w & 255)) >> 16);
+  }
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_recompute_umma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapHi,
+                     const __grid_constant__ CUtensorMap mapLo, const UmmaArgs a) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  if (a.ctrl && a.ctrl->done) return;
+  // 1024-byte aligned operand ring
+  const uint32_t base = (smem_u32(smraw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int KB = a.n_pad / BK;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tm = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // producer (TMA) and MMA issue in one thread, STAGES-1 blocks ahead
+    for (int kb = 0; kb < KB + STAGES - 1 && !abort_flag; ++kb) {
+      if (kb < KB) {
+        const int st = kb % STAGES;
+        if (kb >= STAGES && !mbar_wait(&empty[st], (uint32_t)((kb / STAGES) - 1) & 1u, &abort_flag)) {
+          abort_flag = 1;
+          break;
+        }
+        const uint32_t s0 = base + st * STAGE_BYTES;
+        mbar_expect_tx(&full[st], STAGE_BYTES);
+        tma_load_2d(s0, &mapA, kb * BK, m0, &full[st]);
+        tma_load_2d(s0 + TILE_BYTES, &mapHi, kb * BK, n0, &full[st]);
+        tma_load_2d(s0 + 2 * TILE_BYTES, &mapLo, kb * BK, n0, &full[st]);
+      }
+      const int kc = kb - (STAGES - 1);
+      if (kc >= 0) {
+        const int st = kc % STAGES;
+        if (!mbar_wait(&full[st], (uint32_t)(kc / STAGES) & 1u, &abort_flag)) {
+          abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t s0 = base + st * STAGE_BYTES;
+        const uint64_t da = sdesc(s0), dh = sdesc(s0 + TILE_BYTES), dl = sdesc(s0 + 2 * TILE_BYTES);
+#pragma unroll
+        for (int ks = 0; ks < BK / 16; ++ks) {
+          const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+          // +32 bytes per K step of 16 bf16 inside the 128-byte swizzled row
+          mma_bf16(tm, da + 2 * ks, dh + 2 * ks, acc);
+          mma_bf16(tm + BN, da + 2 * ks, dl + 2 * ks, acc);
+        }
+        mma_commit(&empty[st]);
+      }
+    }
+    if (!abort_flag) mma_commit(&done);
+  }
+  __syncwarp();
+  // everyone waits for the accumulators (bounded)
+  bool ok = true;
+  if (!mbar_wait(&done, 0, &abort_flag)) ok = false;
+  __syncwarp();
+  if (!ok || abort_flag) {
+    if (a.err) atomicExch(a.err, DABS_KERNEL_TIMEOUT);
+    abort_flag = 1;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (!abort_flag) {
+    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
+    const int row = m0 + 32 * warp + lane;
+    const bool row_ok = row < a.count;
+    const uint32_t* drow = a.D + (size_t)(row_ok ? row : 0) * a.nw;
+    int64_t epart = 0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t rh[32], rl[32];
+      const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+      tmem_ld32(tm + lane_off + (uint32_t)c0, rh);
+      tmem_ld32(tm + lane_off + (uint32_t)(BN + c0), rl);
+      const int kbase = n0 + c0;
+      if (row_ok && kbase < a.n) {
+        const uint32_t dword = drow[kbase >> 5];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int k = kbase + j;
+          if (k < a.n) {
+            const int F = 256 * __float2int_rn(__uint_as_float(rh[j])) + __float2int_rn(__uint_as_float(rl[j]));
+            const int wkk = a.diag[k];
+            const bool dk = (dword >> j) & 1u;
+            if (a.delta) a.delta[(size_t)row * a.ld_delta + k] = dk ? -F : F + wkk;  // Eq. (3)
+            if (dk) epart += (int64_t)F + wkk;
+          }
+        }
+      }
+    }
+    if (row_ok && a.E2) atomicAdd(reinterpret_cast<unsigned long long*>(a.E2 + row), (unsigned long long)epart);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(TMEM_COLS) : "memory");
+}
+
+// E = E2 / 2 (E2 holds sum_k d_k (F_k + W_kk), always even)
+__global__ void k_halve(int64_t* E, const int64_t* E2, int count, const DevCtrl* ctrl) {
+  if (ctrl && ctrl->done) return;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x)
+    E[q] = E2[q] / 2;
+}
+
+size_t umma_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + 1024; }
+int umma_tile_m() { return BM; }
+int umma_tile_n() { return BN; }
+int umma_tile_k() { return BK; }
+
+}  // namespace dabs
+
+namespace dabs {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool make_tmap_bf16(CUtensorMap* map, void* ptr, uint64_t rows, uint64_t cols) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return false;
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)umma_tile_k(), (cuuint32_t)umma_tile_m()};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace dabs

@@ -1,0 +1,39 @@
+// umma.cuh -- tensor-core (tcgen05) batched Delta/energy recompute: kernel
+// arguments, launch helpers and the TMA tensor-map builder.
+#pragma once
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace dabs {
+
+constexpr int DABS_KERNEL_TIMEOUT = 1;  // error code a kernel writes when a bounded wait expires
+
+struct UmmaArgs {
+  int count;              // vectors (rows of D)
+  int n, n_pad, nw;       // problem size, padded size (multiple of 128), words per vector
+  int ld_delta;           // row stride of delta
+  const uint32_t* D;      // [count][nw] packed vectors
+  const int32_t* diag;    // W_kk
+  int32_t* delta;         // [count][ld_delta] or null
+  int64_t* E2;            // [count] receives 2 E (zeroed before the launch) or null
+  int* err;               // kernel error flag (0 = ok)
+  const DevCtrl* ctrl;    // optional: skip when a solve has stopped
+};
+
+__global__ void k_bits_to_bf16(const uint32_t* D, int count, int n, int nw, int rows_pad,
+                               int n_pad, uint16_t* A, const DevCtrl* ctrl);
+__global__ void k_limbs(const int16_t* W, int n, int ld, int n_pad, uint16_t* Whi, uint16_t* Wlo);
+__global__ void k_recompute_umma(const __grid_constant__ CUtensorMap mapA,
+                                 const __grid_constant__ CUtensorMap mapHi,
+                                 const __grid_constant__ CUtensorMap mapLo, const UmmaArgs a);
+__global__ void k_halve(int64_t* E, const int64_t* E2, int count, const DevCtrl* ctrl);
+
+size_t umma_smem_bytes();
+int umma_tile_m();
+int umma_tile_n();
+int umma_tile_k();
+// 2-D bf16 tensor map (rows x cols, row-major) with a 64 x 128 box and 128-byte swizzle
+bool make_tmap_bf16(CUtensorMap* map, void* ptr, uint64_t rows, uint64_t cols);
+
+}  // namespace dabs

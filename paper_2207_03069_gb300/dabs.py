@@ -68,6 +68,10 @@ EXPORTS = {
     "dabs_read_generation": (C.c_int, [C.c_void_p] * 7),
     "dabs_write_results": (C.c_int, [C.c_void_p] * 6),
     "dabs_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
+    "dabs_recompute_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                     C.c_int32]),
+    "dabs_set_recompute": (C.c_int, [C.c_void_p, C.c_int32]),
+    "dabs_kernel_status": (C.c_int, [C.c_void_p]),
     "dabs_bulk_search_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                            C.c_uint64, C.c_uint32, C.c_int32] + [C.c_void_p] * 9),
 }
@@ -213,6 +217,18 @@ class Context:
         count = X.shape[0]
         ldd = ld_delta if ld_delta is not None else (delta.shape[-1] if delta is not None else 0)
         self._ck(lib().dabs_energy_delta_dev(self._h, _ptr(X), count, _ptr(E), _ptr(delta), ldd))
+
+    def recompute_dev(self, X, E, delta=None, ld_delta: int | None = None):
+        """Tensor-core Eq. (2)/(3) of X (device, packed) into E (and delta)."""
+        count = X.shape[0]
+        ldd = ld_delta if ld_delta is not None else (delta.shape[-1] if delta is not None else 0)
+        self._ck(lib().dabs_recompute_dev(self._h, _ptr(X), count, _ptr(E), _ptr(delta), ldd))
+
+    def set_recompute(self, mode: int):
+        self._ck(lib().dabs_set_recompute(self._h, mode))
+
+    def kernel_status(self):
+        self._ck(lib().dabs_kernel_status(self._h))
 
     # ---------------------------------------------------------------- solve
     def solve(self, budget: int, seed: int, target: int | None = None):
