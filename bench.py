@@ -150,6 +150,35 @@ def l2_copy_gbs(torch, dev):
     return 2 * a.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
 
 
+def recompute_rate(torch, dabs, dev, n=4096, count=256, reps=20):
+    """Tensor-core recompute of Delta/E (tcgen05, bf16 limbs) for `count`
+    vectors of a dense n x n instance: the batched-seeding step of the batched
+    workload.  Returns timing and the tensor FLOP rate (2 limbs x 2 S n^2)."""
+    W = wl.dense_qubo(n, -1000, 1000, seed=3)
+    ctx = dabs.Context(W, searches=count, pools=1, pool_cap=1)
+    rng = np.random.default_rng(3)
+    X = torch.from_numpy(wl.pack_bits((rng.random((count, n)) < 0.5).astype(np.uint8))
+                         .view(np.int32)).to(dev)
+    E = torch.zeros(count, dtype=torch.int64, device=dev)
+    dl = torch.zeros((count, ctx.ld), dtype=torch.int32, device=dev)
+    st = torch.cuda.Stream(device=dev)
+    ctx.set_stream(st)
+    for _ in range(3):
+        ctx.recompute_dev(X, E, dl)
+    ctx.kernel_status()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(st)
+    for _ in range(reps):
+        ctx.recompute_dev(X, E, dl)
+    ev[1].record(st)
+    ctx.kernel_status()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    flops = 4.0 * count * n * n
+    ctx.close()
+    return {"n": n, "vectors": count, "ms": ms, "tensor_tflops": flops / (ms * 1e-3) / 1e12,
+            "note": "bf16 limbs on tcgen05.mma kind::f16, exact; includes bit->bf16 expansion"}
+
+
 def oracle_rate(Wm, spec, seed, seconds, threads):
     """Oracle (plain C, as it stands) on the same workload: whole generations on
     `threads` host threads until `seconds` have passed.  Returns (flips/s, gens)."""
@@ -223,6 +252,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-recompute", action="store_true")
     ap.add_argument("--variant", default="", help="force warps x chunks, e.g. 4x1")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -328,6 +358,13 @@ def main():
            "d2h_bytes_per_step": n + 8,
            "call": "dabs_load_weights + dabs_solve(budget=1 generation) per step"}
 
+    rec = recompute_rate(torch, dabs, dev) if not args.no_recompute else None
+    if rec:
+        mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        pk = json.load(open(mp))["bf16_tflops"] if os.path.exists(mp) else 1900.0
+        rec["peak_tflops"] = pk
+        rec["frac"] = rec["tensor_tflops"] / pk
+
     # ---------------- CPU baseline: the oracle as it stands, bounded sample
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -352,7 +389,8 @@ def main():
                            "l2": "flushed (256 MiB write) between timed steps",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "delta_updates_per_s": value * n, "autotune": sweep, "gpu_launches": 5 * args.steps,
-                "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
+                "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+                "recompute_tensor": rec}
         print(json.dumps(line), flush=True)
     ctx.close()
     if pg:
