@@ -332,10 +332,13 @@ def main():
     launch_s = sum(search_ms) * 1e-3 / args.steps
     achieved = algo_bytes / launch_s / 1e9
     prof = search_profile()
+    info = ctx.info()
+    vkey = "%dx%d" % (info["warps"], info["chunks"])
+    traffic = prof["dram_bytes_per_launch"].get(vkey) if prof else None
     l2 = l2_copy_gbs(torch, dev)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_kind": f"{peak_kind} HBM copy",
-                "traffic": prof["dram_bytes_per_launch"] if prof else None,
+                "traffic": traffic, "traffic_source": "profiles/search_maxcut800.json" if traffic else None,
                 "kernel": "k_batch_search", "algorithmic_bytes_per_launch": algo_bytes,
                 "launch_ms": launch_s * 1e3, "search_share_of_step": sum(search_ms) / sum(step_ms),
                 "l2_copy_gbs_measured": l2, "frac_of_l2_copy": achieved / l2}
