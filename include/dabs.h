@@ -129,6 +129,42 @@ int dabs_kernel_status(dabs_ctx* ctx);
 int dabs_solve(dabs_ctx* ctx, uint64_t budget, uint64_t seed, int64_t target, uint8_t* best_X,
                int64_t* best_E, uint64_t* flips);
 
+/* ---- batched form: many instances per launch ---------------------------
+ * Solves the k contexts together (Sections III and IV per instance): every
+ * generation runs each instance's offspring, recompute, merge and finalise
+ * kernels and one batch-search launch per kernel variant covering all the
+ * instances of that variant, on one stream.  Each instance stops on its own
+ * budget/target/generation limit; instance i's results (best_X[i], n_i host
+ * bytes; best_E[i]; flips[i]) equal dabs_solve(ctxs[i], budgets[i], seeds[i],
+ * targets[i]) alone.  targets, best_X, best_E, flips may be NULL.
+ * Synchronous. */
+int dabs_batch_solve(dabs_ctx* const* ctxs, int32_t k, const uint64_t* budgets,
+                     const uint64_t* seeds, const int64_t* targets, uint8_t* const* best_X,
+                     int64_t* best_E, uint64_t* flips);
+
+/* ---- served form: request queue with continuous batching ----------------
+ * A server owns a queue of solve requests.  dabs_server_step admits queued
+ * requests (first come, first served) while the device bytes of their
+ * contexts fit the HBM budget, advances every admitted request by the given
+ * number of generations in batched form, then retires finished requests and
+ * frees their device memory, so requests that arrive while others run join
+ * at the next round.  Each request's result equals dabs_solve alone.
+ * Latency = completion (detected at the end of a round) minus submission. */
+typedef struct dabs_server dabs_server;
+int dabs_server_create(size_t hbm_budget_bytes, dabs_server** out);
+void dabs_server_destroy(dabs_server* s);
+/* Copies W (host, n*n int16, symmetric) into the request; TOO_LARGE if the
+ * request alone exceeds the budget or n > DABS_N_MAX.  Does not block. */
+int dabs_server_submit(dabs_server* s, const int16_t* W, int32_t n, const dabs_params* p,
+                       uint64_t budget, uint64_t seed, int64_t target, uint64_t* ticket);
+/* One scheduling round (synchronous); *pending = queued + running requests. */
+int dabs_server_step(dabs_server* s, int32_t generations, int32_t* pending);
+/* status: 0 queued, 1 running, 2 done (outputs written, best_X n bytes),
+ * negative = the request failed with that DABS_E_* code. */
+int dabs_server_poll(dabs_server* s, uint64_t ticket, uint8_t* best_X, int64_t* best_E,
+                     uint64_t* flips, double* latency_s, int32_t* status);
+int dabs_server_info(const dabs_server* s, size_t* used_bytes, int32_t* queued, int32_t* running);
+
 /* ---- stepwise form of dabs_solve (device-resident state) ---------------- */
 /* Resets pools, search state and counters for a new solve.  Asynchronous. */
 int dabs_solve_begin(dabs_ctx* ctx, uint64_t seed, uint64_t budget, int64_t target);

@@ -11,61 +11,11 @@
 #include <string>
 #include <vector>
 
-#include "dabs.h"
-#include "kernels.cuh"
-#include "umma.cuh"
+#include "ctx.cuh"
 
 using namespace dabs;
 
-struct dabs_ctx {
-  int dev = 0;
-  int n = 0, ld = 0, nw = 0;
-  dabs_params p{};
-  int T = 1, tau = 0;
-  uint32_t B = 1;
-  int S = 0, P = 0, C = 0, Mmax = 1;
-  size_t merge_smem = 0;
-  cudaStream_t own = nullptr, stream = nullptr;
-  int16_t* W = nullptr;
-  int16_t* Wneg = nullptr;  // -W: lets the flip kernel read row i of sigma(x_i) W
-  int32_t* diag = nullptr;
-  DevCtrl* ctrl = nullptr;
-  DevCtrl* bulk_ctrl = nullptr;
-  DevCtrl* h_ctrl = nullptr;  // pinned staging
-  uint32_t* poolX[2] = {nullptr, nullptr};
-  int64_t* poolE[2] = {nullptr, nullptr};
-  uint8_t* poolA[2] = {nullptr, nullptr};
-  uint8_t* poolO[2] = {nullptr, nullptr};
-  uint32_t* X = nullptr;
-  int32_t* delta = nullptr;
-  int64_t* E = nullptr;
-  uint32_t* D = nullptr;
-  uint8_t* algo = nullptr;
-  uint8_t* op = nullptr;
-  uint32_t* bestX = nullptr;
-  int64_t* bestE = nullptr;
-  uint32_t* flips = nullptr;
-  int32_t* order = nullptr;   // slot launch order grouped by algorithm
-  uint32_t* gbestX = nullptr;
-  uint32_t* one_X = nullptr;   // single-vector scratch for dabs_energy / dabs_delta
-  int32_t* one_d = nullptr;
-  int64_t* one_E = nullptr;
-  SearchVariant var{};
-  // tensor-core recompute (tcgen05): W limbs, bf16 copy of the vectors, maps
-  int recompute_mode = 0;     // 0 = CUDA cores, 1 = tensor cores
-  bool tc_ready = false;
-  int n_pad = 0, rows_pad = 0;
-  uint16_t* Whi = nullptr;
-  uint16_t* Wlo = nullptr;
-  uint16_t* Abf = nullptr;
-  int64_t* E2 = nullptr;
-  int* kerr = nullptr;
-  CUtensorMap mapA{}, mapHi{}, mapLo{};
-  std::vector<void*> allocs;
-  std::string err;
-};
-
-namespace {
+namespace dabs_internal {
 
 int fail(dabs_ctx* c, int code, const char* fmt, ...) {
   if (c) {
@@ -78,16 +28,6 @@ int fail(dabs_ctx* c, int code, const char* fmt, ...) {
   }
   return code;
 }
-
-#define CK(call)                                                                           \
-  do {                                                                                     \
-    cudaError_t e_ = (call);                                                               \
-    if (e_ != cudaSuccess)                                                                 \
-      return fail(ctx, e_ == cudaErrorMemoryAllocation ? DABS_E_OOM : DABS_E_CUDA,         \
-                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);    \
-  } while (0)
-
-#define CKLAUNCH() CK(cudaGetLastError())
 
 template <class T>
 int dalloc(dabs_ctx* ctx, T** ptr, size_t count) {
@@ -231,9 +171,10 @@ int stage(dabs_ctx* ctx, int which) {
         CKLAUNCH();
       }
     }
-  } else if (which == 1) {
+  } else if (which == 1 || which == 4) {
     k_order_by_algo<<<1, 1024, 0, st>>>(ctx->algo, ctx->S, ctx->order, ctx->ctrl);
     CKLAUNCH();
+    if (which == 4) return DABS_OK;  // launch order only (batched search follows)
     const SearchArgs a = solve_search_args(ctx);
     if (!launch_search(ctx->var.nw, ctx->var.ch, &a, st, nullptr))
       return fail(ctx, DABS_E_INVALID_ARG, "no batch-search variant %d/%d", ctx->var.nw, ctx->var.ch);
@@ -268,16 +209,19 @@ int check_bits(dabs_ctx* ctx, const uint8_t* X) {
   return DABS_OK;
 }
 
-}  // namespace
+}  // namespace dabs_internal
+
+using namespace dabs_internal;
 
 namespace dabs {
-bool launch_search(int nw, int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v) {
+bool launch_search(int nw, int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
+                   const MultiArgs* m) {
   switch (nw) {
-    case 1: return launch_search_w1(ch, a, st, v);
-    case 2: return launch_search_w2(ch, a, st, v);
-    case 4: return launch_search_w4(ch, a, st, v);
-    case 8: return launch_search_w8(ch, a, st, v);
-    case 16: return launch_search_w16(ch, a, st, v);
+    case 1: return launch_search_w1(ch, a, st, v, m);
+    case 2: return launch_search_w2(ch, a, st, v, m);
+    case 4: return launch_search_w4(ch, a, st, v, m);
+    case 8: return launch_search_w8(ch, a, st, v, m);
+    case 16: return launch_search_w16(ch, a, st, v, m);
     default: return false;
   }
 }

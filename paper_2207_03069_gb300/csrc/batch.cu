@@ -1,0 +1,404 @@
+// batch.cu -- the batched and served forms of the solve.
+//
+// Batched: many contexts (instances of different n, each with its own pools,
+// searches, seed, budget and target) advance generation by generation on one
+// stream; their per-instance kernels (offspring, recompute, merge, finalise)
+// are small, and all their batch searches run in one multi-instance launch
+// per kernel variant, so the GPU is filled by the union of the instances.
+// Every instance's result is the one dabs_solve gives it alone: its kernels
+// read only its own buffers and its own control block.
+//
+// Served: a request queue admitted into contexts while an HBM budget allows
+// (first come, first served), batched as above, with requests that arrive
+// while others run admitted between rounds (continuous batching), and their
+// contexts freed as they finish.
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <new>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "ctx.cuh"
+
+using namespace dabs_internal;
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int check(cudaError_t e) { return e == cudaSuccess ? DABS_OK : (e == cudaErrorMemoryAllocation ? DABS_E_OOM : DABS_E_CUDA); }
+
+// Groups the active contexts by batch-search variant and keeps, per group, a
+// device table of their SearchArgs and slot offsets.
+struct Batcher {
+  cudaStream_t stream = nullptr;
+  bool own = false;
+  struct Group {
+    SearchVariant var{};
+    std::vector<dabs_ctx*> ctxs;
+    SearchArgs* d_insts = nullptr;
+    int32_t* d_prefix = nullptr;
+    int cap = 0;
+    int total = 0;
+  };
+  std::vector<Group> groups;
+  std::vector<dabs_ctx*> active;
+  SearchArgs* h_insts = nullptr;  // pinned staging
+  int32_t* h_prefix = nullptr;
+  int h_cap = 0;
+
+  ~Batcher() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto& g : groups) {
+      cudaFree(g.d_insts);
+      cudaFree(g.d_prefix);
+    }
+    if (h_insts) cudaFreeHost(h_insts);
+    if (h_prefix) cudaFreeHost(h_prefix);
+    if (own && stream) cudaStreamDestroy(stream);
+  }
+
+  int init() {
+    if (stream) return DABS_OK;
+    own = true;
+    return check(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+  }
+
+  // rebuild the groups for `active` (contexts must use `stream`)
+  int rebuild() {
+    int rc = check(cudaStreamSynchronize(stream));
+    if (rc) return rc;
+    std::vector<Group> ng;
+    for (dabs_ctx* c : active) {
+      Group* g = nullptr;
+      for (auto& x : ng)
+        if (x.var.nw == c->var.nw && x.var.ch == c->var.ch) g = &x;
+      if (!g) {
+        ng.push_back(Group{});
+        g = &ng.back();
+        g->var = c->var;
+      }
+      g->ctxs.push_back(c);
+    }
+    // reuse device tables
+    for (size_t i = 0; i < ng.size(); ++i) {
+      if (i < groups.size()) {
+        ng[i].d_insts = groups[i].d_insts;
+        ng[i].d_prefix = groups[i].d_prefix;
+        ng[i].cap = groups[i].cap;
+        groups[i].d_insts = nullptr;
+        groups[i].d_prefix = nullptr;
+      }
+    }
+    for (auto& g : groups) {
+      cudaFree(g.d_insts);
+      cudaFree(g.d_prefix);
+    }
+    groups.swap(ng);
+    int need = 1;
+    for (auto& g : groups) need = std::max<int>(need, (int)g.ctxs.size());
+    if (need > h_cap) {
+      if (h_insts) cudaFreeHost(h_insts);
+      if (h_prefix) cudaFreeHost(h_prefix);
+      h_insts = nullptr;
+      h_prefix = nullptr;
+      if ((rc = check(cudaMallocHost(&h_insts, sizeof(SearchArgs) * need)))) return rc;
+      if ((rc = check(cudaMallocHost(&h_prefix, sizeof(int32_t) * (need + 1))))) return rc;
+      h_cap = need;
+    }
+    for (auto& g : groups) {
+      const int k = (int)g.ctxs.size();
+      if (k > g.cap) {
+        cudaFree(g.d_insts);
+        cudaFree(g.d_prefix);
+        g.d_insts = nullptr;
+        g.d_prefix = nullptr;
+        if ((rc = check(cudaMalloc(&g.d_insts, sizeof(SearchArgs) * k)))) return rc;
+        if ((rc = check(cudaMalloc(&g.d_prefix, sizeof(int32_t) * (k + 1))))) return rc;
+        g.cap = k;
+      }
+      int acc = 0;
+      for (int i = 0; i < k; ++i) {
+        h_insts[i] = solve_search_args(g.ctxs[i]);
+        h_prefix[i] = acc;
+        acc += g.ctxs[i]->S;
+      }
+      h_prefix[k] = acc;
+      g.total = acc;
+      if ((rc = check(cudaMemcpyAsync(g.d_insts, h_insts, sizeof(SearchArgs) * k, cudaMemcpyHostToDevice, stream))))
+        return rc;
+      if ((rc = check(cudaMemcpyAsync(g.d_prefix, h_prefix, sizeof(int32_t) * (k + 1), cudaMemcpyHostToDevice, stream))))
+        return rc;
+      // staging is reused by the next group: wait for these copies
+      if ((rc = check(cudaStreamSynchronize(stream)))) return rc;
+    }
+    return DABS_OK;
+  }
+
+  // one generation of every active context
+  int generation() {
+    int rc;
+    for (dabs_ctx* c : active)
+      if ((rc = stage(c, 0)) || (rc = stage(c, 4))) return rc;
+    for (auto& g : groups) {
+      const MultiArgs m{g.d_insts, g.d_prefix, (int32_t)g.ctxs.size(), g.total};
+      const SearchArgs first = solve_search_args(g.ctxs[0]);
+      if (!launch_search(g.var.nw, g.var.ch, &first, stream, nullptr, &m)) return DABS_E_INVALID_ARG;
+      if ((rc = check(cudaGetLastError()))) return rc;
+    }
+    for (dabs_ctx* c : active)
+      if ((rc = stage(c, 2)) || (rc = stage(c, 3))) return rc;
+    return DABS_OK;
+  }
+};
+
+// all control blocks of `ctxs` in one round trip
+int read_done(std::vector<dabs_ctx*>& ctxs, std::vector<DevCtrl>& out, cudaStream_t st) {
+  out.resize(ctxs.size());
+  for (size_t i = 0; i < ctxs.size(); ++i) {
+    const int rc = check(cudaMemcpyAsync(ctxs[i]->h_ctrl, ctxs[i]->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st));
+    if (rc) return rc;
+  }
+  const int rc = check(cudaStreamSynchronize(st));
+  if (rc) return rc;
+  for (size_t i = 0; i < ctxs.size(); ++i) out[i] = *ctxs[i]->h_ctrl;
+  return DABS_OK;
+}
+
+}  // namespace
+
+extern "C" int dabs_batch_solve(dabs_ctx* const* ctxs, int32_t k, const uint64_t* budgets,
+                                const uint64_t* seeds, const int64_t* targets,
+                                uint8_t* const* best_X, int64_t* best_E, uint64_t* flips) {
+  if (k < 0 || (k > 0 && (!ctxs || !budgets || !seeds))) return DABS_E_INVALID_ARG;
+  for (int i = 0; i < k; ++i)
+    if (!ctxs[i]) return DABS_E_INVALID_ARG;
+  if (k == 0) return DABS_OK;
+  Batcher b;
+  int rc = b.init();
+  if (rc) return rc;
+  std::vector<cudaStream_t> saved(k);
+  for (int i = 0; i < k; ++i) {
+    saved[i] = ctxs[i]->stream;
+    cudaStreamSynchronize(saved[i]);
+    ctxs[i]->stream = b.stream;
+  }
+  auto restore = [&]() {
+    cudaStreamSynchronize(b.stream);
+    for (int i = 0; i < k; ++i) ctxs[i]->stream = saved[i];
+  };
+  for (int i = 0; i < k && !rc; ++i)
+    rc = dabs_solve_begin(ctxs[i], seeds[i], budgets[i], targets ? targets[i] : INT64_MIN);
+  b.active.assign(ctxs, ctxs + k);
+  if (!rc) rc = b.rebuild();
+  int chunk = 1;
+  std::vector<DevCtrl> cs;
+  while (!rc && !b.active.empty()) {
+    for (int q = 0; q < chunk && !rc; ++q) rc = b.generation();
+    if (rc) break;
+    if ((rc = read_done(b.active, cs, b.stream))) break;
+    std::vector<dabs_ctx*> still;
+    for (size_t i = 0; i < b.active.size(); ++i)
+      if (!cs[i].done) still.push_back(b.active[i]);
+    if (still.size() != b.active.size()) {
+      b.active.swap(still);
+      if (!b.active.empty()) rc = b.rebuild();
+    }
+    if (chunk < 16) chunk <<= 1;
+  }
+  for (int i = 0; i < k && !rc; ++i) {
+    if (best_X || best_E) rc = dabs_solve_best(ctxs[i], best_X ? best_X[i] : nullptr, best_E ? &best_E[i] : nullptr);
+    if (!rc && flips) rc = dabs_solve_status(ctxs[i], &flips[i], nullptr, nullptr, nullptr);
+  }
+  restore();
+  return rc;
+}
+
+// ------------------------------------------------------------------ server
+namespace {
+
+struct Request {
+  uint64_t ticket = 0;
+  std::vector<int16_t> W;
+  int32_t n = 0;
+  dabs_params p{};
+  uint64_t budget = 0, seed = 0;
+  int64_t target = INT64_MIN;
+  size_t bytes = 0;
+  double t_submit = 0, t_start = 0, t_done = 0;
+  int state = 0;  // 0 queued, 1 running, 2 done, < 0 failed (error code)
+  dabs_ctx* ctx = nullptr;
+  std::vector<uint8_t> best_X;
+  int64_t best_E = INT64_MAX;
+  uint64_t flips = 0;
+};
+
+// device bytes a context for (n, p) allocates (dabs_create's buffers)
+size_t ctx_bytes(int32_t n, const dabs_params& p) {
+  const size_t ld = (size_t)(n + 63) / 64 * 64, nw = (size_t)(n + 31) / 32;
+  const size_t S = (size_t)p.searches, PC = (size_t)p.pools * p.pool_cap;
+  size_t b = 2 * (size_t)n * ld * 2 + (size_t)n * 4;                 // W, -W, diag
+  b += 2 * PC * (nw * 4 + 8 + 2);                                    // pools
+  b += S * (3 * nw * 4 + ld * 4 + 8 + 2 + 8 + 4 + 4);                // search state, results
+  if (p.seed_mode == 1) {                                             // tensor recompute
+    const size_t np = (size_t)(n + 127) / 128 * 128, rows = (S + 127) / 128 * 128;
+    b += 2 * np * np * 2 + rows * np * 2 + rows * 8;
+  }
+  return b + 64 * 1024;
+}
+
+}  // namespace
+
+struct dabs_server {
+  size_t budget = 0, used = 0;
+  uint64_t next = 1;
+  std::deque<Request*> queue;
+  std::vector<Request*> running;
+  std::map<uint64_t, std::unique_ptr<Request>> all;
+  Batcher batch;
+  bool dirty = false;
+};
+
+extern "C" int dabs_server_create(size_t hbm_budget_bytes, dabs_server** out) {
+  if (!out || hbm_budget_bytes == 0) return DABS_E_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return DABS_E_NO_DEVICE;
+  dabs_server* s = new (std::nothrow) dabs_server;
+  if (!s) return DABS_E_OOM;
+  s->budget = hbm_budget_bytes;
+  const int rc = s->batch.init();
+  if (rc) {
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return DABS_OK;
+}
+
+extern "C" void dabs_server_destroy(dabs_server* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->batch.stream);
+  for (auto& kv : s->all)
+    if (kv.second->ctx) dabs_destroy(kv.second->ctx);
+  delete s;
+}
+
+extern "C" int dabs_server_submit(dabs_server* s, const int16_t* W, int32_t n, const dabs_params* p,
+                                  uint64_t budget, uint64_t seed, int64_t target, uint64_t* ticket) {
+  if (!s || !W || !p || !ticket || n < 1) return DABS_E_INVALID_ARG;
+  if (n > DABS_N_MAX) return DABS_E_TOO_LARGE;
+  auto r = std::make_unique<Request>();
+  r->ticket = s->next++;
+  r->W.assign(W, W + (size_t)n * n);
+  r->n = n;
+  r->p = *p;
+  r->budget = budget;
+  r->seed = seed;
+  r->target = target;
+  r->bytes = ctx_bytes(n, *p);
+  if (r->bytes > s->budget) return DABS_E_TOO_LARGE;
+  r->t_submit = now_s();
+  *ticket = r->ticket;
+  s->queue.push_back(r.get());
+  s->all[r->ticket] = std::move(r);
+  return DABS_OK;
+}
+
+// One scheduling round: admit queued requests while the HBM budget allows,
+// advance every running request by `generations` generations (batched), then
+// retire the finished ones and free their device memory.  *pending receives
+// the number of queued plus running requests.
+extern "C" int dabs_server_step(dabs_server* s, int32_t generations, int32_t* pending) {
+  if (!s || generations < 1) return DABS_E_INVALID_ARG;
+  int rc = DABS_OK;
+  while (!s->queue.empty() && s->used + s->queue.front()->bytes <= s->budget) {
+    Request* r = s->queue.front();
+    s->queue.pop_front();
+    rc = dabs_create(r->W.data(), r->n, &r->p, &r->ctx);
+    if (rc) {
+      r->state = rc;
+      r->t_done = now_s();
+      continue;
+    }
+    cudaStreamSynchronize(r->ctx->stream);
+    r->ctx->stream = s->batch.stream;
+    if ((rc = dabs_solve_begin(r->ctx, r->seed, r->budget, r->target))) {
+      r->state = rc;
+      dabs_destroy(r->ctx);
+      r->ctx = nullptr;
+      continue;
+    }
+    r->state = 1;
+    r->t_start = now_s();
+    s->used += r->bytes;
+    s->running.push_back(r);
+    s->dirty = true;
+  }
+  if (!s->running.empty()) {
+    if (s->dirty) {
+      s->batch.active.clear();
+      for (Request* r : s->running) s->batch.active.push_back(r->ctx);
+      if ((rc = s->batch.rebuild())) return rc;
+      s->dirty = false;
+    }
+    for (int q = 0; q < generations; ++q)
+      if ((rc = s->batch.generation())) return rc;
+    std::vector<DevCtrl> cs;
+    if ((rc = read_done(s->batch.active, cs, s->batch.stream))) return rc;
+    std::vector<Request*> still;
+    for (size_t i = 0; i < s->running.size(); ++i) {
+      Request* r = s->running[i];
+      if (!cs[i].done) {
+        still.push_back(r);
+        continue;
+      }
+      r->best_X.resize(r->n);
+      dabs_ctx* c = r->ctx;
+      c->stream = c->own;
+      rc = dabs_solve_best(c, r->best_X.data(), &r->best_E);
+      r->flips = cs[i].flips_total;
+      r->t_done = now_s();
+      r->state = rc ? rc : 2;
+      dabs_destroy(c);
+      r->ctx = nullptr;
+      s->used -= r->bytes;
+      r->W.clear();
+      r->W.shrink_to_fit();
+      s->dirty = true;
+    }
+    s->running.swap(still);
+  }
+  if (pending) *pending = (int32_t)(s->queue.size() + s->running.size());
+  return DABS_OK;
+}
+
+// status: 0 queued, 1 running, 2 done (outputs written), < 0 failed
+extern "C" int dabs_server_poll(dabs_server* s, uint64_t ticket, uint8_t* best_X, int64_t* best_E,
+                                uint64_t* flips, double* latency_s, int32_t* status) {
+  if (!s) return DABS_E_INVALID_ARG;
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return DABS_E_INVALID_ARG;
+  Request* r = it->second.get();
+  if (status) *status = r->state;
+  if (r->state == 2) {
+    if (best_X) std::copy(r->best_X.begin(), r->best_X.end(), best_X);
+    if (best_E) *best_E = r->best_E;
+    if (flips) *flips = r->flips;
+    if (latency_s) *latency_s = r->t_done - r->t_submit;
+  }
+  return DABS_OK;
+}
+
+extern "C" int dabs_server_info(const dabs_server* s, size_t* used_bytes, int32_t* queued,
+                                int32_t* running) {
+  if (!s) return DABS_E_INVALID_ARG;
+  if (used_bytes) *used_bytes = s->used;
+  if (queued) *queued = (int32_t)s->queue.size();
+  if (running) *running = (int32_t)s->running.size();
+  return DABS_OK;
+}

@@ -118,4 +118,13 @@ struct SearchArgs {
   const int32_t* order; // launch order of the slots (grouped by algorithm), or null
 };
 
+// Several instances in one batch-search launch: slot q belongs to the
+// instance i with prefix[i] <= q < prefix[i+1] and is its (q - prefix[i])-th slot.
+struct MultiArgs {
+  const SearchArgs* insts;  // [ninst] in device memory
+  const int32_t* prefix;    // [ninst + 1] slot offsets
+  int32_t ninst;
+  int32_t total;            // prefix[ninst]
+};
+
 }  // namespace dabs

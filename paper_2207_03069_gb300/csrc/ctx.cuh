@@ -1,0 +1,83 @@
+// ctx.cuh -- the solver context behind the C ABI's opaque dabs_ctx, and the
+// internal helpers shared by the single-instance calls (abi.cu), the batched
+// solve and the request server (batch.cu).
+#pragma once
+#include <cuda.h>
+
+#include <string>
+#include <vector>
+
+#include "dabs.h"
+#include "kernels.cuh"
+#include "umma.cuh"
+
+using namespace dabs;
+
+struct dabs_ctx {
+  int dev = 0;
+  int n = 0, ld = 0, nw = 0;
+  dabs_params p{};
+  int T = 1, tau = 0;
+  uint32_t B = 1;
+  int S = 0, P = 0, C = 0, Mmax = 1;
+  size_t merge_smem = 0;
+  cudaStream_t own = nullptr, stream = nullptr;
+  int16_t* W = nullptr;
+  int16_t* Wneg = nullptr;  // -W: lets the flip kernel read row i of sigma(x_i) W
+  int32_t* diag = nullptr;
+  DevCtrl* ctrl = nullptr;
+  DevCtrl* bulk_ctrl = nullptr;
+  DevCtrl* h_ctrl = nullptr;  // pinned staging
+  uint32_t* poolX[2] = {nullptr, nullptr};
+  int64_t* poolE[2] = {nullptr, nullptr};
+  uint8_t* poolA[2] = {nullptr, nullptr};
+  uint8_t* poolO[2] = {nullptr, nullptr};
+  uint32_t* X = nullptr;
+  int32_t* delta = nullptr;
+  int64_t* E = nullptr;
+  uint32_t* D = nullptr;
+  uint8_t* algo = nullptr;
+  uint8_t* op = nullptr;
+  uint32_t* bestX = nullptr;
+  int64_t* bestE = nullptr;
+  uint32_t* flips = nullptr;
+  int32_t* order = nullptr;   // slot launch order grouped by algorithm
+  uint32_t* gbestX = nullptr;
+  uint32_t* one_X = nullptr;   // single-vector scratch for dabs_energy / dabs_delta
+  int32_t* one_d = nullptr;
+  int64_t* one_E = nullptr;
+  SearchVariant var{};
+  // tensor-core recompute (tcgen05): W limbs, bf16 copy of the vectors, maps
+  int recompute_mode = 0;     // 0 = CUDA cores, 1 = tensor cores
+  bool tc_ready = false;
+  int n_pad = 0, rows_pad = 0;
+  uint16_t* Whi = nullptr;
+  uint16_t* Wlo = nullptr;
+  uint16_t* Abf = nullptr;
+  int64_t* E2 = nullptr;
+  int* kerr = nullptr;
+  CUtensorMap mapA{}, mapHi{}, mapLo{};
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? DABS_E_OOM : DABS_E_CUDA,         \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);    \
+  } while (0)
+
+#define CKLAUNCH() CK(cudaGetLastError())
+
+
+namespace dabs_internal {
+int fail(dabs_ctx* c, int code, const char* fmt, ...);
+SearchArgs solve_search_args(dabs_ctx* ctx);
+// 0 offspring (+ recompute), 1 launch order + batch search, 2 merge,
+// 3 finalise, 4 launch order only
+int stage(dabs_ctx* ctx, int which);
+int read_ctrl(dabs_ctx* ctx, DevCtrl* out);
+}  // namespace dabs_internal

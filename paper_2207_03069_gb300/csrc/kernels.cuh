@@ -90,11 +90,17 @@ struct SearchVariant {
   int nw, ch, cap, cta, spc;
 };
 // launches k_batch_search<NW, CH>; returns false if (nw, ch) is not built
-bool launch_search(int nw, int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
-bool launch_search_w1(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
-bool launch_search_w2(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
-bool launch_search_w4(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
-bool launch_search_w8(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
-bool launch_search_w16(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v);
+bool launch_search(int nw, int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
+                   const MultiArgs* m = nullptr);
+bool launch_search_w1(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
+                       const MultiArgs* m = nullptr);
+bool launch_search_w2(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
+                       const MultiArgs* m = nullptr);
+bool launch_search_w4(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
+                       const MultiArgs* m = nullptr);
+bool launch_search_w8(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
+                       const MultiArgs* m = nullptr);
+bool launch_search_w16(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
+                       const MultiArgs* m = nullptr);
 
 }  // namespace dabs

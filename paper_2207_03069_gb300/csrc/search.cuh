@@ -721,15 +721,30 @@ struct Searcher {
 };
 
 template <int NW, int CH>
-__global__ void __launch_bounds__(Cfg<NW, CH>::CTA) k_batch_search(const SearchArgs a) {
+__global__ void __launch_bounds__(Cfg<NW, CH>::CTA)
+    k_batch_search(const SearchArgs single, const MultiArgs multi) {
   using C = Cfg<NW, CH>;
   __shared__ SmemSearch<C> smem[C::SPC];
   const int sl = threadIdx.x / C::NT;
   const uint32_t slot = blockIdx.x * C::SPC + sl;
-  if (slot >= (uint32_t)a.S) return;
+  // one instance (single) or several (multi: find the slot's instance)
+  const SearchArgs* ap = &single;
+  uint32_t local = slot;
+  if (multi.insts) {
+    if (slot >= (uint32_t)multi.total) return;
+    int lo = 0, hi = multi.ninst;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if ((uint32_t)multi.prefix[mid] <= slot) lo = mid; else hi = mid;
+    }
+    ap = multi.insts + lo;
+    local = slot - (uint32_t)multi.prefix[lo];
+  }
+  const SearchArgs& a = *ap;
+  if (local >= (uint32_t)a.S) return;
   // slots grouped by algorithm keep each SM on one loop body (instruction
   // cache); the search index s, and with it every result, is unchanged
-  const uint32_t s = a.order ? (uint32_t)a.order[slot] : slot;
+  const uint32_t s = a.order ? (uint32_t)a.order[local] : local;
   const DevCtrl* ctrl = a.ctrl;
   if (ctrl->done) return;
   Searcher<C> sr(a, &smem[sl], threadIdx.x % C::NT, s, ctrl->g, ctrl->seed);

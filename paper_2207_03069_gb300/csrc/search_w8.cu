@@ -5,28 +5,42 @@
 
 namespace dabs {
 
-// a == nullptr: only report the variant; otherwise launch one batch search per slot
-bool launch_search_w8(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v) {
+// a == nullptr: only report the variant; otherwise launch one batch search per
+// slot of one instance (m == nullptr) or of the instances listed in *m
+bool launch_search_w8(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
+                       const MultiArgs* m) {
   switch (ch) {
     case 1: {
       using C = Cfg<8, 1>;
       if (v) *v = SearchVariant{8, 1, C::CAP, C::CTA, C::SPC};
-      if (a && a->S > 0)
-        k_batch_search<8, 1><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      if (a) {
+        const int slots = m ? m->total : a->S;
+        if (slots > 0)
+          k_batch_search<8, 1><<<(slots + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(
+              *a, m ? *m : MultiArgs{nullptr, nullptr, 0, 0});
+      }
       return true;
     }
     case 2: {
       using C = Cfg<8, 2>;
       if (v) *v = SearchVariant{8, 2, C::CAP, C::CTA, C::SPC};
-      if (a && a->S > 0)
-        k_batch_search<8, 2><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      if (a) {
+        const int slots = m ? m->total : a->S;
+        if (slots > 0)
+          k_batch_search<8, 2><<<(slots + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(
+              *a, m ? *m : MultiArgs{nullptr, nullptr, 0, 0});
+      }
       return true;
     }
     case 4: {
       using C = Cfg<8, 4>;
       if (v) *v = SearchVariant{8, 4, C::CAP, C::CTA, C::SPC};
-      if (a && a->S > 0)
-        k_batch_search<8, 4><<<(a->S + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(*a);
+      if (a) {
+        const int slots = m ? m->total : a->S;
+        if (slots > 0)
+          k_batch_search<8, 4><<<(slots + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(
+              *a, m ? *m : MultiArgs{nullptr, nullptr, 0, 0});
+      }
       return true;
     }
     default: return false;

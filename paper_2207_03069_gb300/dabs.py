@@ -72,6 +72,14 @@ EXPORTS = {
                                      C.c_int32]),
     "dabs_set_recompute": (C.c_int, [C.c_void_p, C.c_int32]),
     "dabs_kernel_status": (C.c_int, [C.c_void_p]),
+    "dabs_batch_solve": (C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 6),
+    "dabs_server_create": (C.c_int, [C.c_size_t, C.c_void_p]),
+    "dabs_server_destroy": (None, [C.c_void_p]),
+    "dabs_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_uint64,
+                                     C.c_uint64, C.c_int64, C.c_void_p]),
+    "dabs_server_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "dabs_server_poll": (C.c_int, [C.c_void_p, C.c_uint64] + [C.c_void_p] * 5),
+    "dabs_server_info": (C.c_int, [C.c_void_p] * 4),
     "dabs_bulk_search_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                            C.c_uint64, C.c_uint32, C.c_int32] + [C.c_void_p] * 9),
 }
@@ -121,6 +129,82 @@ def default_params(**kw) -> Params:
         else:
             setattr(p, k, v)
     return p
+
+
+def batch_solve(ctxs, budgets, seeds, targets=None):
+    """dabs_batch_solve: returns [(X, E, flips)] per context."""
+    k = len(ctxs)
+    hs = (C.c_void_p * k)(*[c._h.value for c in ctxs])
+    bud = np.asarray([min(int(b), 2**64 - 1) for b in budgets], np.uint64)
+    sd = np.asarray(seeds, np.uint64)
+    tg = None if targets is None else np.asarray(
+        [INT64_MIN if t is None else int(t) for t in targets], np.int64)
+    Xs = [np.zeros(c.n, np.uint8) for c in ctxs]
+    xp = (C.c_void_p * k)(*[x.ctypes.data for x in Xs])
+    E = np.zeros(k, np.int64)
+    F = np.zeros(k, np.uint64)
+    rc = lib().dabs_batch_solve(hs, k, _ptr(bud), _ptr(sd), _ptr(tg), xp, _ptr(E), _ptr(F))
+    if rc != OK:
+        raise DabsError(rc, lib().dabs_last_error(ctxs[0]._h).decode() if k else "")
+    return [(Xs[i], int(E[i]), int(F[i])) for i in range(k)]
+
+
+class Server:
+    """Request server (continuous batching under an HBM budget)."""
+
+    def __init__(self, hbm_budget_bytes: int):
+        h = C.c_void_p()
+        rc = lib().dabs_server_create(int(hbm_budget_bytes), C.byref(h))
+        if rc != OK:
+            raise DabsError(rc)
+        self._h = h
+        self.n_of = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dabs_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, W, params: Params, budget: int, seed: int, target=None) -> int:
+        W = np.ascontiguousarray(W, dtype=np.int16)
+        t = C.c_uint64()
+        rc = lib().dabs_server_submit(self._h, _ptr(W), W.shape[0], C.byref(params),
+                                      min(int(budget), 2**64 - 1), seed,
+                                      INT64_MIN if target is None else int(target), C.byref(t))
+        if rc != OK:
+            raise DabsError(rc)
+        self.n_of[t.value] = W.shape[0]
+        return int(t.value)
+
+    def step(self, generations: int = 1) -> int:
+        p = C.c_int32()
+        rc = lib().dabs_server_step(self._h, generations, C.byref(p))
+        if rc != OK:
+            raise DabsError(rc)
+        return int(p.value)
+
+    def poll(self, ticket: int):
+        """(status, X, E, flips, latency_s); status 2 = done."""
+        X = np.zeros(self.n_of[ticket], np.uint8)
+        e, f, lat, st = C.c_int64(), C.c_uint64(), C.c_double(), C.c_int32()
+        rc = lib().dabs_server_poll(self._h, ticket, _ptr(X), C.byref(e), C.byref(f),
+                                    C.byref(lat), C.byref(st))
+        if rc != OK:
+            raise DabsError(rc)
+        return int(st.value), X, int(e.value), int(f.value), float(lat.value)
+
+    def info(self):
+        u, q, r = C.c_size_t(), C.c_int32(), C.c_int32()
+        rc = lib().dabs_server_info(self._h, C.byref(u), C.byref(q), C.byref(r))
+        if rc != OK:
+            raise DabsError(rc)
+        return int(u.value), int(q.value), int(r.value)
 
 
 def bulk_search_noalloc(W, n, ld, params, seed, g, X, delta, E, D, algo, best_X, best_E, flips,

@@ -1,0 +1,81 @@
+"""Batched and served forms: every instance's result equals its solve alone
+(and the oracle's), whatever the mix, kernel variants and arrival order;
+the server never exceeds its HBM budget."""
+import numpy as np
+import pytest
+
+from paper_2207_03069_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_03069_gb300 import build, dabs
+    build.build()
+    return dabs
+
+
+SIZES = [64, 200, 300, 700, 1100, 2100]
+
+
+def instance(n, k):
+    return wl.dense_qubo(n, -1000, 1000, seed=100 + k)
+
+
+@pytest.mark.parametrize("seed_mode", [0, 1])
+def test_batch_solve_equals_alone(D, orc, seed_mode):
+    kw = dict(searches=48, pools=4, pool_cap=16, tabu=8, s=(1, 10), b=(1, 1), seed_mode=seed_mode,
+              max_generations=5)
+    Ws = [instance(n, k) for k, n in enumerate(SIZES)]
+    ctxs = [D.Context(W, **kw) for W in Ws]
+    budgets = [10**9, 10**9, 40000, 10**9, 10**9, 10**9]  # one stops early on its budget
+    seeds = [11 + k for k in range(len(Ws))]
+    out = D.batch_solve(ctxs, budgets, seeds)
+    variants = {(c.info()["warps"], c.info()["chunks"]) for c in ctxs}
+    assert len(variants) >= 3  # several multi-instance search launches
+    for k, (W, c) in enumerate(zip(Ws, ctxs)):
+        alone = D.Context(W, **kw).solve(budgets[k], seeds[k])
+        assert out[k][1] == alone[1] and out[k][2] == alone[2], k
+        assert np.array_equal(out[k][0], alone[0]), k
+        if W.shape[0] <= 300:
+            ox, oe, of, _ = orc.solve(W, orc.make_params(**kw), budgets[k], seeds[k], threads=8)
+            assert (out[k][1], out[k][2]) == (oe, of) and np.array_equal(out[k][0], ox)
+
+
+def test_server_equals_alone_and_respects_budget(D):
+    kw = dict(searches=64, pools=4, pool_cap=16, tabu=8, s=(1, 10), b=(1, 1), seed_mode=1,
+              max_generations=4)
+    sizes = [512, 1024, 128, 2048, 256, 768, 1500, 96]
+    Ws = [instance(n, k) for k, n in enumerate(sizes)]
+    params = D.default_params(**kw)
+    # a budget that holds about two of the larger contexts at once
+    srv = D.Server(hbm_budget_bytes=48 << 20)
+    tickets = []
+    for k, W in enumerate(Ws[:4]):
+        tickets.append(srv.submit(W, params, 10**9, 7 + k))
+    max_running, max_used, rounds = 0, 0, 0
+    while True:
+        if rounds == 1:  # requests arriving while others run
+            for k, W in enumerate(Ws[4:], start=4):
+                tickets.append(srv.submit(W, params, 10**9, 7 + k))
+        pending = srv.step(1)
+        used, q, r = srv.info()
+        max_running, max_used = max(max_running, r), max(max_used, used)
+        rounds += 1
+        if pending == 0 and rounds > 1:
+            break
+        assert rounds < 200
+    assert max_used <= 48 << 20 and max_running >= 2
+    for k, (t, W) in enumerate(zip(tickets, Ws)):
+        st, X, E, F, lat = srv.poll(t)
+        assert st == 2 and lat > 0
+        aX, aE, aF = D.Context(W, **kw).solve(10**9, 7 + k)
+        assert (E, F) == (aE, aF) and np.array_equal(X, aX), k
+    too_big = np.zeros((8192, 8192), np.int16)
+    with pytest.raises(D.DabsError):
+        srv.submit(too_big, params, 10, 1)
