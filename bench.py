@@ -179,6 +179,142 @@ def recompute_rate(torch, dabs, dev, n=4096, count=256, reps=20):
             "note": "bf16 limbs on tcgen05.mma kind::f16, exact; includes bit->bf16 expansion"}
 
 
+def pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(np.ceil(q / 100.0 * len(xs))) - 1))
+    return xs[k]
+
+
+def tsp_ttt(dabs, seeds=8, generations=30):
+    """TSP-shaped QUBO (32 cities, one-hot 1024 bits, 2048 searches, b = 1,
+    s = 1/10): per seed the target is the best energy that seed's solve reaches
+    in `generations` generations; time-to-target = wall time of the solve with
+    that target (host API, results back on the host)."""
+    W, dist, p = wl.tsp_qubo(32, 1000, seed=2)
+    kw = dict(searches=2048, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=0)
+    ctx = dabs.Context(W, **kw, max_generations=generations)
+    ttt, flips, feasible = [], 0, 0
+    ctx.solve(10**12, seed=10**6)  # warm
+    for sd in range(seeds):
+        X, target, _ = ctx.solve(10**12, seed=sd)
+        t0 = time.perf_counter()
+        X2, E2, F2 = ctx.solve(10**12, seed=sd, target=target)
+        ttt.append(time.perf_counter() - t0)
+        flips += F2
+        assert E2 == target
+        M = X2.reshape(32, 32)  # one-hot feasible: every position and city used once
+        feasible += int((M.sum(0) == 1).all() and (M.sum(1) == 1).all())
+    ctx.close()
+    return {"workload": "TSP 32 cities one-hot n=1024, 2048 searches, b=1, s=1/10",
+            "seeds": seeds, "target": f"best energy of the same seed after {generations} generations",
+            "ttt_p50_s": pct(ttt, 50), "ttt_p99_s": pct(ttt, 99), "flips_per_s": flips / sum(ttt),
+            "feasible_targets": feasible}
+
+
+def batched_vs_plain(dabs, count=64, generations=3):
+    """64 dense QUBOs, n log-uniform in [256, 4096] (seed 3), W ~ U[-1000, 1000],
+    256 searches each, recompute seeding on the tensor cores: one batched solve
+    vs one solve per instance (one instance per launch), same seeds."""
+    ns = wl.batched_sizes(count, 256, 4096, seed=3)
+    kw = dict(searches=256, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=1,
+              max_generations=generations)
+    Ws = [wl.dense_qubo(int(n), -1000, 1000, seed=1000 + i) for i, n in enumerate(ns)]
+    ctxs = [dabs.Context(W, **kw) for W in Ws]
+    seeds = list(range(count))
+    big = [10**12] * count
+    dabs.batch_solve(ctxs[:2], big[:2], seeds[:2])  # warm
+    for c in ctxs[:2]:
+        c.solve(10**12, seed=0)
+    torch_sync()
+    t0 = time.perf_counter()
+    bout = dabs.batch_solve(ctxs, big, seeds)
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pout = [c.solve(10**12, seed=sd) for c, sd in zip(ctxs, seeds)]
+    tp = time.perf_counter() - t0
+    same = all(b[1] == q[1] and b[2] == q[2] and np.array_equal(b[0], q[0])
+               for b, q in zip(bout, pout))
+    fl = sum(b[2] for b in bout)
+    for c in ctxs:
+        c.close()
+    return {"workload": f"{count} dense QUBOs n log-uniform [256,4096], 256 searches each, "
+                        f"{generations} generations, tensor-core recompute seeding",
+            "batched_flips_per_s": fl / tb, "plain_flips_per_s": fl / tp,
+            "speedup": tp / tb, "identical_results": bool(same), "flips": fl}
+
+
+def serving(dabs, seconds=4.0, rate=50.0, generations=20, sizes=(512, 1024, 2048, 4096, 8192),
+            budget_gb=60, plain=True):
+    """Poisson arrivals (seed 4) of dense QUBOs, n uniform in `sizes`, 256
+    searches, 20 generations each, recompute seeding; served with continuous
+    batching under an HBM budget, and (plain) one request at a time on the
+    same trace.  Latency = completion - arrival."""
+    rng = np.random.default_rng(4)
+    arr = wl.poisson_arrivals(rate, seconds, seed=4)
+    reqs = [(float(t), int(rng.choice(sizes)), 5000 + i) for i, t in enumerate(arr)]
+    kw = dict(searches=256, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=1,
+              max_generations=generations)
+    params = dabs.default_params(**kw)
+    Wcache = {}
+
+    def W_of(n, sd):
+        key = (n, sd)
+        if key not in Wcache:
+            Wcache[key] = wl.dense_qubo(n, -1000, 1000, seed=sd)
+        return Wcache[key]
+
+    for _, n, sd in reqs:  # instances are prepared before the clock starts
+        W_of(n, sd)
+    out = {"workload": f"Poisson {rate}/s for {seconds}s, n in {list(sizes)}, 256 searches, "
+                       f"{generations} generations, recompute seeding", "requests": len(reqs)}
+    srv = dabs.Server(budget_gb << 30)
+    t0 = time.perf_counter()
+    tickets, i, pending = [], 0, 0
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i][0] <= now:
+            _, n, sd = reqs[i]
+            tickets.append(srv.submit(W_of(n, sd), params, 10**12, sd))
+            i += 1
+        if srv.info()[1] + srv.info()[2] == 0:
+            time.sleep(0.001)
+            pending = 0
+            continue
+        pending = srv.step(1)
+    wall = time.perf_counter() - t0
+    lat, fl = [], 0
+    for t in tickets:
+        st, X, E, F, L = srv.poll(t)
+        lat.append(L)
+        fl += F
+    srv.close()
+    out.update({"served_p50_s": pct(lat, 50), "served_p99_s": pct(lat, 99),
+                "served_flips_per_s": fl / wall, "served_wall_s": wall})
+    if plain:
+        t0 = time.perf_counter()
+        lat2, free_at = [], 0.0
+        for (ta, n, sd) in reqs:
+            start = max(ta, free_at)
+            now = time.perf_counter() - t0
+            if now < start:
+                time.sleep(start - now)
+            c = dabs.Context(W_of(n, sd), **kw)
+            c.solve(10**12, seed=sd)
+            c.close()
+            free_at = time.perf_counter() - t0
+            lat2.append(free_at - ta)
+        out.update({"plain_p50_s": pct(lat2, 50), "plain_p99_s": pct(lat2, 99),
+                    "plain_flips_per_s": fl / (time.perf_counter() - t0)})
+    return out
+
+
+def torch_sync():
+    import torch
+    torch.cuda.synchronize()
+
+
 def oracle_rate(Wm, spec, seed, seconds, threads):
     """Oracle (plain C, as it stands) on the same workload: whole generations on
     `threads` host threads until `seconds` have passed.  Returns (flips/s, gens)."""
@@ -253,6 +389,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-recompute", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the TSP time-to-target, batched and serving measurements")
+    ap.add_argument("--trace-seconds", type=float, default=4.0)
     ap.add_argument("--variant", default="", help="force warps x chunks, e.g. 4x1")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -362,6 +501,11 @@ def main():
            "call": "dabs_load_weights + dabs_solve(budget=1 generation) per step"}
 
     rec = recompute_rate(torch, dabs, dev) if not args.no_recompute else None
+    extra = {}
+    if not args.no_extra and ws == 1:
+        extra["time_to_target"] = tsp_ttt(dabs)
+        extra["batched"] = batched_vs_plain(dabs)
+        extra["serving"] = serving(dabs, seconds=args.trace_seconds)
     if rec:
         mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
         pk = json.load(open(mp))["bf16_tflops"] if os.path.exists(mp) else 1900.0
@@ -393,7 +537,7 @@ def main():
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "delta_updates_per_s": value * n, "autotune": sweep, "gpu_launches": 5 * args.steps,
                 "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-                "recompute_tensor": rec}
+                "recompute_tensor": rec, **extra}
         print(json.dumps(line), flush=True)
     ctx.close()
     if pg:
