@@ -164,6 +164,11 @@ int dabs_server_step(dabs_server* s, int32_t generations, int32_t* pending);
 int dabs_server_poll(dabs_server* s, uint64_t ticket, uint8_t* best_X, int64_t* best_E,
                      uint64_t* flips, double* latency_s, int32_t* status);
 int dabs_server_info(const dabs_server* s, size_t* used_bytes, int32_t* queued, int32_t* running);
+/* Admission also stops while the running requests' batch searches hold more
+ * than max_warps resident warps (searches x warps per search; default two
+ * waves, 64 x SM count; 0 = no cap).  A request is always admitted when
+ * nothing runs. */
+int dabs_server_set_limits(dabs_server* s, int64_t max_warps);
 
 /* ---- stepwise form of dabs_solve (device-resident state) ---------------- */
 /* Resets pools, search state and counters for a new solve.  Asynchronous. */
@@ -223,9 +228,11 @@ int dabs_info(const dabs_ctx* ctx, int32_t* n, int32_t* ld, int32_t* words, int3
               int32_t* pools, int32_t* pool_cap, int32_t* warps, int32_t* chunks);
 /* Chooses the batch-search variant; returns TOO_LARGE if it cannot hold n. */
 int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
-/* Times the batch-search stage of every built variant that holds n over
- * `generations` generations of a throwaway solve on the context's workload
- * and keeps the fastest per flip (results never depend on the variant).
+/* Runs a throwaway solve on the context's workload for `generations` warm-up
+ * generations, breeds the next generation's targets, then times the batch
+ * search of that same generation with every built variant that holds n (each
+ * from the same snapshot of the search state) and keeps the fastest per flip
+ * (results never depend on the variant).
  * table (may be NULL) receives DABS_N_VARIANTS nanoseconds-per-flip entries
  * in the order (warps x chunks) 1x1 1x2 1x4 2x1 2x2 2x4 4x1 4x2 4x4 8x1 8x2
  * 8x4 16x1 16x2, 0 where a variant cannot hold n.  Resets the solve state;

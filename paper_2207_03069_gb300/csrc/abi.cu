@@ -542,44 +542,59 @@ int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* c
                                                {16, 1}, {16, 2}};
   if (table)
     for (int q = 0; q < DABS_N_VARIANTS; ++q) table[q] = 0.f;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  // warm a throwaway solve for `generations` generations, breed the next
+  // targets, snapshot the search state, then time every variant's batch
+  // search of that same generation from the same snapshot
+  int rc = dabs_solve_begin(ctx, 0x5eed, UINT64_MAX, INT64_MIN);
+  if (rc) return rc;
+  if ((rc = dabs_solve_generations(ctx, generations))) return rc;
+  if ((rc = stage(ctx, 0)) || (rc = stage(ctx, 4))) return rc;
+  const size_t xb = (size_t)ctx->S * ctx->nw * 4, db = (size_t)ctx->S * ctx->ld * 4,
+               eb = (size_t)ctx->S * 8;
+  void* snap = nullptr;
+  CK(cudaMalloc(&snap, xb + db + eb));
+  unsigned char* sp = static_cast<unsigned char*>(snap);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   const SearchVariant keep = ctx->var;
   SearchVariant best = keep;
   float best_ns = 0.f;
-  int rc = DABS_OK;
-  for (int ci = 0; ci < DABS_N_VARIANTS; ++ci) {
-    const int* c = cand[ci];
-    SearchVariant v;
-    if (!launch_search(c[0], c[1], nullptr, nullptr, &v) || v.cap < ctx->n) continue;
-    ctx->var = v;
-    // a throwaway solve: results never depend on the variant
-    if ((rc = dabs_solve_begin(ctx, 0x5eed, UINT64_MAX, INT64_MIN)) != DABS_OK) break;
-    if ((rc = dabs_solve_generations(ctx, 1)) != DABS_OK) break;
-    float ms_total = 0.f;
-    DevCtrl c0, c1;
-    if ((rc = read_ctrl(ctx, &c0)) != DABS_OK) break;
-    for (int q = 0; q < generations; ++q) {
-      if ((rc = stage(ctx, 0)) != DABS_OK) break;
-      CK(cudaEventRecord(e0, ctx->stream));
-      if ((rc = stage(ctx, 1)) != DABS_OK) break;
-      CK(cudaEventRecord(e1, ctx->stream));
-      if ((rc = stage(ctx, 2)) != DABS_OK || (rc = stage(ctx, 3)) != DABS_OK) break;
-      CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      ms_total += ms;
+  do {
+    if ((rc = cudaMemcpyAsync(sp, ctx->X, xb, cudaMemcpyDeviceToDevice, ctx->stream)) ||
+        (rc = cudaMemcpyAsync(sp + xb, ctx->delta, db, cudaMemcpyDeviceToDevice, ctx->stream)) ||
+        (rc = cudaMemcpyAsync(sp + xb + db, ctx->E, eb, cudaMemcpyDeviceToDevice, ctx->stream)) ||
+        (rc = cudaEventCreate(&e0)) || (rc = cudaEventCreate(&e1))) {
+      rc = fail(ctx, DABS_E_CUDA, "autotune set-up failed");
+      break;
     }
-    if (rc != DABS_OK) break;
-    if ((rc = read_ctrl(ctx, &c1)) != DABS_OK) break;
-    const double fl = (double)(c1.flips_total - c0.flips_total);
-    const float ns = fl > 0 ? (float)(ms_total * 1e6 / fl) : 1e30f;
-    if (table) table[ci] = ns;
-    if (best_ns == 0.f || ns < best_ns) { best_ns = ns; best = v; }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+    for (int ci = 0; ci < DABS_N_VARIANTS && !rc; ++ci) {
+      SearchVariant v;
+      if (!launch_search(cand[ci][0], cand[ci][1], nullptr, nullptr, &v) || v.cap < ctx->n) continue;
+      cudaMemcpyAsync(ctx->X, sp, xb, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaMemcpyAsync(ctx->delta, sp + xb, db, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaMemcpyAsync(ctx->E, sp + xb + db, eb, cudaMemcpyDeviceToDevice, ctx->stream);
+      const SearchArgs a = solve_search_args(ctx);
+      cudaEventRecord(e0, ctx->stream);
+      launch_search(v.nw, v.ch, &a, ctx->stream, nullptr);
+      cudaEventRecord(e1, ctx->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        rc = fail(ctx, DABS_E_CUDA, "autotune launch failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      std::vector<uint32_t> fl(ctx->S);
+      cudaMemcpy(fl.data(), ctx->flips, fl.size() * 4, cudaMemcpyDeviceToHost);
+      double total = 0;
+      for (uint32_t f : fl) total += f;
+      const float ns = total > 0 ? (float)(ms * 1e6 / total) : 1e30f;
+      if (table) table[ci] = ns;
+      if (best_ns == 0.f || ns < best_ns) { best_ns = ns; best = v; }
+    }
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(snap);
   if (rc != DABS_OK) { ctx->var = keep; return rc; }
   ctx->var = best;
   if (warps) *warps = best.nw;

@@ -229,6 +229,7 @@ struct Request {
   uint64_t budget = 0, seed = 0;
   int64_t target = INT64_MIN;
   size_t bytes = 0;
+  int64_t warps = 0;  // resident warps of its batch searches (searches x warps per search)
   double t_submit = 0, t_start = 0, t_done = 0;
   int state = 0;  // 0 queued, 1 running, 2 done, < 0 failed (error code)
   dabs_ctx* ctx = nullptr;
@@ -255,6 +256,7 @@ size_t ctx_bytes(int32_t n, const dabs_params& p) {
 
 struct dabs_server {
   size_t budget = 0, used = 0;
+  int64_t max_warps = 0, running_warps = 0;
   uint64_t next = 1;
   std::deque<Request*> queue;
   std::vector<Request*> running;
@@ -271,6 +273,10 @@ extern "C" int dabs_server_create(size_t hbm_budget_bytes, dabs_server** out) {
   dabs_server* s = new (std::nothrow) dabs_server;
   if (!s) return DABS_E_OOM;
   s->budget = hbm_budget_bytes;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  s->max_warps = 2LL * 32 * (sms > 0 ? sms : 152);  // about two full waves of warps
   const int rc = s->batch.init();
   if (rc) {
     delete s;
@@ -302,6 +308,15 @@ extern "C" int dabs_server_submit(dabs_server* s, const int16_t* W, int32_t n, c
   r->target = target;
   r->bytes = ctx_bytes(n, *p);
   if (r->bytes > s->budget) return DABS_E_TOO_LARGE;
+  {
+    static const int order[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 4}, {4, 4}, {8, 4}};
+    int nwarp = 1;
+    for (auto& o : order) {
+      SearchVariant v;
+      if (launch_search(o[0], o[1], nullptr, nullptr, &v) && v.cap >= n) { nwarp = v.nw; break; }
+    }
+    r->warps = (int64_t)p->searches * nwarp;
+  }
   r->t_submit = now_s();
   *ticket = r->ticket;
   s->queue.push_back(r.get());
@@ -316,7 +331,12 @@ extern "C" int dabs_server_submit(dabs_server* s, const int16_t* W, int32_t n, c
 extern "C" int dabs_server_step(dabs_server* s, int32_t generations, int32_t* pending) {
   if (!s || generations < 1) return DABS_E_INVALID_ARG;
   int rc = DABS_OK;
-  while (!s->queue.empty() && s->used + s->queue.front()->bytes <= s->budget) {
+  // first come, first served while the HBM budget holds and the running
+  // searches do not exceed the warp cap (admitting every waiting request at
+  // once would only share the GPU among them and delay all of them)
+  while (!s->queue.empty() && s->used + s->queue.front()->bytes <= s->budget &&
+         (s->running.empty() || s->max_warps <= 0 ||
+          s->running_warps + s->queue.front()->warps <= s->max_warps)) {
     Request* r = s->queue.front();
     s->queue.pop_front();
     rc = dabs_create(r->W.data(), r->n, &r->p, &r->ctx);
@@ -336,6 +356,7 @@ extern "C" int dabs_server_step(dabs_server* s, int32_t generations, int32_t* pe
     r->state = 1;
     r->t_start = now_s();
     s->used += r->bytes;
+    s->running_warps += r->warps;
     s->running.push_back(r);
     s->dirty = true;
   }
@@ -367,6 +388,7 @@ extern "C" int dabs_server_step(dabs_server* s, int32_t generations, int32_t* pe
       dabs_destroy(c);
       r->ctx = nullptr;
       s->used -= r->bytes;
+      s->running_warps -= r->warps;
       r->W.clear();
       r->W.shrink_to_fit();
       s->dirty = true;
@@ -391,6 +413,12 @@ extern "C" int dabs_server_poll(dabs_server* s, uint64_t ticket, uint8_t* best_X
     if (flips) *flips = r->flips;
     if (latency_s) *latency_s = r->t_done - r->t_submit;
   }
+  return DABS_OK;
+}
+
+extern "C" int dabs_server_set_limits(dabs_server* s, int64_t max_warps) {
+  if (!s || max_warps < 0) return DABS_E_INVALID_ARG;
+  s->max_warps = max_warps;
   return DABS_OK;
 }
 

@@ -80,6 +80,7 @@ EXPORTS = {
     "dabs_server_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "dabs_server_poll": (C.c_int, [C.c_void_p, C.c_uint64] + [C.c_void_p] * 5),
     "dabs_server_info": (C.c_int, [C.c_void_p] * 4),
+    "dabs_server_set_limits": (C.c_int, [C.c_void_p, C.c_int64]),
     "dabs_bulk_search_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                            C.c_uint64, C.c_uint32, C.c_int32] + [C.c_void_p] * 9),
 }
@@ -198,6 +199,11 @@ class Server:
         if rc != OK:
             raise DabsError(rc)
         return int(st.value), X, int(e.value), int(f.value), float(lat.value)
+
+    def set_limits(self, max_warps: int):
+        rc = lib().dabs_server_set_limits(self._h, int(max_warps))
+        if rc != OK:
+            raise DabsError(rc)
 
     def info(self):
         u, q, r = C.c_size_t(), C.c_int32(), C.c_int32()

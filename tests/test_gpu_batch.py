@@ -55,6 +55,7 @@ def test_server_equals_alone_and_respects_budget(D):
     params = D.default_params(**kw)
     # a budget that holds about two of the larger contexts at once
     srv = D.Server(hbm_budget_bytes=48 << 20)
+    srv.set_limits(0)  # HBM budget only
     tickets = []
     for k, W in enumerate(Ws[:4]):
         tickets.append(srv.submit(W, params, 10**9, 7 + k))
@@ -79,3 +80,27 @@ def test_server_equals_alone_and_respects_budget(D):
     too_big = np.zeros((8192, 8192), np.int16)
     with pytest.raises(D.DabsError):
         srv.submit(too_big, params, 10, 1)
+
+
+def test_server_warp_cap_serves_in_arrival_order(D):
+    kw = dict(searches=128, pools=2, pool_cap=8, tabu=8, s=(1, 10), b=(1, 1), seed_mode=0,
+              max_generations=3)
+    params = D.default_params(**kw)
+    Ws = [instance(300, k) for k in range(6)]
+    srv = D.Server(hbm_budget_bytes=8 << 30)
+    srv.set_limits(2 * 128)  # two one-warp requests at a time
+    tickets = [srv.submit(W, params, 10**9, 40 + k) for k, W in enumerate(Ws)]
+    order = []
+    while True:
+        pending = srv.step(1)
+        assert srv.info()[2] <= 2
+        for t in tickets:
+            if t not in order and srv.poll(t)[0] == 2:
+                order.append(t)
+        if pending == 0:
+            break
+    assert order == tickets  # equal requests finish in arrival order
+    for k, (t, W) in enumerate(zip(tickets, Ws)):
+        st, X, E, F, _ = srv.poll(t)
+        aX, aE, aF = D.Context(W, **kw).solve(10**9, 40 + k)
+        assert (E, F) == (aE, aF) and np.array_equal(X, aX)
