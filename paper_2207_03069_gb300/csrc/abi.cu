@@ -214,6 +214,18 @@ int check_bits(dabs_ctx* ctx, const uint8_t* X) {
 using namespace dabs_internal;
 
 namespace dabs {
+int spc_for(int slots, int maxspc) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 152;
+  }
+  const int want = (slots + sms - 1) / sms;
+  return std::min(maxspc, std::max(1, want));
+}
+
 bool launch_search(int nw, int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
                    const MultiArgs* m) {
   switch (nw) {

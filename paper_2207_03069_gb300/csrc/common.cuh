@@ -116,6 +116,7 @@ struct SearchArgs {
   int64_t* best_E;   // [S]
   uint32_t* flips;   // [S]
   const int32_t* order; // launch order of the slots (grouped by algorithm), or null
+  int32_t spc;          // searches per CTA actually used (<= the variant's maximum; 0 = maximum)
 };
 
 // Several instances in one batch-search launch: slot q belongs to the

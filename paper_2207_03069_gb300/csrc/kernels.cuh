@@ -85,6 +85,9 @@ __global__ void k_order_by_algo(const uint8_t* algo, int S, int32_t* order, cons
 __global__ void k_copy_targets(const uint32_t* D, uint32_t* X, int64_t* E, size_t words, int S,
                                const DevCtrl* ctrl);
 
+// searches per CTA: spread `slots` searches over the SMs (at most `maxspc` per CTA)
+int spc_for(int slots, int maxspc);
+
 // Batch-search variants: NW warps per search, CH chunks of 8 bits per thread.
 struct SearchVariant {
   int nw, ch, cap, cta, spc;

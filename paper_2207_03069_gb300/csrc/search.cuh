@@ -31,7 +31,7 @@ struct Cfg {
   static constexpr int EPT = 8 * CH;           // bits per thread
   static constexpr int SPAN = 8 * NT;          // bits per chunk
   static constexpr int NMW = (EPT + 31) / 32;  // mask words per thread
-  static constexpr int SPC = NW == 1 ? 4 : 1;  // searches per CTA
+  static constexpr int SPC = NW == 1 ? 8 : 1;  // searches per CTA (at most)
   static constexpr int CTA = NT * SPC;
   static constexpr int CAP = SPAN * CH;        // largest n this variant holds
 };
@@ -726,7 +726,11 @@ __global__ void __launch_bounds__(Cfg<NW, CH>::CTA)
   using C = Cfg<NW, CH>;
   __shared__ SmemSearch<C> smem[C::SPC];
   const int sl = threadIdx.x / C::NT;
-  const uint32_t slot = blockIdx.x * C::SPC + sl;
+  // the launcher may use fewer searches per CTA than the maximum, so that the
+  // CTAs spread over all SMs; the other warps of the CTA leave at once
+  const int spc = single.spc > 0 ? single.spc : C::SPC;
+  if (sl >= spc) return;
+  const uint32_t slot = blockIdx.x * spc + sl;
   // one instance (single) or several (multi: find the slot's instance)
   const SearchArgs* ap = &single;
   uint32_t local = slot;

@@ -15,8 +15,11 @@ bool launch_search_w2(int ch, const SearchArgs* a, cudaStream_t st, SearchVarian
       if (v) *v = SearchVariant{2, 1, C::CAP, C::CTA, C::SPC};
       if (a) {
         const int slots = m ? m->total : a->S;
+        SearchArgs a2 = *a;
+        a2.spc = spc_for(slots, C::SPC);
+        a = &a2;
         if (slots > 0)
-          k_batch_search<2, 1><<<(slots + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(
+          k_batch_search<2, 1><<<(slots + a->spc - 1) / a->spc, C::CTA, 0, st>>>(
               *a, m ? *m : MultiArgs{nullptr, nullptr, 0, 0});
       }
       return true;
@@ -26,8 +29,11 @@ bool launch_search_w2(int ch, const SearchArgs* a, cudaStream_t st, SearchVarian
       if (v) *v = SearchVariant{2, 2, C::CAP, C::CTA, C::SPC};
       if (a) {
         const int slots = m ? m->total : a->S;
+        SearchArgs a2 = *a;
+        a2.spc = spc_for(slots, C::SPC);
+        a = &a2;
         if (slots > 0)
-          k_batch_search<2, 2><<<(slots + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(
+          k_batch_search<2, 2><<<(slots + a->spc - 1) / a->spc, C::CTA, 0, st>>>(
               *a, m ? *m : MultiArgs{nullptr, nullptr, 0, 0});
       }
       return true;
@@ -37,8 +43,11 @@ bool launch_search_w2(int ch, const SearchArgs* a, cudaStream_t st, SearchVarian
       if (v) *v = SearchVariant{2, 4, C::CAP, C::CTA, C::SPC};
       if (a) {
         const int slots = m ? m->total : a->S;
+        SearchArgs a2 = *a;
+        a2.spc = spc_for(slots, C::SPC);
+        a = &a2;
         if (slots > 0)
-          k_batch_search<2, 4><<<(slots + C::SPC - 1) / C::SPC, C::CTA, 0, st>>>(
+          k_batch_search<2, 4><<<(slots + a->spc - 1) / a->spc, C::CTA, 0, st>>>(
               *a, m ? *m : MultiArgs{nullptr, nullptr, 0, 0});
       }
       return true;
