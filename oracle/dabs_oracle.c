@@ -30,8 +30,9 @@
  *      CyclicMin run and each next one starts where the last one ended
  *      (cyclically); argmin over non-tabu bits of the window, ties to the
  *      first bit in cyclic order from the window start.
- *  R8  RandomMin: threshold thr = clamp(cube21(t,T) >> 16, ceil(2^21 / n),
- *      65536); bit k is a candidate iff its 16-bit uniform < thr; argmin of
+ *  R8  RandomMin: threshold thr = clamp(cube21(t,T) >> 24, ceil(2^13 / n),
+ *      256), i.e. p(t) in units of 1/256 with the floor ceil(8192/n)/256 >=
+ *      32/n; bit k is a candidate iff its 8-bit uniform < thr; argmin of
  *      Delta over non-tabu candidates (lowest index on ties); if there is no
  *      candidate, argmin over all non-tabu bits.
  *  R9  PositiveMin: posmin = min Delta > 0 over non-tabu bits; candidates are
@@ -77,7 +78,7 @@
  *      (x, y, z, w):
  *        MaxMin      (flip, g, s, 1<<24)         u0 threshold, u1 pick
  *        PositiveMin (flip, g, s, 2<<24)         u0 pick
- *        RandomMin   (flip, g, s, 3<<24 | k/8)   16-bit word (k%8) of the block
+ *        RandomMin   (flip, g, s, 3<<24 | k/16)  byte (k%16) of the block
  *        choice      (0, g, s, 4<<24)            u0..u3 of R15
  *        parents     (0, g, s, 5<<24)            u0 rank A, u1 rank B, u2/u3 R17
  *        bits        (word, g, s, 6<<24)         R16
@@ -289,7 +290,7 @@ static void main_search(search_run* b, int32_t algo, int32_t T, int32_t tau) {
     uint8_t* cand = (uint8_t*)malloc((size_t)n);
     int32_t win_start = 0;
     const int32_t c_win = n < 32 ? n : 32;
-    const uint32_t c16 = (uint32_t)(((1u << 21) + (uint32_t)n - 1) / (uint32_t)n);
+    const uint32_t c8 = (uint32_t)(((1u << 13) + (uint32_t)n - 1) / (uint32_t)n);
     for (int32_t t = 1; t <= T; ++t) {
         step1(b, &j);
         int32_t i = -1;
@@ -324,14 +325,14 @@ static void main_search(search_run* b, int32_t algo, int32_t T, int32_t tau) {
             }
             win_start = (int32_t)((win_start + (int64_t)w) % n);
         } else if (algo == ORC_RANDOMMIN) {
-            uint64_t thr = orc_cube21((uint64_t)t, (uint64_t)T) >> 16;
-            if (thr < c16) thr = c16;
-            if (thr > 65536) thr = 65536;
+            uint64_t thr = orc_cube21((uint64_t)t, (uint64_t)T) >> 24;
+            if (thr < c8) thr = c8;
+            if (thr > 256) thr = 256;
             for (int32_t k = 0; k < n; ++k) {
                 if (is_tabu(b, k, t, tau)) continue;
-                draw(b->seed, (uint32_t)b->flips, b->g, b->s, (3u << 24) | (uint32_t)(k >> 3), u);
-                uint32_t u16 = (u[(k & 7) >> 1] >> (16 * (k & 1))) & 0xFFFFu;
-                if (u16 < thr && (i < 0 || b->delta[k] < b->delta[i])) i = k;
+                draw(b->seed, (uint32_t)b->flips, b->g, b->s, (3u << 24) | (uint32_t)(k >> 4), u);
+                uint32_t u8 = (u[(k & 15) >> 2] >> (8 * (k & 3))) & 0xFFu;
+                if (u8 < thr && (i < 0 || b->delta[k] < b->delta[i])) i = k;
             }
             if (i < 0)
                 for (int32_t k = 0; k < n; ++k)

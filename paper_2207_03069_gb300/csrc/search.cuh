@@ -195,19 +195,23 @@ struct Searcher {
     Ebest = E + m;
   }
 
-  // Step 3: flip bit i (x_i = xi before the flip, di = Delta_i before the flip)
-  __device__ __forceinline__ void flip(int i, int xi, int di) {
+  // Step 3, in two halves so that independent work can run while row i is in
+  // flight: row_load issues the loads of row i of sigma(x_i) W (x_i = xi
+  // before the flip), row_apply updates E and Delta by Eqs. (4) and (5)
+  // (di = Delta_i before the flip) and flips x_i.
+  __device__ __forceinline__ void row_load(int i, int xi, uint4 (&rv)[CH]) const {
     // every selector yields 0 <= i < n; the clamp only keeps a logic error
     // from turning into an out-of-bounds read (parity tests would flag it)
     i = min(max(i, 0), n - 1);
-    // row i of sigma(x_i) W, so that Eq. (4) is Delta_k += row_k * sigma(x_k)
     const int16_t* row = (xi ? W : Wneg) + (size_t)i * ld;
-    uint4 rv[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
       const int off = c * SPAN + 8 * t;
       rv[c] = off < ld ? __ldg(reinterpret_cast<const uint4*>(row + off)) : make_uint4(0, 0, 0, 0);
     }
+  }
+  __device__ __forceinline__ void row_apply(const uint4 (&rv)[CH], int i, int di) {
+    i = min(max(i, 0), n - 1);
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
 #pragma unroll
@@ -223,6 +227,28 @@ struct Searcher {
     }
     E += di;
     ++flips;
+  }
+
+  // RandomMin draws of one iteration: byte (k % 16) of the Philox block
+  // (flip, g, s, RNG_RANDMIN | k/16) for each owned bit k.  A block covers the
+  // 8-bit runs of two neighbouring lanes; lane pairs split two chunks' blocks
+  // and swap halves, so a lane computes one block per two chunks.
+  __device__ __forceinline__ void randmin_draw(uint32_t flip_idx, uint2 (&r)[CH]) const {
+    const bool odd = t & 1;
+#pragma unroll
+    for (int c = 0; c + 1 < CH; c += 2) {
+      const int cc = odd ? c + 1 : c;
+      const uint4 u = draw(seed, flip_idx, g, s, RNG_RANDMIN | (uint32_t)(cc * (NT / 2) + (t >> 1)));
+      const uint32_t s0 = odd ? u.x : u.z, s1 = odd ? u.y : u.w;
+      const uint32_t g0 = __shfl_xor_sync(FULL, s0, 1), g1 = __shfl_xor_sync(FULL, s1, 1);
+      r[c] = odd ? make_uint2(g0, g1) : make_uint2(u.x, u.y);
+      r[c + 1 < CH ? c + 1 : c] = odd ? make_uint2(u.z, u.w) : make_uint2(g0, g1);
+    }
+    if constexpr (CH & 1) {
+      const int c = CH - 1;
+      const uint4 u = draw(seed, flip_idx, g, s, RNG_RANDMIN | (uint32_t)(c * (NT / 2) + (t >> 1)));
+      r[c] = odd ? make_uint2(u.z, u.w) : make_uint2(u.x, u.y);
+    }
   }
 
   // ------------------------------------------------------------ k-th pick
@@ -417,8 +443,10 @@ struct Searcher {
     uint32_t fup = 0, rup = 0, fdn = 1u << 21;
     int rdn = 0;
     uint32_t rnd0 = 0, rnd1 = 0;  // 32 MaxMin/PositiveMin draws, one per lane
+    uint2 rr[CH];                 // RandomMin draws of the current iteration
+    bool rr_ready = false;
     const int cwin = n < 32 ? n : 32;
-    const uint32_t c16 = ((1u << 21) + (uint32_t)n - 1) / (uint32_t)n;
+    const uint32_t c8 = ((1u << 13) + (uint32_t)n - 1) / (uint32_t)n;
     for (;;) {
       int i = 0, xi = 0, di = 0;
       uint32_t kj = UINT_MAX;
@@ -601,30 +629,38 @@ struct Searcher {
           ws += wsz;
           if (ws >= n) ws -= n;
         } else {  // RANDOMMIN
-          uint32_t thr = (uint32_t)(cube_of(fup) >> 16);
-          thr = thr < c16 ? c16 : (thr > 65536u ? 65536u : thr);
+          uint32_t thr = (uint32_t)(cube_of(fup) >> 24);
+          thr = thr < c8 ? c8 : (thr > 256u ? 256u : thr);
+          if (!rr_ready) randmin_draw(flips, rr);
+          rr_ready = false;
           uint32_t Cm = 0;
 #pragma unroll
-          for (int c = 0; c < CH; ++c) {
-            const uint4 u = draw(seed, flips, g, s, RNG_RANDMIN | (uint32_t)(c * NT + t));
+          for (int c = 0; c < CH; ++c)
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-              const uint32_t u16 = (u32of(u, e >> 1) >> (16 * (e & 1))) & 0xFFFFu;
-              Cm |= (uint32_t)(u16 < thr) << (8 * c + e);
+              const uint32_t u8 = ((e < 4 ? rr[c].x : rr[c].y) >> (8 * (e & 3))) & 0xFFu;
+              Cm |= (uint32_t)(u8 < thr) << (8 * c + e);
             }
-          }
           Cm &= F;
-          int cmc[CH], cmf[CH];
+          int cmc[CH];
           chunk_min(Cm, cmc);
-          chunk_min(F, cmf);
-          int v[3] = {min_of(cma), min_of(cmc), min_of(cmf)};
+          int v[2] = {min_of(cma), min_of(cmc)};
           gmin(v);
           m = v[0];
           improve = E + m < Ebest;
-          const bool have = v[1] != INT_MAX;  // no candidate: argmin over free bits
-          di = have ? v[1] : v[2];
-          uint32_t k[2] = {improve ? warp_key(FULL, cma, m) : UINT_MAX,
-                           have ? warp_key(Cm, cmc, di) : warp_key(F, cmf, di)};
+          uint32_t ks;
+          if (v[1] != INT_MAX) {
+            di = v[1];
+            ks = warp_key(Cm, cmc, di);
+          } else {  // no candidate: argmin over the free bits (rare)
+            int cmf[CH];
+            chunk_min(F, cmf);
+            int vf[1] = {min_of(cmf)};
+            gmin(vf);
+            di = vf[0];
+            ks = warp_key(F, cmf, di);
+          }
+          uint32_t k[2] = {improve ? warp_key(FULL, cma, m) : UINT_MAX, ks};
           gminu(k);
           kj = k[0];
           i = (int)(k[1] >> 1);
@@ -632,14 +668,21 @@ struct Searcher {
         }
       }
       if (improve) take_best(kj, m);
-      flip(i, xi, di);
+      uint4 rv[CH];
+      row_load(i, xi, rv);
+      // independent of row i: overlaps its load latency
       if (phase == PH_MAIN) {
         if (ALGO != TWONEIGHBOR) tabu_push(i, tau);
-        if (++it == Tmain) {
-          phase = PH_GREEDY;
-          ++runs;
-          tb[0] = 0;
+        if (ALGO == RANDOMMIN && it + 1 < Tmain) {
+          randmin_draw(flips + 1, rr);  // draws of the next iteration
+          rr_ready = true;
         }
+      }
+      row_apply(rv, i, di);
+      if (phase == PH_MAIN && ++it == Tmain) {
+        phase = PH_GREEDY;
+        ++runs;
+        tb[0] = 0;
       }
     }
   }
