@@ -332,6 +332,19 @@ def oracle_rate(Wm, spec, seed, seconds, threads):
     return flips / (time.perf_counter() - t0), gens
 
 
+def aggregate(pg, seconds, flips):
+    """Whole-job figures over replicas: the slowest rank's time and the sum of
+    all ranks' flips (host-side gloo reduction; no collective on the data path)."""
+    if pg is None:
+        return seconds, flips
+    import torch
+    t = torch.tensor([seconds, flips], dtype=torch.float64)
+    tmax = t.clone()
+    pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -456,12 +469,7 @@ def main():
     search_ms = [e[1].elapsed_time(e[2]) for e in ev]
     total_s = sum(step_ms) * 1e-3
     flips = st1["flips"] - st0["flips"]
-    if pg:
-        t = torch.tensor([total_s, flips], dtype=torch.float64)
-        tmax = t.clone()
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-        pg.all_reduce(t, op=pg.ReduceOp.SUM)
-        total_s, flips = float(tmax[0]), float(t[1])
+    total_s, flips = aggregate(pg, total_s, flips)
     value = flips / total_s
     flips_rank = st1["flips"] - st0["flips"]
 
