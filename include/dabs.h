@@ -44,7 +44,7 @@ extern "C" {
 #define DABS_E_BUSY (-7)         /* the context is in a state that forbids it   */
 #define DABS_E_NO_DEVICE (-8)    /* no CUDA device of compute capability 10.3   */
 
-#define DABS_N_MAX 8192          /* largest n of the register-resident search   */
+#define DABS_N_MAX 16384         /* largest n of the register-resident search   */
 
 enum { DABS_MAXMIN = 0, DABS_CYCLICMIN = 1, DABS_RANDOMMIN = 2, DABS_POSITIVEMIN = 3,
        DABS_TWONEIGHBOR = 4 };
@@ -235,9 +235,9 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
  * (results never depend on the variant).
  * table (may be NULL) receives DABS_N_VARIANTS nanoseconds-per-flip entries
  * in the order (warps x chunks) 1x1 1x2 1x4 2x1 2x2 2x4 4x1 4x2 4x4 8x1 8x2
- * 8x4 16x1 16x2, 0 where a variant cannot hold n.  Resets the solve state;
+ * 8x4 16x1 16x2 16x4, 0 where a variant cannot hold n.  Resets the solve state;
  * call before dabs_solve_begin.  Synchronous. */
-#define DABS_N_VARIANTS 14
+#define DABS_N_VARIANTS 15
 int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* chunks,
                   float* ns_per_flip, float* table);
 /* Current pools (the ones the next generation breeds from): X [P][C][words],

@@ -47,7 +47,7 @@ bool params_ok(const dabs_params* p) {
 }
 
 bool default_variant(int n, SearchVariant* v) {
-  static const int order[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 4}, {4, 4}, {8, 4}};
+  static const int order[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 4}, {4, 4}, {8, 4}, {16, 4}};
   for (auto& o : order) {
     SearchVariant q;
     if (launch_search(o[0], o[1], nullptr, nullptr, &q) && q.cap >= n) {
@@ -551,7 +551,7 @@ int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* c
   if (!ctx || generations < 1) return DABS_E_INVALID_ARG;
   static const int cand[DABS_N_VARIANTS][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4},
                                                {4, 1}, {4, 2}, {4, 4}, {8, 1}, {8, 2}, {8, 4},
-                                               {16, 1}, {16, 2}};
+                                               {16, 1}, {16, 2}, {16, 4}};
   if (table)
     for (int q = 0; q < DABS_N_VARIANTS; ++q) table[q] = 0.f;
   // warm a throwaway solve for `generations` generations, breed the next

@@ -764,7 +764,7 @@ struct Searcher {
 };
 
 template <int NW, int CH>
-__global__ void __launch_bounds__(Cfg<NW, CH>::CTA)
+__global__ void __launch_bounds__(Cfg<NW, CH>::CTA, 1)
     k_batch_search(const SearchArgs single, const MultiArgs multi) {
   using C = Cfg<NW, CH>;
   __shared__ SmemSearch<C> smem[C::SPC];

@@ -38,6 +38,20 @@ bool launch_search_w16(int ch, const SearchArgs* a, cudaStream_t st, SearchVaria
       }
       return true;
     }
+    case 4: {
+      using C = Cfg<16, 4>;
+      if (v) *v = SearchVariant{16, 4, C::CAP, C::CTA, C::SPC};
+      if (a) {
+        const int slots = m ? m->total : a->S;
+        SearchArgs a2 = *a;
+        a2.spc = spc_for(slots, C::SPC);
+        a = &a2;
+        if (slots > 0)
+          k_batch_search<16, 4><<<(slots + a->spc - 1) / a->spc, C::CTA, 0, st>>>(
+              *a, m ? *m : MultiArgs{nullptr, nullptr, 0, 0});
+      }
+      return true;
+    }
     default: return false;
   }
 }

@@ -20,7 +20,7 @@ _lib = None
 
 OK, E_INVALID_ARG, E_NOT_SYMMETRIC, E_TOO_LARGE, E_OOM, E_TIMEOUT, E_CUDA, E_BUSY, E_NO_DEVICE = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
-N_MAX = 8192
+N_MAX = 16384
 INT64_MAX = np.iinfo(np.int64).max
 INT64_MIN = np.iinfo(np.int64).min
 STAGE_OFFSPRING, STAGE_SEARCH, STAGE_MERGE, STAGE_FINALIZE = range(4)
@@ -269,7 +269,7 @@ class Context:
         self._ck(lib().dabs_set_variant(self._h, warps, chunks))
 
     VARIANTS = ((1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (4, 1), (4, 2), (4, 4), (8, 1),
-                (8, 2), (8, 4), (16, 1), (16, 2))
+                (8, 2), (8, 4), (16, 1), (16, 2), (16, 4))
 
     def autotune(self, generations: int = 2):
         """Picks the fastest batch-search variant; resets the solve state.

@@ -121,7 +121,8 @@ def test_bulk_search_matches_oracle(D, orc, n):
 
 
 @pytest.mark.parametrize("variant", [(1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (4, 1),
-                                     (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (16, 1), (16, 2)])
+                                     (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (16, 1), (16, 2),
+                                     (16, 4)])
 def test_every_variant_matches_oracle(D, orc, variant):
     nw, ch = variant
     cap = 256 * nw * ch
