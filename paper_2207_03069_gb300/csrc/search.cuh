@@ -302,13 +302,13 @@ struct Searcher {
 #pragma unroll
       for (int c = 0; c < CH; ++c)
         if (c == csel) mycnt = cnt[c];
-      int incl = mycnt;
+      // exclusive prefix of the per-lane counts (0..8) from four bit-sliced
+      // ballots: independent votes instead of a serial shuffle scan
+      const unsigned below = (1u << lane) - 1u;
+      int excl = 0;
 #pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(FULL, incl, off);
-        if (lane >= off) incl += y;
-      }
-      const int excl = incl - mycnt;
+      for (int b = 0; b < 4; ++b) excl += __popc(__ballot_sync(FULL, (mycnt >> b) & 1) & below) << b;
+      const int incl = excl + mycnt;
       const bool mine = excl <= rel && rel < incl;
       uint32_t byte = (Cm >> (8 * csel)) & 0xFFu;
       for (int r = rel - excl; r > 0 && byte; --r) byte &= byte - 1;  // drop r lowest set bits
@@ -406,25 +406,26 @@ struct Searcher {
   // key (k << 1 | x_k) of this warp's lowest bit k in M with d == target, found
   // chunk by chunk with a ballot over the chunk minima (UINT_MAX if none)
   __device__ __forceinline__ uint32_t warp_key(uint32_t M, const int (&cm)[CH], int target) const {
-    uint32_t key = UINT_MAX;
-    bool found = false;
+    // all chunk ballots at once (independent), then the first chunk that has one
+    unsigned bal[CH];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      if (!found) {
-        const unsigned bal = __ballot_sync(FULL, cm[c] == target);
-        if (bal) {
-          found = true;
-          int e0 = 0;
+    for (int c = 0; c < CH; ++c) bal[c] = __ballot_sync(FULL, cm[c] == target);
+    int csel = -1;
+    unsigned b = 0;
 #pragma unroll
-          for (int e = 7; e >= 0; --e)
-            if (((M >> (8 * c + e)) & 1u) && d[8 * c + e] == target) e0 = e;
-          const int p = 8 * c + e0;
-          const uint32_t kk = ((uint32_t)kidx(p) << 1) | ((xb[0] >> p) & 1u);
-          key = __shfl_sync(FULL, kk, __ffs(bal) - 1);
-        }
-      }
-    }
-    return key;
+    for (int c = CH - 1; c >= 0; --c)
+      if (bal[c]) { csel = c; b = bal[c]; }
+    if (csel < 0) return UINT_MAX;
+    uint32_t mm = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+      if (c == csel)
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          mm |= (uint32_t)(((M >> (8 * c + e)) & 1u) && d[8 * c + e] == target) << e;
+    const int p = 8 * csel + (mm ? __ffs(mm) - 1 : 0);
+    const uint32_t kk = ((uint32_t)kidx(p) << 1) | ((xb[0] >> p) & 1u);
+    return __shfl_sync(FULL, kk, __ffs(b) - 1);
   }
 
   // ------------------------------------------------------------ the batch search
