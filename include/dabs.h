@@ -240,6 +240,20 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
 #define DABS_N_VARIANTS 15
 int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* chunks,
                   float* ns_per_flip, float* table);
+/* Counters of the running solve (the paper's Tables V and VI): runs of each
+ * main algorithm (DABS_MAXMIN..) and uses of each genetic operation
+ * (DABS_MUTATION..) over all searches and generations, and the algorithm and
+ * operation of every result that improved the global best.  Any pointer may
+ * be NULL; arrays of 5 and 8 entries.  Synchronous. */
+int dabs_read_stats(dabs_ctx* ctx, uint64_t* algo_count, uint64_t* op_count, uint64_t* best_algo,
+                    uint64_t* best_op);
+/* Checkpoint of a solve at a generation boundary: pools, per-search state,
+ * global best, counters and the control block, into a host buffer (call with
+ * buf = NULL to learn *size).  dabs_restore loads it into a context created
+ * with the same W, n and parameters; the solve then continues exactly as the
+ * original would have.  Synchronous. */
+int dabs_checkpoint(dabs_ctx* ctx, void* buf, size_t cap, size_t* size);
+int dabs_restore(dabs_ctx* ctx, const void* buf, size_t size);
 /* Current pools (the ones the next generation breeds from): X [P][C][words],
  * E [P][C], algo [P][C], op [P][C].  Any pointer may be NULL. */
 int dabs_read_pools(dabs_ctx* ctx, uint32_t* X, int64_t* E, uint8_t* algo, uint8_t* op);

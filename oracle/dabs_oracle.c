@@ -74,6 +74,10 @@
  *  R20 Global best: first result (generation, then search order) with the
  *      lowest energy.  A solve stops at the first generation boundary with
  *      total flips >= budget, best E <= target or generations == limit.
+ *  R22 Statistics (Tables V and VI): per generation, every search counts its
+ *      main algorithm and genetic operation; a generation whose best result
+ *      improves the global best credits that result's algorithm and operation
+ *      (the first finder).
  *  R21 Random numbers: Philox4x32-10 keyed by (seed lo, seed hi) with counter
  *      (x, y, z, w):
  *        MaxMin      (flip, g, s, 1<<24)         u0 threshold, u1 pick
@@ -430,6 +434,8 @@ struct orc_solver {
     int64_t gbest_E;
     uint64_t flips_total;
     uint32_t g;
+    uint64_t algo_count[ORC_N_ALGOS], op_count[ORC_N_OPS];
+    uint64_t best_algo[ORC_N_ALGOS], best_op[ORC_N_OPS];
 };
 
 static int nibble(const uint32_t u[4], int32_t j) { return (int)((u[j >> 3] >> (4 * (j & 7))) & 0xFu); }
@@ -559,11 +565,20 @@ void orc_pool_merge(orc_solver* so, const uint8_t* best_X, const int64_t* best_E
                     const int32_t* algo, const int32_t* op) {
     for (uint32_t s = 0; s < (uint32_t)so->S; ++s)
         pool_insert(so, s % (uint32_t)so->P, best_X + (size_t)s * so->n, best_E[s], algo[s], op[s]);
-    for (uint32_t s = 0; s < (uint32_t)so->S; ++s)
+    int32_t winner = -1;
+    for (uint32_t s = 0; s < (uint32_t)so->S; ++s) {
+        so->algo_count[algo[s]] += 1;
+        so->op_count[op[s]] += 1;
         if (best_E[s] < so->gbest_E) {
             so->gbest_E = best_E[s];
             memcpy(so->gbest_X, best_X + (size_t)s * so->n, (size_t)so->n);
+            winner = (int32_t)s;
         }
+    }
+    if (winner >= 0) { /* Table VI: the finder of the new global best */
+        so->best_algo[algo[winner]] += 1;
+        so->best_op[op[winner]] += 1;
+    }
 }
 
 typedef struct {
@@ -639,6 +654,14 @@ void orc_solver_get_results(const orc_solver* so, uint8_t* best_X, int64_t* best
     if (flips) memcpy(flips, so->res_flips, S * sizeof(uint64_t));
     if (algo) memcpy(algo, so->algo, S * sizeof(int32_t));
     if (op) memcpy(op, so->op, S * sizeof(int32_t));
+}
+
+void orc_solver_get_stats(const orc_solver* so, uint64_t* algo_count, uint64_t* op_count,
+                          uint64_t* best_algo, uint64_t* best_op) {
+    memcpy(algo_count, so->algo_count, sizeof so->algo_count);
+    memcpy(op_count, so->op_count, sizeof so->op_count);
+    memcpy(best_algo, so->best_algo, sizeof so->best_algo);
+    memcpy(best_op, so->best_op, sizeof so->best_op);
 }
 
 void orc_solver_get_best(const orc_solver* so, uint8_t* X, int64_t* E, uint64_t* flips_total,

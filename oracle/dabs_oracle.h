@@ -78,6 +78,10 @@ void        orc_solver_get_results(const orc_solver* so, uint8_t* best_X, int64_
                                    uint64_t* flips, int32_t* algo, int32_t* op);
 void        orc_solver_get_best(const orc_solver* so, uint8_t* X, int64_t* E,
                                 uint64_t* flips_total, uint32_t* generations);
+/* Tables V/VI counters: per-search algorithm/operation counts and the
+ * algorithm/operation of each result that improved the global best */
+void        orc_solver_get_stats(const orc_solver* so, uint64_t* algo_count, uint64_t* op_count,
+                                 uint64_t* best_algo, uint64_t* best_op);
 /* merges externally given results into the pools (Section IV, packets) */
 void        orc_pool_merge(orc_solver* so, const uint8_t* best_X, const int64_t* best_E,
                            const int32_t* algo, const int32_t* op);

@@ -87,6 +87,7 @@ def lib():
         L.orc_solver_get_results.argtypes = [C.c_void_p, u8p, i64p, u64p, i32p, i32p]
         L.orc_solver_get_best.argtypes = [C.c_void_p, u8p, i64p, u64p, u32p]
         L.orc_pool_merge.argtypes = [C.c_void_p, u8p, i64p, i32p, i32p]
+        L.orc_solver_get_stats.argtypes = [C.c_void_p, u64p, u64p, u64p, u64p]
         L.orc_solve.restype = C.c_int
         L.orc_solve.argtypes = [i16p, C.c_int32, P(Params), C.c_uint64, C.c_uint64, C.c_int64,
                                 C.c_int32, u8p, i64p, u64p, u32p]
@@ -232,6 +233,14 @@ class Solver:
         o = np.ascontiguousarray(op, np.int32)
         lib().orc_pool_merge(self._h, _p(bX, C.c_uint8), _p(bE, C.c_int64), _p(a, C.c_int32),
                              _p(o, C.c_int32))
+
+    def stats(self):
+        """(algo counts [5], op counts [8], first-finder algo [5], first-finder op [8])"""
+        a, o, ba, bo = (np.zeros(5, np.uint64), np.zeros(8, np.uint64), np.zeros(5, np.uint64),
+                        np.zeros(8, np.uint64))
+        lib().orc_solver_get_stats(self._h, _p(a, C.c_uint64), _p(o, C.c_uint64),
+                                   _p(ba, C.c_uint64), _p(bo, C.c_uint64))
+        return a, o, ba, bo
 
     def best(self):
         X = np.zeros(self.n, np.uint8)

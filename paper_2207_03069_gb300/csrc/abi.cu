@@ -78,6 +78,9 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
     }
     dg[i] = W[(size_t)i * n + i];
   }
+  uint64_t h = 1469598103934665603ull;  // FNV-1a of W, ties checkpoints to their instance
+  for (size_t q = 0; q < (size_t)n * n; ++q) h = (h ^ (uint16_t)W[q]) * 1099511628211ull;
+  ctx->w_hash = h;
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaMemcpy(ctx->W, pad.data(), pad.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->Wneg, neg.data(), neg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
@@ -187,7 +190,8 @@ int stage(dabs_ctx* ctx, int which) {
     k_merge<<<ctx->P, kMergeThreads, ctx->merge_smem, st>>>(m);
     CKLAUNCH();
   } else if (which == 3) {
-    FinArgs f{ctx->nw, ctx->S, ctx->ctrl, ctx->bestX, ctx->bestE, ctx->flips, ctx->gbestX};
+    FinArgs f{ctx->nw, ctx->S, ctx->ctrl, ctx->bestX, ctx->bestE, ctx->flips, ctx->gbestX,
+              ctx->algo, ctx->op, ctx->stats};
     k_finalize<<<1, 1024, 0, st>>>(f);
     CKLAUNCH();
   } else {
@@ -333,6 +337,7 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
   TRY(dalloc(ctx, &ctx->flips, S));
   TRY(dalloc(ctx, &ctx->order, S));
   TRY(dalloc(ctx, &ctx->gbestX, nw));
+  TRY(dalloc(ctx, &ctx->stats, kStats));
   TRY(dalloc(ctx, &ctx->one_X, nw));
   TRY(dalloc(ctx, &ctx->one_d, ld));
   TRY(dalloc(ctx, &ctx->one_E, 1));
@@ -422,6 +427,7 @@ int dabs_solve_begin(dabs_ctx* ctx, uint64_t seed, uint64_t budget, int64_t targ
   c.best_E = INT64_MAX;
   *ctx->h_ctrl = c;
   CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * kStats, ctx->stream));
   StateArgs s{ctx->n, ctx->ld, ctx->nw, ctx->S, ctx->diag, ctx->X, ctx->delta, ctx->E, ctx->gbestX};
   k_state_init<<<304, 256, 0, ctx->stream>>>(s);
   CKLAUNCH();
@@ -645,6 +651,99 @@ int dabs_kernel_status(dabs_ctx* ctx) {
   if (e) {
     CK(cudaMemset(ctx->kerr, 0, sizeof(int)));
     return fail(ctx, DABS_E_TIMEOUT, "a device wait ran out (kernel error %d)", e);
+  }
+  return DABS_OK;
+}
+
+int dabs_read_stats(dabs_ctx* ctx, uint64_t* algo_count, uint64_t* op_count, uint64_t* best_algo,
+                    uint64_t* best_op) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  unsigned long long h[kStats];
+  CK(cudaMemcpy(h, ctx->stats, sizeof h, cudaMemcpyDeviceToHost));
+  for (int q = 0; q < N_ALGOS; ++q) {
+    if (algo_count) algo_count[q] = h[q];
+    if (best_algo) best_algo[q] = h[N_ALGOS + N_OPS + q];
+  }
+  for (int q = 0; q < N_OPS; ++q) {
+    if (op_count) op_count[q] = h[N_ALGOS + q];
+    if (best_op) best_op[q] = h[2 * N_ALGOS + N_OPS + q];
+  }
+  return DABS_OK;
+}
+
+// ---- checkpoint / restore: the whole device state of a solve at a
+// generation boundary (pools, per-search state, global best, counters)
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version, n, S, P, C, pad;
+  dabs_params p;
+  uint64_t w_hash, bytes;
+};
+struct Piece {
+  void* ptr;
+  size_t bytes;
+};
+std::vector<Piece> ckpt_pieces(dabs_ctx* c) {
+  const size_t S = c->S, PC = (size_t)c->P * c->C, nw = c->nw, ld = c->ld;
+  std::vector<Piece> v = {{c->ctrl, sizeof(DevCtrl)}, {c->X, S * nw * 4}, {c->delta, S * ld * 4},
+                          {c->E, S * 8}, {c->D, S * nw * 4}, {c->bestX, S * nw * 4}, {c->bestE, S * 8},
+                          {c->flips, S * 4}, {c->algo, S}, {c->op, S}, {c->gbestX, nw * 4},
+                          {c->stats, sizeof(unsigned long long) * kStats}};
+  for (int b = 0; b < 2; ++b) {
+    v.push_back({c->poolX[b], PC * nw * 4});
+    v.push_back({c->poolE[b], PC * 8});
+    v.push_back({c->poolA[b], PC});
+    v.push_back({c->poolO[b], PC});
+  }
+  return v;
+}
+}  // namespace
+
+int dabs_checkpoint(dabs_ctx* ctx, void* buf, size_t cap, size_t* size) {
+  if (!ctx || !size) return DABS_E_INVALID_ARG;
+  const auto pieces = ckpt_pieces(ctx);
+  size_t total = sizeof(CkptHeader);
+  for (auto& q : pieces) total += q.bytes;
+  *size = total;
+  if (!buf) return DABS_OK;
+  if (cap < total) return fail(ctx, DABS_E_INVALID_ARG, "checkpoint buffer of %zu < %zu bytes", cap, total);
+  CK(cudaStreamSynchronize(ctx->stream));
+  CkptHeader h{};
+  memcpy(h.magic, "DABSCKP1", 8);
+  h.version = 1;
+  h.n = ctx->n; h.S = ctx->S; h.P = ctx->P; h.C = ctx->C;
+  h.p = ctx->p;
+  h.w_hash = ctx->w_hash;
+  h.bytes = total;
+  unsigned char* o = static_cast<unsigned char*>(buf);
+  memcpy(o, &h, sizeof h);
+  o += sizeof h;
+  for (auto& q : pieces) {
+    CK(cudaMemcpy(o, q.ptr, q.bytes, cudaMemcpyDeviceToHost));
+    o += q.bytes;
+  }
+  return DABS_OK;
+}
+
+int dabs_restore(dabs_ctx* ctx, const void* buf, size_t size) {
+  if (!ctx || !buf || size < sizeof(CkptHeader)) return DABS_E_INVALID_ARG;
+  CkptHeader h;
+  memcpy(&h, buf, sizeof h);
+  if (memcmp(h.magic, "DABSCKP1", 8) != 0 || h.version != 1 || h.bytes != size || h.n != ctx->n ||
+      h.S != ctx->S || h.P != ctx->P || h.C != ctx->C || h.w_hash != ctx->w_hash ||
+      memcmp(&h.p, &ctx->p, sizeof h.p) != 0)
+    return fail(ctx, DABS_E_INVALID_ARG, "checkpoint does not match this context");
+  const auto pieces = ckpt_pieces(ctx);
+  size_t total = sizeof h;
+  for (auto& q : pieces) total += q.bytes;
+  if (total != size) return fail(ctx, DABS_E_INVALID_ARG, "checkpoint size mismatch");
+  CK(cudaStreamSynchronize(ctx->stream));
+  const unsigned char* in = static_cast<const unsigned char*>(buf) + sizeof h;
+  for (auto& q : pieces) {
+    CK(cudaMemcpy(q.ptr, in, q.bytes, cudaMemcpyHostToDevice));
+    in += q.bytes;
   }
   return DABS_OK;
 }

@@ -17,6 +17,7 @@ struct dabs_ctx {
   int dev = 0;
   int n = 0, ld = 0, nw = 0;
   dabs_params p{};
+  uint64_t w_hash = 0;  // FNV-1a of the host W
   int T = 1, tau = 0;
   uint32_t B = 1;
   int S = 0, P = 0, C = 0, Mmax = 1;
@@ -43,6 +44,7 @@ struct dabs_ctx {
   uint32_t* flips = nullptr;
   int32_t* order = nullptr;   // slot launch order grouped by algorithm
   uint32_t* gbestX = nullptr;
+  unsigned long long* stats = nullptr;  // [kStats] Tables V/VI counters
   uint32_t* one_X = nullptr;   // single-vector scratch for dabs_energy / dabs_delta
   int32_t* one_d = nullptr;
   int64_t* one_E = nullptr;

@@ -294,7 +294,15 @@ __global__ void __launch_bounds__(1024) k_finalize(const FinArgs a) {
   __shared__ int64_t sbestE[32];
   __shared__ int sbestS[32];
   __shared__ int winner;
+  __shared__ unsigned long long cnt[kStats];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid < kStats) cnt[tid] = 0;
+  __syncthreads();
+  if (a.stats)  // Table V: main algorithm and genetic operation of every search
+    for (int s = tid; s < a.S; s += blockDim.x) {
+      atomicAdd(&cnt[min((int)a.algo[s], N_ALGOS - 1)], 1ull);
+      atomicAdd(&cnt[N_ALGOS + min((int)a.op[s], N_OPS - 1)], 1ull);
+    }
   uint64_t f = 0;
   int64_t be = INT64_MAX;
   int bs = INT_MAX;
@@ -331,7 +339,12 @@ __global__ void __launch_bounds__(1024) k_finalize(const FinArgs a) {
   __syncthreads();
   if (winner >= 0)
     for (int w = tid; w < a.nw; w += blockDim.x) a.gbest_X[w] = a.best_X[(size_t)winner * a.nw + w];
+  if (a.stats && tid == 0 && winner >= 0) {  // Table VI: the finder of the new global best
+    cnt[N_ALGOS + N_OPS + min((int)a.algo[winner], N_ALGOS - 1)] += 1;
+    cnt[2 * N_ALGOS + N_OPS + min((int)a.op[winner], N_OPS - 1)] += 1;
+  }
   __syncthreads();
+  if (a.stats && tid < kStats && cnt[tid]) a.stats[tid] += cnt[tid];
   if (tid == 0) {
     const bool stop = ctrl->flips_total >= ctrl->budget || ctrl->best_E <= ctrl->target ||
                       (ctrl->max_generations > 0 && ctrl->g >= ctrl->max_generations);

@@ -56,6 +56,10 @@ struct MergeArgs {
   const uint8_t* op;
 };
 
+// statistics counters (Tables V and VI): [0,5) algorithm runs, [5,13) operation
+// uses, [13,18) algorithm of each new global best, [18,26) its operation
+constexpr int kStats = 26;
+
 struct FinArgs {
   int nw, S;
   DevCtrl* ctrl;
@@ -63,6 +67,9 @@ struct FinArgs {
   const int64_t* best_E;
   const uint32_t* flips;
   uint32_t* gbest_X;
+  const uint8_t* algo;
+  const uint8_t* op;
+  unsigned long long* stats;  // [kStats]
 };
 
 struct EDArgs {

@@ -68,6 +68,9 @@ EXPORTS = {
     "dabs_read_generation": (C.c_int, [C.c_void_p] * 7),
     "dabs_write_results": (C.c_int, [C.c_void_p] * 6),
     "dabs_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
+    "dabs_read_stats": (C.c_int, [C.c_void_p] * 5),
+    "dabs_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "dabs_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "dabs_recompute_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                      C.c_int32]),
     "dabs_set_recompute": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -392,6 +395,24 @@ class Context:
         self._ck(lib().dabs_read_generation(self._h, _ptr(D), _ptr(a), _ptr(o), _ptr(bX),
                                             _ptr(bE), _ptr(f)))
         return D, a, o, bX, bE, f
+
+    def stats(self):
+        """(algo counts [5], op counts [8], first-finder algo [5], first-finder op [8])"""
+        a, o, ba, bo = (np.zeros(5, np.uint64), np.zeros(8, np.uint64), np.zeros(5, np.uint64),
+                        np.zeros(8, np.uint64))
+        self._ck(lib().dabs_read_stats(self._h, _ptr(a), _ptr(o), _ptr(ba), _ptr(bo)))
+        return a, o, ba, bo
+
+    def checkpoint(self) -> bytes:
+        size = C.c_size_t()
+        self._ck(lib().dabs_checkpoint(self._h, None, 0, C.byref(size)))
+        buf = np.zeros(size.value, np.uint8)
+        self._ck(lib().dabs_checkpoint(self._h, _ptr(buf), size.value, C.byref(size)))
+        return buf.tobytes()
+
+    def restore(self, blob: bytes):
+        buf = np.frombuffer(blob, np.uint8).copy()
+        self._ck(lib().dabs_restore(self._h, _ptr(buf), buf.size))
 
     def write_results(self, best_X, best_E, flips, algo, op):
         args = [np.ascontiguousarray(best_X, np.uint32), np.ascontiguousarray(best_E, np.int64),

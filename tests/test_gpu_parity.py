@@ -190,6 +190,44 @@ def test_generations_match_oracle(D, orc, n, S, P, C, seed_mode):
     assert (st["best_E"], st["flips"], st["generations"]) == (be, bf, bg)
     gx, ge = ctx.solve_best()
     assert ge == be and np.array_equal(gx, bx)
+    # Tables V/VI counters
+    for got, want in zip(ctx.stats(), so.stats()):
+        assert np.array_equal(got, want)
+
+
+def test_checkpoint_restore_continues_exactly(D, orc):
+    n, S = 90, 48
+    W = wl.dense_qubo(n, -100, 100, seed=6)
+    kw = dict(searches=S, pools=3, pool_cap=16, tabu=8, s=(1, 10), b=(1, 1), seed_mode=0)
+    a = D.Context(W, **kw)
+    a.solve_begin(4)
+    a.solve_generations(3)
+    blob = a.checkpoint()
+    a.solve_generations(4)
+    want = (a.read_pools(), a.read_state(), a.solve_status(), a.solve_best(), a.stats())
+    b = D.Context(W, **kw)
+    b.solve_begin(99)  # a different solve in flight; the restore replaces all of it
+    b.solve_generations(1)
+    b.restore(blob)
+    b.solve_generations(4)
+    got = (b.read_pools(), b.read_state(), b.solve_status(), b.solve_best(), b.stats())
+    assert got[2] == want[2]
+    for g, w in zip(got[0] + got[1] + got[3] + got[4], want[0] + want[1] + want[3] + want[4]):
+        assert np.array_equal(np.asarray(g), np.asarray(w))
+    # the oracle, run straight through, agrees with the restored continuation
+    so = orc.Solver(W, orc.make_params(**kw), 4)
+    for _ in range(7):
+        so.generation()
+    bx, be, bf, bg = so.best()
+    assert (got[2]["best_E"], got[2]["flips"], got[2]["generations"]) == (be, bf, bg)
+    # a checkpoint only restores into a context of the same instance and parameters
+    with pytest.raises(D.DabsError):
+        D.Context(W, **dict(kw, tabu=9)).restore(blob)
+    W2 = W.copy(); W2[0, 1] += 1; W2[1, 0] += 1
+    with pytest.raises(D.DabsError):
+        D.Context(W2, **kw).restore(blob)
+    with pytest.raises(D.DabsError):
+        b.restore(blob[:-1])
 
 
 def test_offspring_and_merge_on_crafted_pools(D, orc):

@@ -206,3 +206,20 @@ def test_solver_budget_and_target_stop(orc):
     assert f < 10000
     X2, E2, _, g2 = orc.solve(W, p, budget=2**63, seed=4, target=E)
     assert E2 <= E and g2 <= gens
+
+
+def test_statistics_count_every_search_and_each_new_best(orc):
+    """Tables V/VI counters: one algorithm and one operation count per search
+    per generation; first-finder credits only on improvements of the best."""
+    W = wl.dense_qubo(48, -100, 100, 3)
+    S, G = 24, 7
+    so = orc.Solver(W, orc.make_params(searches=S, pools=3, pool_cap=8), seed=2)
+    bests, improvements = [], 0
+    for g in range(G):
+        so.generation()
+        X, E, f, a, o = so.results()
+        bests.append(so.best()[1])
+    improvements = sum(1 for g in range(G) if g == 0 or bests[g] < bests[g - 1])
+    ac, oc, ba, bo = so.stats()
+    assert ac.sum() == S * G and oc.sum() == S * G
+    assert ba.sum() == improvements and bo.sum() == improvements
