@@ -86,9 +86,23 @@
  *        choice      (0, g, s, 4<<24)            u0..u3 of R15
  *        parents     (0, g, s, 5<<24)            u0 rank A, u1 rank B, u2/u3 R17
  *        bits        (word, g, s, 6<<24)         R16
- *        pool init   (word, entry, pool, 7<<24)  bit 0 of each nibble
- *        pool tags   (0, entry, pool, 8<<24)     algo (u0*5)>>32, op (u1*8)>>32
- *      where flip is the number of flips already made in the batch search.
+ *        pool init   (word, entry, pool, 7<<24 | r)  bit 0 of each nibble
+ *        pool tags   (0, entry, pool, 8<<24 | r)     algo (u0*5)>>32, op (u1*8)>>32
+ *      where flip is the number of flips already made in the batch search and
+ *      r the number of restarts so far (R23).
+ *  R23 Restart (Section IV-B, last paragraph): "all pools merged" is read as
+ *      every entry of every pool lying within Hamming distance h (a parameter)
+ *      of the global best.  Tested after each generation's merge and global
+ *      best update (when restarts are enabled); if it holds, r += 1, every pool
+ *      is drawn afresh as at the start with epoch r, and every search restarts
+ *      from X = 0, E = 0, Delta = diag.  The global best, the flip count, the
+ *      generation index and the statistics carry on.
+ *  R24 ABS mode (Section I, the earlier Adaptive Bulk Search): every search
+ *      runs CyclicMin and every target is a mutation after a crossover of
+ *      two parents of its own pool (ranks as R14).  Per bit, with the bits
+ *      draw of R16: coin = bit 3 of the nibble picks parent B, then the bit
+ *      is inverted iff its low three bits are 0.  The result is recorded as
+ *      a Crossover for R22.
  */
 #include "dabs_oracle.h"
 
@@ -436,9 +450,50 @@ struct orc_solver {
     uint32_t g;
     uint64_t algo_count[ORC_N_ALGOS], op_count[ORC_N_OPS];
     uint64_t best_algo[ORC_N_ALGOS], best_op[ORC_N_OPS];
+    uint32_t restarts;
 };
 
 static int nibble(const uint32_t u[4], int32_t j) { return (int)((u[j >> 3] >> (4 * (j & 7))) & 0xFu); }
+
+/* Section III-B: every search starts at X = 0, E = 0, Delta_k = W_kk. */
+static void reset_searches(orc_solver* so) {
+    const size_t S = (size_t)so->S, N = (size_t)so->n;
+    memset(so->X, 0, S * N);
+    memset(so->E, 0, S * sizeof(int64_t));
+    for (size_t s = 0; s < S; ++s)
+        for (int32_t k = 0; k < so->n; ++k) so->delta[s * N + k] = so->W[(int64_t)k * so->n + k];
+}
+
+/* Section IV-A: random vectors with +infinity energy, random fields; the
+ * epoch r separates the draws of each restart (R23). */
+static void init_pools(orc_solver* so, uint32_t r) {
+    const int32_t n = so->n;
+    const size_t C = (size_t)so->C, N = (size_t)n;
+    for (uint32_t pp = 0; pp < (uint32_t)so->P; ++pp)
+        for (uint32_t e = 0; e < (uint32_t)C; ++e) {
+            uint8_t* x = so->pool_X + ((size_t)pp * C + e) * N;
+            uint32_t u[4];
+            for (int32_t k = 0; k < n; ++k) {
+                draw(so->seed, (uint32_t)(k >> 5), e, pp, (7u << 24) | r, u);
+                x[k] = (uint8_t)(nibble(u, k & 31) & 1);
+            }
+            so->pool_E[pp * C + e] = INT64_MAX;
+            draw(so->seed, 0, e, pp, (8u << 24) | r, u);
+            so->pool_algo[pp * C + e] = (int32_t)uidx(u[0], ORC_N_ALGOS);
+            so->pool_op[pp * C + e] = (int32_t)uidx(u[1], ORC_N_OPS);
+        }
+}
+
+/* R23: all pools merged around the global best? */
+static int pools_merged(const orc_solver* so) {
+    const size_t PC = (size_t)so->P * so->C, N = (size_t)so->n;
+    for (size_t q = 0; q < PC; ++q) {
+        int64_t d = 0;
+        for (size_t k = 0; k < N; ++k) d += so->pool_X[q * N + k] != so->gbest_X[k];
+        if (d > so->p.restart_dist) return 0;
+    }
+    return 1;
+}
 
 orc_solver* orc_solver_create(const int16_t* W, int32_t n, const orc_params* p, uint64_t seed) {
     orc_solver* so = (orc_solver*)calloc(1, sizeof *so);
@@ -463,23 +518,8 @@ orc_solver* orc_solver_create(const int16_t* W, int32_t n, const orc_params* p, 
     so->res_flips = (uint64_t*)calloc(S, sizeof(uint64_t));
     so->gbest_X = (uint8_t*)calloc(N, 1);
     so->gbest_E = INT64_MAX;
-    /* Section III-B: every search starts at X = 0, E = 0, Delta_k = W_kk. */
-    for (size_t s = 0; s < S; ++s)
-        for (int32_t k = 0; k < n; ++k) so->delta[s * N + k] = W[(int64_t)k * n + k];
-    /* Section IV-A: random vectors with +infinity energy, random fields. */
-    for (uint32_t pp = 0; pp < (uint32_t)P; ++pp)
-        for (uint32_t e = 0; e < (uint32_t)C; ++e) {
-            uint8_t* x = so->pool_X + ((size_t)pp * C + e) * N;
-            uint32_t u[4];
-            for (int32_t k = 0; k < n; ++k) {
-                draw(seed, (uint32_t)(k >> 5), e, pp, 7u << 24, u);
-                x[k] = (uint8_t)(nibble(u, k & 31) & 1);
-            }
-            so->pool_E[pp * C + e] = INT64_MAX;
-            draw(seed, 0, e, pp, 8u << 24, u);
-            so->pool_algo[pp * C + e] = (int32_t)uidx(u[0], ORC_N_ALGOS);
-            so->pool_op[pp * C + e] = (int32_t)uidx(u[1], ORC_N_OPS);
-        }
+    reset_searches(so);
+    init_pools(so, 0);
     return so;
 }
 
@@ -503,6 +543,10 @@ static void breed(const orc_solver* so, uint32_t g, uint32_t s, uint8_t* D, int3
                                          : so->pool_op[pp * C + uidx(c[1], C)];
     int32_t algo = (c[2] < MIX_THRESHOLD) ? (int32_t)uidx(c[3], ORC_N_ALGOS)
                                            : so->pool_algo[pp * C + uidx(c[3], C)];
+    if (so->p.abs_mode) { /* R24 */
+        op = ORC_CROSSOVER;
+        algo = ORC_CYCLICMIN;
+    }
     draw(so->seed, 0, g, s, 5u << 24, r);
     const uint8_t* A = so->pool_X + ((size_t)pp * C + orc_parent_rank(r[0], C)) * (size_t)n;
     const uint32_t bpool = (op == ORC_XROSSOVER) ? qq : pp;
@@ -512,6 +556,10 @@ static void breed(const orc_solver* so, uint32_t g, uint32_t s, uint8_t* D, int3
         draw(so->seed, (uint32_t)(k >> 5), g, s, 6u << 24, u);
         int nib = nibble(u, k & 31);
         int hit = (nib & 7) == 0, coin = nib & 1;
+        if (so->p.abs_mode) { /* R24: crossover, then mutation */
+            D[k] = (uint8_t)(((nib >> 3) ? Bv[k] : A[k]) ^ hit);
+            continue;
+        }
         switch (op) {
             case ORC_MUTATION: D[k] = (uint8_t)(A[k] ^ hit); break;
             case ORC_CROSSOVER:
@@ -619,6 +667,11 @@ uint64_t orc_solver_generation(orc_solver* so, int32_t threads) {
     for (int32_t s = 0; s < so->S; ++s) f += so->res_flips[s];
     so->flips_total += f;
     so->g += 1;
+    if (so->p.restart && pools_merged(so)) { /* R23 */
+        so->restarts += 1;
+        init_pools(so, so->restarts);
+        reset_searches(so);
+    }
     return f;
 }
 
@@ -663,6 +716,8 @@ void orc_solver_get_stats(const orc_solver* so, uint64_t* algo_count, uint64_t* 
     memcpy(best_algo, so->best_algo, sizeof so->best_algo);
     memcpy(best_op, so->best_op, sizeof so->best_op);
 }
+
+uint32_t orc_solver_get_restarts(const orc_solver* so) { return so->restarts; }
 
 void orc_solver_get_best(const orc_solver* so, uint8_t* X, int64_t* E, uint64_t* flips_total,
                          uint32_t* generations) {

@@ -39,6 +39,9 @@ typedef struct {
     int32_t b_num, b_den;    /* batch flip factor  b = b_num / b_den          */
     int32_t seed_mode;       /* 0 = Straight walk to D, 1 = from-scratch X=D  */
     int32_t max_generations; /* 0 = unlimited                                 */
+    int32_t restart;         /* 1 = restart when the pools have merged (R23)  */
+    int32_t restart_dist;    /* h: merged = every entry within distance h     */
+    int32_t abs_mode;        /* 1 = ABS: CyclicMin, crossover then mutation   */
 } orc_params;
 
 /* ---- definitions (Section I-A Eq. (2); Section III Eq. (3)) ---- */
@@ -82,6 +85,8 @@ void        orc_solver_get_best(const orc_solver* so, uint8_t* X, int64_t* E,
  * algorithm/operation of each result that improved the global best */
 void        orc_solver_get_stats(const orc_solver* so, uint64_t* algo_count, uint64_t* op_count,
                                  uint64_t* best_algo, uint64_t* best_op);
+/* restarts made so far (Section IV-B, all pools merged) */
+uint32_t    orc_solver_get_restarts(const orc_solver* so);
 /* merges externally given results into the pools (Section IV, packets) */
 void        orc_pool_merge(orc_solver* so, const uint8_t* best_X, const int64_t* best_E,
                            const int32_t* algo, const int32_t* op);

@@ -31,13 +31,14 @@ INT64_MAX = np.iinfo(np.int64).max
 class Params(C.Structure):
     _fields_ = [(k, C.c_int32) for k in (
         "searches", "pools", "pool_cap", "tabu", "s_num", "s_den", "b_num", "b_den",
-        "seed_mode", "max_generations")]
+        "seed_mode", "max_generations", "restart", "restart_dist", "abs_mode")]
 
 
 def make_params(searches=32, pools=4, pool_cap=64, tabu=8, s=(1, 10), b=(1, 1),
-                seed_mode=0, max_generations=0) -> Params:
+                seed_mode=0, max_generations=0, restart=0, restart_dist=0,
+                abs_mode=0) -> Params:
     return Params(searches, pools, pool_cap, tabu, s[0], s[1], b[0], b[1], seed_mode,
-                  max_generations)
+                  max_generations, restart, restart_dist, abs_mode)
 
 
 def build(force: bool = False) -> str:
@@ -88,6 +89,8 @@ def lib():
         L.orc_solver_get_best.argtypes = [C.c_void_p, u8p, i64p, u64p, u32p]
         L.orc_pool_merge.argtypes = [C.c_void_p, u8p, i64p, i32p, i32p]
         L.orc_solver_get_stats.argtypes = [C.c_void_p, u64p, u64p, u64p, u64p]
+        L.orc_solver_get_restarts.restype = C.c_uint32
+        L.orc_solver_get_restarts.argtypes = [C.c_void_p]
         L.orc_solve.restype = C.c_int
         L.orc_solve.argtypes = [i16p, C.c_int32, P(Params), C.c_uint64, C.c_uint64, C.c_int64,
                                 C.c_int32, u8p, i64p, u64p, u32p]
@@ -241,6 +244,9 @@ class Solver:
         lib().orc_solver_get_stats(self._h, _p(a, C.c_uint64), _p(o, C.c_uint64),
                                    _p(ba, C.c_uint64), _p(bo, C.c_uint64))
         return a, o, ba, bo
+
+    def restarts(self) -> int:
+        return int(lib().orc_solver_get_restarts(self._h))
 
     def best(self):
         X = np.zeros(self.n, np.uint8)

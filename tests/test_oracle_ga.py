@@ -223,3 +223,92 @@ def test_statistics_count_every_search_and_each_new_best(orc):
     ac, oc, ba, bo = so.stats()
     assert ac.sum() == S * G and oc.sum() == S * G
     assert ba.sum() == improvements and bo.sum() == improvements
+
+
+def hamming_to(pX, x):
+    return (pX.reshape(-1, x.size) != x[None, :]).sum(axis=1)
+
+
+@pytest.mark.parametrize("P,C,h", [(6, 1, 1), (3, 2, 6)])
+def test_restart_fires_exactly_when_every_pool_entry_is_near_the_best(orc, P, C, h):
+    """Section IV-B, last paragraph (reading R23): a twin without restarts
+    shows the pools after each merge; the restarting solver must leave them
+    untouched until the first generation where every entry lies within
+    Hamming distance h of the global best, then redraw them and reset the
+    searches while keeping the global best."""
+    n = 14
+    W = wl.dense_qubo(n, -20, 20, seed=5)
+    kw = dict(searches=8, pools=P, pool_cap=C, b=(2, 1))
+    on = orc.Solver(W, orc.make_params(restart=1, restart_dist=h, **kw), seed=3)
+    off = orc.Solver(W, orc.make_params(**kw), seed=3)
+    fired = None
+    for g in range(60):
+        on.generation(); off.generation()
+        bx, be, _, _ = off.best()
+        merged = (hamming_to(off.pools()[0], bx) <= h).all()
+        if not merged:
+            assert on.restarts() == 0
+            for a, b in zip(on.pools(), off.pools()):
+                assert np.array_equal(a, b)
+            continue
+        fired = g
+        assert on.restarts() == 1
+        X, E, a, o = on.pools()
+        assert (E == np.iinfo(np.int64).max).all()
+        assert not np.array_equal(X, off.pools()[0])
+        sX, sd, sE = on.state()
+        assert not sX.any() and (sE == 0).all()
+        assert np.array_equal(sd, np.tile(np.diag(W).astype(np.int32), (8, 1)))
+        assert on.best()[1] == be and np.array_equal(on.best()[0], bx)
+        break
+    assert fired is not None, "the pools never merged on this easy instance"
+
+
+def test_restart_disabled_by_negative_radius_changes_nothing(orc):
+    W = wl.dense_qubo(24, -20, 20, seed=6)
+    kw = dict(searches=16, pools=2, pool_cap=4)
+    a = orc.solve(W, orc.make_params(restart=1, restart_dist=-1, max_generations=20, **kw), 10**9, 4)
+    b = orc.solve(W, orc.make_params(max_generations=20, **kw), 10**9, 4)
+    assert a[1:] == b[1:] and np.array_equal(a[0], b[0])
+
+
+def test_restart_every_generation_keeps_the_best_monotone(orc):
+    W = wl.dense_qubo(40, -50, 50, seed=7)
+    so = orc.Solver(W, orc.make_params(searches=16, pools=2, pool_cap=4, restart=1,
+                                       restart_dist=40), seed=1)
+    prev = None
+    for g in range(6):
+        so.generation()
+        assert so.restarts() == g + 1
+        be = so.best()[1]
+        assert prev is None or be <= prev
+        prev = be
+    # each restart draws pools of its own
+    X1 = so.pools()[0]
+    so.generation()
+    assert not np.array_equal(so.pools()[0], X1)
+
+
+def test_abs_mode_is_cyclicmin_with_mutation_after_crossover(orc):
+    """Section I (reading R24): the earlier ABS runs CyclicMin only and breeds
+    every target as a crossover of two pool parents followed by a mutation.
+    With parents all-zero (rank 0) and all-one (rank 1), a target's density
+    of ones is 1/8 (both zero), 7/8 (both one) or 1/2 (mixed: independent
+    coin, then 1/8 inversions) -- a coin correlated with the mutation mask
+    would give 3/8 or 5/8."""
+    n, S = 4096, 64
+    W = np.zeros((n, n), np.int16)
+    so = orc.Solver(W, orc.make_params(searches=S, pools=1, pool_cap=2, abs_mode=1), seed=8)
+    X = np.zeros((1, 2, n), np.uint8)
+    X[0, 1] = 1
+    so.set_pools(X, np.array([[0, 1]], np.int64), np.full((1, 2), 0, np.int32),
+                 np.full((1, 2), 6, np.int32))
+    seen = set()
+    for g in range(4):
+        D, a, o = so.offspring(g)
+        assert (a == 1).all() and (o == 1).all()
+        for dens in D.mean(axis=1):
+            near = [c for c in (1 / 8, 1 / 2, 7 / 8) if abs(dens - c) < 0.035]
+            assert near, dens
+            seen.add(near[0])
+    assert seen == {1 / 8, 1 / 2, 7 / 8}
