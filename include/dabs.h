@@ -53,7 +53,8 @@ enum { DABS_MUTATION = 0, DABS_CROSSOVER = 1, DABS_XROSSOVER = 2, DABS_ZERO = 3,
 
 /* Solver parameters (Sections III-B and IV).  Defaults (dabs_params_default):
  * 32 searches, 4 pools, pool_cap 100 and tabu 8 (the paper's experiments),
- * s = 1/10, b = 1, Straight seeding, no generation limit.                   */
+ * s = 1/10, b = 1, Straight seeding, no generation limit, no restarts, DABS
+ * (not ABS) breeding.                                                       */
 typedef struct dabs_params {
     int32_t searches;        /* concurrent batch searches S (1..65535)          */
     int32_t pools;           /* solution pools P (islands), 1..S                */
@@ -64,6 +65,16 @@ typedef struct dabs_params {
     int32_t seed_mode;       /* 0: Straight walk to each target (Section III-B);
                                 1: X = target, Delta and E recomputed           */
     int32_t max_generations; /* 0 = unlimited                                  */
+    int32_t restart;         /* 1: when every pool entry lies within Hamming
+                                distance restart_dist of the global best (the
+                                pools have merged, Section IV-B), draw all
+                                pools afresh and restart every search from
+                                X = 0; the global best carries on.  0: never */
+    int32_t restart_dist;    /* h of the merge test (negative: never merged)  */
+    int32_t abs_mode;        /* 1: the earlier Adaptive Bulk Search (Section I):
+                                CyclicMin only, and every target is a mutation
+                                after a crossover of two parents of its own
+                                pool.  0: DABS                                */
 } dabs_params;
 
 typedef struct dabs_ctx dabs_ctx;
@@ -179,6 +190,9 @@ int dabs_solve_generations(dabs_ctx* ctx, int32_t count);
 /* Waits for the stream, then reports the counters. */
 int dabs_solve_status(dabs_ctx* ctx, uint64_t* flips, uint32_t* generations, int64_t* best_E,
                       int32_t* done);
+/* Waits for the stream, then reports the pool restarts made so far
+ * (dabs_params.restart). */
+int dabs_solve_restarts(dabs_ctx* ctx, uint32_t* restarts);
 /* Waits for the stream, then copies the best vector (host, n bytes) and E. */
 int dabs_solve_best(dabs_ctx* ctx, uint8_t* best_X, int64_t* best_E);
 

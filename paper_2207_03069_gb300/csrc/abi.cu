@@ -43,7 +43,8 @@ bool params_ok(const dabs_params* p) {
   return p->searches >= 1 && p->searches <= 65535 && p->pools >= 1 && p->pools <= p->searches &&
          p->pool_cap >= 1 && p->pool_cap <= 1024 && p->tabu >= 0 && p->tabu <= 31 &&
          p->s_num >= 0 && p->s_den >= 1 && p->b_num >= 0 && p->b_den >= 1 &&
-         (p->seed_mode == 0 || p->seed_mode == 1) && p->max_generations >= 0;
+         (p->seed_mode == 0 || p->seed_mode == 1) && p->max_generations >= 0 &&
+         (p->restart == 0 || p->restart == 1) && (p->abs_mode == 0 || p->abs_mode == 1);
 }
 
 bool default_variant(int n, SearchVariant* v) {
@@ -158,7 +159,7 @@ int stage(dabs_ctx* ctx, int which) {
     OffArgs o{};
     o.n = ctx->n; o.nw = ctx->nw; o.S = ctx->S; o.P = ctx->P; o.C = ctx->C; o.ctrl = ctx->ctrl;
     for (int b = 0; b < 2; ++b) { o.pool_X[b] = ctx->poolX[b]; o.pool_algo[b] = ctx->poolA[b]; o.pool_op[b] = ctx->poolO[b]; }
-    o.D = ctx->D; o.algo = ctx->algo; o.op = ctx->op;
+    o.D = ctx->D; o.algo = ctx->algo; o.op = ctx->op; o.abs_mode = ctx->p.abs_mode;
     k_offspring<<<(ctx->S * 32 + 255) / 256, 256, 0, st>>>(o);
     CKLAUNCH();
     if (ctx->p.seed_mode == 1) {
@@ -190,10 +191,29 @@ int stage(dabs_ctx* ctx, int which) {
     k_merge<<<ctx->P, kMergeThreads, ctx->merge_smem, st>>>(m);
     CKLAUNCH();
   } else if (which == 3) {
+    const bool restart = ctx->p.restart != 0;
+    if (restart) CK(cudaMemsetAsync(ctx->rflag, 1, sizeof(uint32_t), st));  // skip unless armed
     FinArgs f{ctx->nw, ctx->S, ctx->ctrl, ctx->bestX, ctx->bestE, ctx->flips, ctx->gbestX,
-              ctx->algo, ctx->op, ctx->stats};
+              ctx->algo, ctx->op, ctx->stats, restart ? ctx->rflag : nullptr};
     k_finalize<<<1, 1024, 0, st>>>(f);
     CKLAUNCH();
+    if (restart) {  // Section IV-B: restart once every pool has merged around the best
+      const int entries = ctx->P * ctx->C;
+      RestartArgs r{ctx->nw, ctx->P, ctx->C, ctx->p.restart_dist, ctx->ctrl,
+                    {ctx->poolX[0], ctx->poolX[1]}, ctx->gbestX, ctx->rflag};
+      k_restart_check<<<std::min((entries * 32 + 255) / 256, 1216), 256, 0, st>>>(r);
+      CKLAUNCH();
+      PoolArgs pa{};
+      pa.n = ctx->n; pa.nw = ctx->nw; pa.P = ctx->P; pa.C = ctx->C; pa.ctrl = ctx->ctrl;
+      pa.cond = ctx->rflag;
+      for (int b = 0; b < 2; ++b) { pa.pool_X[b] = ctx->poolX[b]; pa.pool_E[b] = ctx->poolE[b]; pa.pool_algo[b] = ctx->poolA[b]; pa.pool_op[b] = ctx->poolO[b]; }
+      k_pool_init<<<(entries * 32 + 255) / 256, 256, 0, st>>>(pa);
+      CKLAUNCH();
+      StateArgs sa{ctx->n, ctx->ld, ctx->nw, ctx->S, ctx->diag, ctx->X, ctx->delta, ctx->E,
+                   nullptr, ctx->rflag, ctx->ctrl};
+      k_state_init<<<304, 256, 0, st>>>(sa);
+      CKLAUNCH();
+    }
   } else {
     return fail(ctx, DABS_E_INVALID_ARG, "stage %d", which);
   }
@@ -247,7 +267,7 @@ extern "C" {
 
 int dabs_params_default(dabs_params* p) {
   if (!p) return DABS_E_INVALID_ARG;
-  *p = dabs_params{32, 4, 100, 8, 1, 10, 1, 1, 0, 0};
+  *p = dabs_params{32, 4, 100, 8, 1, 10, 1, 1, 0, 0, 0, 0, 0};
   return DABS_OK;
 }
 
@@ -338,6 +358,7 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
   TRY(dalloc(ctx, &ctx->order, S));
   TRY(dalloc(ctx, &ctx->gbestX, nw));
   TRY(dalloc(ctx, &ctx->stats, kStats));
+  TRY(dalloc(ctx, &ctx->rflag, 1));
   TRY(dalloc(ctx, &ctx->one_X, nw));
   TRY(dalloc(ctx, &ctx->one_d, ld));
   TRY(dalloc(ctx, &ctx->one_E, 1));
@@ -428,7 +449,8 @@ int dabs_solve_begin(dabs_ctx* ctx, uint64_t seed, uint64_t budget, int64_t targ
   *ctx->h_ctrl = c;
   CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * kStats, ctx->stream));
-  StateArgs s{ctx->n, ctx->ld, ctx->nw, ctx->S, ctx->diag, ctx->X, ctx->delta, ctx->E, ctx->gbestX};
+  StateArgs s{ctx->n, ctx->ld, ctx->nw, ctx->S, ctx->diag, ctx->X, ctx->delta, ctx->E, ctx->gbestX,
+              nullptr, nullptr};
   k_state_init<<<304, 256, 0, ctx->stream>>>(s);
   CKLAUNCH();
   PoolArgs pa{};
@@ -465,6 +487,15 @@ int dabs_solve_status(dabs_ctx* ctx, uint64_t* flips, uint32_t* generations, int
   if (generations) *generations = c.g;
   if (best_E) *best_E = c.best_E;
   if (done) *done = (int32_t)c.done;
+  return DABS_OK;
+}
+
+int dabs_solve_restarts(dabs_ctx* ctx, uint32_t* restarts) {
+  if (!ctx || !restarts) return DABS_E_INVALID_ARG;
+  DevCtrl c;
+  const int rc = read_ctrl(ctx, &c);
+  if (rc) return rc;
+  *restarts = c.restarts;
   return DABS_OK;
 }
 

@@ -92,7 +92,7 @@ struct DevCtrl {
   uint64_t budget;
   int64_t target;
   uint32_t max_generations;  // 0 = unlimited
-  uint32_t pad;
+  uint32_t restarts;         // pool restarts so far (the epoch of the pool draws)
   int64_t best_E;
 };
 

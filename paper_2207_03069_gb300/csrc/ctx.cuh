@@ -45,6 +45,7 @@ struct dabs_ctx {
   int32_t* order = nullptr;   // slot launch order grouped by algorithm
   uint32_t* gbestX = nullptr;
   unsigned long long* stats = nullptr;  // [kStats] Tables V/VI counters
+  uint32_t* rflag = nullptr;            // restart flag of the running generation
   uint32_t* one_X = nullptr;   // single-vector scratch for dabs_energy / dabs_delta
   int32_t* one_d = nullptr;
   int64_t* one_E = nullptr;

@@ -14,11 +14,14 @@ __global__ void k_pool_init(const PoolArgs a) {
   const int lane = threadIdx.x & 31;
   const int e_glob = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // entry = p*C + e
   if (e_glob >= a.P * a.C) return;
+  if (a.cond && *a.cond != 0) return;  // no restart this generation
   const uint32_t p = (uint32_t)(e_glob / a.C), e = (uint32_t)(e_glob % a.C);
   const uint64_t seed = a.ctrl->seed;
-  uint32_t* x = a.pool_X[0] + (size_t)e_glob * a.nw;
+  const uint32_t epoch = a.cond ? a.ctrl->restarts + 1 : 0;  // the restart being made
+  const int cur = a.ctrl->g & 1;
+  uint32_t* x = a.pool_X[cur] + (size_t)e_glob * a.nw;
   for (int w = lane; w < a.nw; w += 32) {
-    const uint4 u = draw(seed, (uint32_t)w, e, p, RNG_INIT_BITS);
+    const uint4 u = draw(seed, (uint32_t)w, e, p, RNG_INIT_BITS | epoch);
     uint32_t v = 0;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -28,15 +31,17 @@ __global__ void k_pool_init(const PoolArgs a) {
     x[w] = v & valid_mask(w, a.n);
   }
   if (lane == 0) {
-    const uint4 u = draw(seed, 0, e, p, RNG_INIT_TAGS);
-    a.pool_E[0][e_glob] = INT64_MAX;
-    a.pool_algo[0][e_glob] = (uint8_t)uniform_below(u.x, N_ALGOS);
-    a.pool_op[0][e_glob] = (uint8_t)uniform_below(u.y, N_OPS);
+    const uint4 u = draw(seed, 0, e, p, RNG_INIT_TAGS | epoch);
+    a.pool_E[cur][e_glob] = INT64_MAX;
+    a.pool_algo[cur][e_glob] = (uint8_t)uniform_below(u.x, N_ALGOS);
+    a.pool_op[cur][e_glob] = (uint8_t)uniform_below(u.y, N_OPS);
   }
 }
 
 // X = 0, E = 0, Delta_k = W_kk for every search slot (Section III-B start).
 __global__ void k_state_init(const StateArgs a) {
+  if (a.cond && *a.cond != 0) return;
+  if (a.bump && blockIdx.x == 0 && threadIdx.x == 0) a.bump->restarts += 1;
   const size_t total = (size_t)a.S * a.ld;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
        q += (size_t)gridDim.x * blockDim.x) {
@@ -50,9 +55,31 @@ __global__ void k_state_init(const StateArgs a) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)a.S;
        q += (size_t)gridDim.x * blockDim.x)
     a.E[q] = 0;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)a.nw;
-       q += (size_t)gridDim.x * blockDim.x)
-    a.gbest_X[q] = 0;
+  if (a.gbest_X)
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)a.nw;
+         q += (size_t)gridDim.x * blockDim.x)
+      a.gbest_X[q] = 0;
+}
+
+// Section IV-B, last paragraph: the pools have merged when every entry lies
+// within Hamming distance h of the global best.  One warp per entry; any
+// entry farther than h sets the flag.  The flag reads 1 (skip) unless
+// k_finalize ran in this generation and armed it.
+__global__ void k_restart_check(const RestartArgs a) {
+  if (*a.flag != 0) return;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t* PX = a.pool_X[a.ctrl->g & 1];
+  for (int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); q < a.P * a.C; q += warps) {
+    const uint32_t* x = PX + (size_t)q * a.nw;
+    int d = 0;
+    for (int w = lane; w < a.nw; w += 32) d += __popc(x[w] ^ a.gbest_X[w]);
+    d = __reduce_add_sync(FULLMASK, d);
+    if (d > a.h) {
+      if (lane == 0) atomicOr(a.flag, 1u);
+      return;
+    }
+  }
 }
 
 // ---------------------------------------------------------------- offspring
@@ -79,10 +106,14 @@ __global__ void k_offspring(const OffArgs a) {
   const uint32_t* PX = a.pool_X[cur];
   // Section IV-A: 5% uniform choice, 95% copy of a random pool row's field
   const uint4 c = draw(seed, 0, g, (uint32_t)s, RNG_CHOICE);
-  const int op = c.x < kMixThreshold ? (int)uniform_below(c.y, N_OPS)
-                                     : (int)a.pool_op[cur][p * C + uniform_below(c.y, C)];
-  const int algo = c.z < kMixThreshold ? (int)uniform_below(c.w, N_ALGOS)
-                                       : (int)a.pool_algo[cur][p * C + uniform_below(c.w, C)];
+  int op = c.x < kMixThreshold ? (int)uniform_below(c.y, N_OPS)
+                               : (int)a.pool_op[cur][p * C + uniform_below(c.y, C)];
+  int algo = c.z < kMixThreshold ? (int)uniform_below(c.w, N_ALGOS)
+                                 : (int)a.pool_algo[cur][p * C + uniform_below(c.w, C)];
+  if (a.abs_mode) {  // the earlier ABS: CyclicMin, mutation after crossover
+    op = CROSSOVER;
+    algo = CYCLICMIN;
+  }
   const uint4 r = draw(seed, 0, g, (uint32_t)s, RNG_PARENT);
   const uint32_t* A = PX + ((size_t)p * C + parent_rank(r.x, C)) * a.nw;
   const uint32_t bp = op == XROSSOVER ? q : p;  // Section IV-B: neighbour island
@@ -94,16 +125,21 @@ __global__ void k_offspring(const OffArgs a) {
   uint32_t* D = a.D + (size_t)s * a.nw;
   for (int w = lane; w < a.nw; w += 32) {
     const uint4 u = draw(seed, (uint32_t)w, g, (uint32_t)s, RNG_BITS);
-    uint32_t hit = 0, coin = 0;
+    uint32_t hit = 0, coin = 0, coin3 = 0;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const uint32_t word = j < 8 ? u.x : j < 16 ? u.y : j < 24 ? u.z : u.w;
       const uint32_t nib = (word >> (4 * (j & 7))) & 0xFu;
       hit |= (uint32_t)((nib & 7u) == 0u) << j;
       coin |= (nib & 1u) << j;
+      coin3 |= (nib >> 3) << j;
     }
     const uint32_t av = A[w], bv = Bv[w];
     uint32_t v;
+    if (a.abs_mode) {  // coin from bit 3 of the nibble, then the mutation mask
+      D[w] = (((bv & coin3) | (av & ~coin3)) ^ hit) & valid_mask(w, a.n);
+      continue;
+    }
     switch (op) {
       case MUTATION: v = av ^ hit; break;
       case CROSSOVER:
@@ -345,6 +381,7 @@ __global__ void __launch_bounds__(1024) k_finalize(const FinArgs a) {
   }
   __syncthreads();
   if (a.stats && tid < kStats && cnt[tid]) a.stats[tid] += cnt[tid];
+  if (a.rflag && tid == 0) *a.rflag = 0;
   if (tid == 0) {
     const bool stop = ctrl->flips_total >= ctrl->budget || ctrl->best_E <= ctrl->target ||
                       (ctrl->max_generations > 0 && ctrl->g >= ctrl->max_generations);

@@ -17,6 +17,7 @@ __host__ __device__ __forceinline__ uint32_t valid_mask(int w, int n) {
 struct PoolArgs {
   int n, nw, P, C;
   const DevCtrl* ctrl;
+  const uint32_t* cond;  // restart flag: draw only where it reads 0 (NULL: always, epoch 0)
   uint32_t* pool_X[2];
   int64_t* pool_E[2];
   uint8_t* pool_algo[2];
@@ -29,7 +30,17 @@ struct StateArgs {
   uint32_t* X;
   int32_t* delta;
   int64_t* E;
-  uint32_t* gbest_X;
+  uint32_t* gbest_X;     // cleared unless NULL
+  const uint32_t* cond;  // restart flag: reset only where it reads 0 (NULL: always)
+  DevCtrl* bump;         // restarts += 1 here after a restart (NULL: none)
+};
+
+struct RestartArgs {
+  int nw, P, C, h;
+  const DevCtrl* ctrl;
+  const uint32_t* pool_X[2];
+  const uint32_t* gbest_X;
+  uint32_t* flag;  // 0 after k_finalize ran; set to 1 when some entry is farther than h
 };
 
 struct OffArgs {
@@ -41,6 +52,7 @@ struct OffArgs {
   uint32_t* D;
   uint8_t* algo;
   uint8_t* op;
+  int abs_mode;  // 1: CyclicMin and mutation after crossover for every search
 };
 
 struct MergeArgs {
@@ -70,6 +82,7 @@ struct FinArgs {
   const uint8_t* algo;
   const uint8_t* op;
   unsigned long long* stats;  // [kStats]
+  uint32_t* rflag;            // restart flag armed (0) here when restarts are on
 };
 
 struct EDArgs {
@@ -87,6 +100,7 @@ __global__ void k_state_init(const StateArgs a);
 __global__ void k_offspring(const OffArgs a);
 __global__ void k_merge(const MergeArgs a);
 __global__ void k_finalize(const FinArgs a);
+__global__ void k_restart_check(const RestartArgs a);
 __global__ void k_energy_delta(const EDArgs a);
 __global__ void k_order_by_algo(const uint8_t* algo, int S, int32_t* order, const DevCtrl* ctrl);
 __global__ void k_copy_targets(const uint32_t* D, uint32_t* X, int64_t* E, size_t words, int S,

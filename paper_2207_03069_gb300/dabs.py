@@ -29,7 +29,7 @@ STAGE_OFFSPRING, STAGE_SEARCH, STAGE_MERGE, STAGE_FINALIZE = range(4)
 class Params(C.Structure):
     _fields_ = [(k, C.c_int32) for k in (
         "searches", "pools", "pool_cap", "tabu", "s_num", "s_den", "b_num", "b_den",
-        "seed_mode", "max_generations")]
+        "seed_mode", "max_generations", "restart", "restart_dist", "abs_mode")]
 
 
 class DabsError(RuntimeError):
@@ -69,6 +69,7 @@ EXPORTS = {
     "dabs_write_results": (C.c_int, [C.c_void_p] * 6),
     "dabs_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
     "dabs_read_stats": (C.c_int, [C.c_void_p] * 5),
+    "dabs_solve_restarts": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dabs_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dabs_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "dabs_recompute_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
@@ -345,6 +346,11 @@ class Context:
         self._ck(lib().dabs_solve_status(self._h, C.byref(f), C.byref(g), C.byref(e), C.byref(d)))
         return dict(flips=int(f.value), generations=int(g.value), best_E=int(e.value),
                     done=bool(d.value))
+
+    def restarts(self) -> int:
+        r = C.c_uint32()
+        self._ck(lib().dabs_solve_restarts(self._h, C.byref(r)))
+        return int(r.value)
 
     def solve_best(self):
         X = np.zeros(self.n, np.uint8)

@@ -27,10 +27,11 @@ def instance(n, k):
     return wl.dense_qubo(n, -1000, 1000, seed=100 + k)
 
 
-@pytest.mark.parametrize("seed_mode", [0, 1])
-def test_batch_solve_equals_alone(D, orc, seed_mode):
+@pytest.mark.parametrize("seed_mode,extra", [(0, {}), (1, {}),
+                                             (0, dict(restart=1, restart_dist=100, abs_mode=1))])
+def test_batch_solve_equals_alone(D, orc, seed_mode, extra):
     kw = dict(searches=48, pools=4, pool_cap=16, tabu=8, s=(1, 10), b=(1, 1), seed_mode=seed_mode,
-              max_generations=5)
+              max_generations=5, **extra)
     Ws = [instance(n, k) for k, n in enumerate(SIZES)]
     ctxs = [D.Context(W, **kw) for W in Ws]
     budgets = [10**9, 10**9, 40000, 10**9, 10**9, 10**9]  # one stops early on its budget

@@ -322,3 +322,39 @@ def test_autotune_keeps_results(D, orc):
     gx, ge, gf = ctx.solve(10**9, seed=2)
     ox, oe, of, _ = orc.solve(W, orc.make_params(**kw), 10**9, 2, threads=4)
     assert (ge, gf) == (oe, of) and np.array_equal(gx, ox)
+
+
+@pytest.mark.parametrize("P,C,h,abs_mode", [(6, 1, 1, 0), (3, 2, 6, 0), (2, 4, 10, 1),
+                                            (1, 4, 6, 1)])
+def test_restart_and_abs_modes_match_oracle(D, orc, P, C, h, abs_mode):
+    """Restart on merged pools (Section IV-B) and the ABS ablation (Section I)
+    generation by generation against the oracle, restarts included."""
+    n = 14
+    W = wl.dense_qubo(n, -20, 20, seed=5)
+    kw = dict(searches=8, pools=P, pool_cap=C, b=(2, 1), restart=1, restart_dist=h,
+              abs_mode=abs_mode)
+    ctx = D.Context(W, **kw)
+    so = orc.Solver(W, orc.make_params(**kw), 3)
+    ctx.solve_begin(3)
+    for g in range(25):
+        ctx.solve_generations(1)
+        so.generation()
+        compare_generation(ctx, so, n, f"generation {g}")
+        assert ctx.restarts() == so.restarts()
+    assert so.restarts() > 0
+    st = ctx.solve_status()
+    bx, be, bf, bg = so.best()
+    assert (st["best_E"], st["flips"], st["generations"]) == (be, bf, bg)
+    for got, want in zip(ctx.stats(), so.stats()):
+        assert np.array_equal(got, want)
+
+
+def test_abs_mode_solve_at_size_matches_oracle(D, orc):
+    n = 300
+    W = wl.dense_qubo(n, -100, 100, seed=8)
+    kw = dict(searches=64, pools=2, pool_cap=16, tabu=8, s=(1, 10), b=(1, 1), abs_mode=1,
+              restart=1, restart_dist=60, max_generations=6)
+    ctx = D.Context(W, **kw)
+    gx, ge, gf = ctx.solve(10**9, seed=5)
+    ox, oe, of, og = orc.solve(W, orc.make_params(**kw), 10**9, 5, threads=4)
+    assert (ge, gf) == (oe, of) and np.array_equal(gx, ox)
