@@ -430,10 +430,10 @@ def main():
     ctx.set_stream(stream)
     sweep = {}
     if args.variant:
-        ctx.set_variant(*[int(x) for x in args.variant.split("x")])
+        ctx.set_variant_name(args.variant)
     elif not args.no_autotune:
-        tuned = ctx.autotune(3)  # untimed: picks warps x chunks for this workload
-        sweep = {"chosen": "%dx%d" % tuned[:2], "ns_per_flip": tuned[3]}
+        tuned = ctx.autotune(3)  # untimed: picks warps x chunks and the row format
+        sweep = {"chosen": ctx.variant_name(), "ns_per_flip": tuned[3]}
     seed = args.seed + 1000 * rank
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 

@@ -240,8 +240,30 @@ int dabs_bulk_search_noalloc(const int16_t* W, int32_t n, int32_t ld, const dabs
  * kernel variant (warps per search, 8-bit chunks per thread). */
 int dabs_info(const dabs_ctx* ctx, int32_t* n, int32_t* ld, int32_t* words, int32_t* searches,
               int32_t* pools, int32_t* pool_cap, int32_t* warps, int32_t* chunks);
-/* Chooses the batch-search variant; returns TOO_LARGE if it cannot hold n. */
+/* Chooses the batch-search variant; returns TOO_LARGE if it cannot hold n.
+ * Sparse rows stay selected only if they fit the new variant. */
 int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
+/* Row format of the batch search (Step 3, Eq. (4) reads row i of W):
+ *   DABS_ROWS_DENSE          the dense int16 rows of W in global memory;
+ *   DABS_ROWS_SPARSE_SMEM    every CTA keeps the off-diagonal non-zeros of all
+ *                            rows (column << 16 | 16-bit weight, 4 bytes each,
+ *                            plus n+1 row offsets) in shared memory;
+ *   DABS_ROWS_SPARSE_GLOBAL  the same entries read from global memory (L2).
+ * With sparse rows a flip scatters row i into a zeroed per-search scratch row
+ * in shared memory, so it reads 4 bytes per non-zero instead of 2n bytes.
+ * Sparse rows are stored while the non-zeros are at most n^2/4; TOO_LARGE
+ * when they are not, or when the format's shared memory (the copy, about
+ * 56,000 entries at most on this GPU, and ld int16 per search of a CTA)
+ * exceeds the device's opt-in size per block.  The default is shared-memory
+ * sparse rows when they fit, else global sparse rows, for W with at most one
+ * non-zero in eight entries, and dense rows otherwise.  Results do not depend
+ * on the format.  Batched launches (dabs_batch_solve, the server) read dense
+ * rows. */
+enum { DABS_ROWS_DENSE = 0, DABS_ROWS_SPARSE_SMEM = 1, DABS_ROWS_SPARSE_GLOBAL = 2 };
+int dabs_set_rows(dabs_ctx* ctx, int32_t mode);
+/* Current row format and the number of stored off-diagonal non-zeros (-1
+ * when sparse rows are not stored). */
+int dabs_get_rows(const dabs_ctx* ctx, int32_t* mode, int32_t* nnz);
 /* Runs a throwaway solve on the context's workload for `generations` warm-up
  * generations, breeds the next generation's targets, then times the batch
  * search of that same generation with every built variant that holds n (each
@@ -249,9 +271,12 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
  * (results never depend on the variant).
  * table (may be NULL) receives DABS_N_VARIANTS nanoseconds-per-flip entries
  * in the order (warps x chunks) 1x1 1x2 1x4 2x1 2x2 2x4 4x1 4x2 4x4 8x1 8x2
- * 8x4 16x1 16x2 16x4, 0 where a variant cannot hold n.  Resets the solve state;
- * call before dabs_solve_begin.  Synchronous. */
-#define DABS_N_VARIANTS 15
+ * 8x4 16x1 16x2 16x4 with dense rows, then the same 15 with sparse rows in
+ * shared memory and 15 with sparse rows in global memory (dabs_set_rows), 0
+ * where a variant cannot hold n or the row format is unavailable.  Sets the
+ * fastest variant and row format.  Resets the solve state; call before
+ * dabs_solve_begin.  Synchronous. */
+#define DABS_N_VARIANTS 45
 int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* chunks,
                   float* ns_per_flip, float* table);
 /* Counters of the running solve (the paper's Tables V and VI): runs of each

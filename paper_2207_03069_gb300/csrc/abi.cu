@@ -60,6 +60,7 @@ bool default_variant(int n, SearchVariant* v) {
 }
 
 int tc_limbs(dabs_ctx* ctx);
+bool rows_ok(const dabs_ctx* ctx, const SearchVariant& v, int mode);
 
 int upload_weights(dabs_ctx* ctx, const int16_t* W) {
   const int n = ctx->n, ld = ctx->ld;
@@ -86,8 +87,57 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
   CK(cudaMemcpy(ctx->W, pad.data(), pad.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->Wneg, neg.data(), neg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->diag, dg.data(), dg.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  // sparse rows: the off-diagonal non-zeros of each row, column ascending,
+  // kept while they take at most half the bytes of the dense rows
+  const size_t limit = (size_t)n * n / 4;
+  std::vector<uint32_t> rp(4 * (size_t)sparse_row16(n), 0), ent;
+  bool keep = true;
+  for (int i = 0; i < n && keep; ++i) {
+    rp[i] = (uint32_t)ent.size();
+    for (int k = 0; k < n; ++k) {
+      const int16_t w = W[(size_t)i * n + k];
+      if (k != i && w != 0) ent.push_back(((uint32_t)k << 16) | (uint16_t)w);
+    }
+    keep = ent.size() <= limit;
+  }
+  ctx->sp_nnz = -1;
+  if (keep) {
+    rp[n] = (uint32_t)ent.size();
+    const int nnz = (int)ent.size();
+    ent.resize(4 * (size_t)sparse_ent16(nnz), 0u);
+    if (ent.size() > ctx->sp_cap) {
+      if (ctx->sp_ent) cudaFree(ctx->sp_ent);
+      ctx->sp_ent = nullptr;
+      ctx->sp_cap = 0;
+      CK(cudaMalloc(&ctx->sp_ent, ent.size() * 4));
+      ctx->sp_cap = ent.size();
+    }
+    CK(cudaMemcpy(ctx->sp_row, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice));
+    if (!ent.empty()) CK(cudaMemcpy(ctx->sp_ent, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice));
+    ctx->sp_nnz = nnz;
+  }
+  if (!rows_ok(ctx, ctx->var, ctx->rows_mode)) ctx->rows_mode = ROWS_DENSE;
   if (ctx->tc_ready) return tc_limbs(ctx);
   return DABS_OK;
+}
+
+// a row format is usable with variant v: sparse rows are stored, and the
+// shared memory they need (the copy for ROWS_SPARSE_SMEM, one scratch row per
+// search of a CTA) fits the opt-in size of a block with 2 KiB to spare for
+// the kernel's static arrays
+bool rows_ok(const dabs_ctx* ctx, const SearchVariant& v, int mode) {
+  if (mode == ROWS_DENSE) return true;
+  if (ctx->sp_nnz < 0 || (mode != ROWS_SPARSE_SMEM && mode != ROWS_SPARSE_GLOBAL)) return false;
+  const size_t need = sparse_smem_bytes(mode, ctx->n, ctx->sp_nnz, ctx->ld, v.spc) + 2048;
+  return need <= (size_t)ctx->smem_optin;
+}
+
+// sparse rows in shared memory when they fit, else from global memory, for
+// instances with at most one non-zero in eight entries; dense rows otherwise
+int default_rows(const dabs_ctx* ctx) {
+  if (ctx->sp_nnz < 0 || (int64_t)ctx->sp_nnz * 8 > (int64_t)ctx->n * ctx->n) return ROWS_DENSE;
+  if (rows_ok(ctx, ctx->var, ROWS_SPARSE_SMEM)) return ROWS_SPARSE_SMEM;
+  return rows_ok(ctx, ctx->var, ROWS_SPARSE_GLOBAL) ? ROWS_SPARSE_GLOBAL : ROWS_DENSE;
 }
 
 int tc_limbs(dabs_ctx* ctx) {
@@ -150,6 +200,12 @@ SearchArgs solve_search_args(dabs_ctx* ctx) {
   a.X = ctx->X; a.delta = ctx->delta; a.E = ctx->E; a.D = ctx->D; a.algo = ctx->algo;
   a.best_X = ctx->bestX; a.best_E = ctx->bestE; a.flips = ctx->flips;
   a.order = ctx->order;
+  if (ctx->rows_mode != ROWS_DENSE) {
+    a.sp_mode = ctx->rows_mode;
+    a.sp_row = ctx->sp_row;
+    a.sp_ent = ctx->sp_ent;
+    a.sp_nnz = ctx->sp_nnz;
+  }
   return a;
 }
 
@@ -292,6 +348,7 @@ void dabs_destroy(dabs_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->sp_ent) cudaFree(ctx->sp_ent);
   if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
   if (ctx->own) cudaStreamDestroy(ctx->own);
   delete ctx;
@@ -335,6 +392,12 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
   }
   ctx->stream = ctx->own;
   const size_t S = ctx->S, PC = (size_t)ctx->P * ctx->C, nw = ctx->nw, ld = ctx->ld;
+  {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    ctx->smem_optin = optin;
+  }
+  TRY(dalloc(ctx, &ctx->sp_row, 4 * (size_t)sparse_row16(n)));
   TRY(dalloc(ctx, &ctx->W, (size_t)n * ld));
   TRY(dalloc(ctx, &ctx->Wneg, (size_t)n * ld));
   TRY(dalloc(ctx, &ctx->diag, (size_t)n));
@@ -371,6 +434,7 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
     }
   }
   TRY(upload_weights(ctx, W));
+  ctx->rows_mode = default_rows(ctx);
   if (p->seed_mode == 1) {  // recompute seeding runs on the tensor cores by default
     TRY(tc_setup(ctx));
     ctx->recompute_mode = 1;
@@ -580,15 +644,31 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks) {
     return fail(ctx, DABS_E_INVALID_ARG, "variant %d/%d not built", warps, chunks);
   if (v.cap < ctx->n) return fail(ctx, DABS_E_TOO_LARGE, "variant holds %d < n", v.cap);
   ctx->var = v;
+  if (!rows_ok(ctx, v, ctx->rows_mode)) ctx->rows_mode = ROWS_DENSE;
+  return DABS_OK;
+}
+
+int dabs_set_rows(dabs_ctx* ctx, int32_t mode) {
+  if (!ctx || mode < DABS_ROWS_DENSE || mode > DABS_ROWS_SPARSE_GLOBAL) return DABS_E_INVALID_ARG;
+  if (!rows_ok(ctx, ctx->var, mode))
+    return fail(ctx, DABS_E_TOO_LARGE, "row format %d unavailable (%d stored entries)", mode, ctx->sp_nnz);
+  ctx->rows_mode = mode;
+  return DABS_OK;
+}
+
+int dabs_get_rows(const dabs_ctx* ctx, int32_t* mode, int32_t* nnz) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  if (mode) *mode = ctx->rows_mode;
+  if (nnz) *nnz = ctx->sp_nnz;
   return DABS_OK;
 }
 
 int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* chunks,
                   float* ns_per_flip, float* table) {
   if (!ctx || generations < 1) return DABS_E_INVALID_ARG;
-  static const int cand[DABS_N_VARIANTS][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4},
-                                               {4, 1}, {4, 2}, {4, 4}, {8, 1}, {8, 2}, {8, 4},
-                                               {16, 1}, {16, 2}, {16, 4}};
+  constexpr int NV = DABS_N_VARIANTS / 3;  // dense rows, sparse in shared, sparse in global
+  static const int cand[NV][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {4, 1}, {4, 2},
+                                  {4, 4}, {8, 1}, {8, 2}, {8, 4}, {16, 1}, {16, 2}, {16, 4}};
   if (table)
     for (int q = 0; q < DABS_N_VARIANTS; ++q) table[q] = 0.f;
   // warm a throwaway solve for `generations` generations, breed the next
@@ -605,7 +685,9 @@ int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* c
   unsigned char* sp = static_cast<unsigned char*>(snap);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   const SearchVariant keep = ctx->var;
+  const int keep_rows = ctx->rows_mode;
   SearchVariant best = keep;
+  int best_rows = keep_rows;
   float best_ns = 0.f;
   do {
     if ((rc = cudaMemcpyAsync(sp, ctx->X, xb, cudaMemcpyDeviceToDevice, ctx->stream)) ||
@@ -617,10 +699,14 @@ int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* c
     }
     for (int ci = 0; ci < DABS_N_VARIANTS && !rc; ++ci) {
       SearchVariant v;
-      if (!launch_search(cand[ci][0], cand[ci][1], nullptr, nullptr, &v) || v.cap < ctx->n) continue;
+      const int rows = ci / NV;  // RowFormat
+      if (!launch_search(cand[ci % NV][0], cand[ci % NV][1], nullptr, nullptr, &v) || v.cap < ctx->n)
+        continue;
+      if (!rows_ok(ctx, v, rows)) continue;
       cudaMemcpyAsync(ctx->X, sp, xb, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaMemcpyAsync(ctx->delta, sp + xb, db, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaMemcpyAsync(ctx->E, sp + xb + db, eb, cudaMemcpyDeviceToDevice, ctx->stream);
+      ctx->rows_mode = rows;
       const SearchArgs a = solve_search_args(ctx);
       cudaEventRecord(e0, ctx->stream);
       launch_search(v.nw, v.ch, &a, ctx->stream, nullptr);
@@ -637,15 +723,16 @@ int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* c
       for (uint32_t f : fl) total += f;
       const float ns = total > 0 ? (float)(ms * 1e6 / total) : 1e30f;
       if (table) table[ci] = ns;
-      if (best_ns == 0.f || ns < best_ns) { best_ns = ns; best = v; }
+      if (best_ns == 0.f || ns < best_ns) { best_ns = ns; best = v; best_rows = rows; }
     }
   } while (0);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(ctx->stream);
   cudaFree(snap);
-  if (rc != DABS_OK) { ctx->var = keep; return rc; }
+  if (rc != DABS_OK) { ctx->var = keep; ctx->rows_mode = keep_rows; return rc; }
   ctx->var = best;
+  ctx->rows_mode = best_rows;
   if (warps) *warps = best.nw;
   if (chunks) *chunks = best.ch;
   if (ns_per_flip) *ns_per_flip = best_ns;

@@ -117,7 +117,28 @@ struct SearchArgs {
   uint32_t* flips;   // [S]
   const int32_t* order; // launch order of the slots (grouped by algorithm), or null
   int32_t spc;          // searches per CTA actually used (<= the variant's maximum; 0 = maximum)
+  // row format (single-instance launches only): 0 dense rows of W; sparse
+  // rows, where row i holds the entries sp_ent[sp_row[i] .. sp_row[i+1]), each
+  // (k << 16) | (uint16) W_ik for k != i with W_ik != 0, k ascending, both
+  // arrays padded with zeros to a multiple of four entries, read from a
+  // shared-memory copy (1) or from global memory (2)
+  int32_t sp_mode;
+  const uint32_t* sp_row;
+  const uint32_t* sp_ent;
+  int32_t sp_nnz;
 };
+
+enum RowFormat : int { ROWS_DENSE = 0, ROWS_SPARSE_SMEM = 1, ROWS_SPARSE_GLOBAL = 2 };
+
+// Dynamic shared memory of the sparse-row batch search: with the shared-memory
+// copy, the row offsets and the entries (each section padded to 16 bytes);
+// then one scratch row of ld int16 per search of the CTA.
+__host__ __device__ inline int sparse_row16(int n) { return (n + 1 + 3) / 4; }
+__host__ __device__ inline int sparse_ent16(int nnz) { return (nnz + 3) / 4; }
+__host__ __device__ inline size_t sparse_smem_bytes(int mode, int n, int nnz, int ld, int spc) {
+  const size_t copy = mode == ROWS_SPARSE_SMEM ? 16 * ((size_t)sparse_row16(n) + sparse_ent16(nnz)) : 0;
+  return copy + (size_t)spc * ld * 2;
+}
 
 // Several instances in one batch-search launch: slot q belongs to the
 // instance i with prefix[i] <= q < prefix[i+1] and is its (q - prefix[i])-th slot.

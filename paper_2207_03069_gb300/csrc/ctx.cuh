@@ -50,6 +50,13 @@ struct dabs_ctx {
   int32_t* one_d = nullptr;
   int64_t* one_E = nullptr;
   SearchVariant var{};
+  // sparse rows of the batch search (Max-Cut- and QASP-like instances)
+  int rows_mode = 0;          // RowFormat the batch search reads
+  int sp_nnz = -1;            // stored off-diagonal non-zeros; -1 when not stored (> n^2/4)
+  size_t sp_cap = 0;          // capacity of sp_ent in entries
+  int smem_optin = 0;         // opt-in shared memory per block of the device
+  uint32_t* sp_row = nullptr; // [4 * sparse_row16(n)]
+  uint32_t* sp_ent = nullptr; // [sp_cap], owned here (not in allocs: it is resized)
   // tensor-core recompute (tcgen05): W limbs, bf16 copy of the vectors, maps
   int recompute_mode = 0;     // 0 = CUDA cores, 1 = tensor cores
   bool tc_ready = false;

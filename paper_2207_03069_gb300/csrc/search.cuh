@@ -21,12 +21,14 @@
 // order from the window start).
 #pragma once
 #include "common.cuh"
+#include "kernels.cuh"
 
 namespace dabs {
 
-template <int NW_, int CH_>
+template <int NW_, int CH_, int RF_ = ROWS_DENSE>
 struct Cfg {
   static constexpr int NW = NW_, CH = CH_;
+  static constexpr int RF = RF_;               // row format (RowFormat)
   static constexpr int NT = 32 * NW;           // threads per search
   static constexpr int EPT = 8 * CH;           // bits per thread
   static constexpr int SPAN = 8 * NT;          // bits per chunk
@@ -97,6 +99,12 @@ struct Searcher {
   int n, ld;
   int ring_len, ring_head;  // tabu ring (uniform); entry j lives in lane j's ringv
   int ringv;
+  // sparse rows (C::RF != ROWS_DENSE): offsets and entries (shared or global
+  // memory), and this search's scratch row in shared memory, all zero between
+  // flips
+  const uint32_t* srow = nullptr;
+  const uint32_t* sent = nullptr;
+  int16_t* scr = nullptr;
 
   __device__ __forceinline__ Searcher(const SearchArgs& a, SmemSearch<C>* smem, int tid,
                                       uint32_t sidx, uint32_t gen, uint64_t sd)
@@ -199,10 +207,47 @@ struct Searcher {
   // flight: row_load issues the loads of row i of sigma(x_i) W (x_i = xi
   // before the flip), row_apply updates E and Delta by Eqs. (4) and (5)
   // (di = Delta_i before the flip) and flips x_i.
+  __device__ __forceinline__ static void group_sync() {
+    if constexpr (NW == 1) __syncwarp();
+    else __syncthreads();
+  }
   __device__ __forceinline__ void row_load(int i, int xi, uint4 (&rv)[CH]) const {
     // every selector yields 0 <= i < n; the clamp only keeps a logic error
     // from turning into an out-of-bounds read (parity tests would flag it)
     i = min(max(i, 0), n - 1);
+    if constexpr (C::RF != ROWS_DENSE) {
+      // scatter sigma(x_i) W_ik of the stored entries into the zeroed scratch
+      // row, then every thread reads its chunks exactly as from a dense row
+      // and clears them again; the first barrier orders the previous flip's
+      // clearing before this scatter
+      group_sync();
+      uint32_t b, e;
+      if constexpr (C::RF == ROWS_SPARSE_GLOBAL) {
+        b = __ldg(srow + i);
+        e = __ldg(srow + i + 1);
+      } else {
+        b = srow[i];
+        e = srow[i + 1];
+      }
+      for (uint32_t j = b + (uint32_t)t; j < e; j += NT) {
+        const uint32_t en = C::RF == ROWS_SPARSE_GLOBAL ? __ldg(sent + j) : sent[j];
+        const int w = sext_lo(en);
+        scr[en >> 16] = (int16_t)(xi ? w : -w);
+      }
+      group_sync();
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int off = c * SPAN + 8 * t;
+        if (off < ld) {
+          uint4* q = reinterpret_cast<uint4*>(scr + off);
+          rv[c] = *q;
+          *q = make_uint4(0, 0, 0, 0);
+        } else {
+          rv[c] = make_uint4(0, 0, 0, 0);
+        }
+      }
+      return;
+    }
     const int16_t* row = (xi ? W : Wneg) + (size_t)i * ld;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -764,15 +809,33 @@ struct Searcher {
   }
 };
 
-template <int NW, int CH>
-__global__ void __launch_bounds__(Cfg<NW, CH>::CTA, 1)
+template <int NW, int CH, int RF>
+__global__ void __launch_bounds__(Cfg<NW, CH, RF>::CTA, 1)
     k_batch_search(const SearchArgs single, const MultiArgs multi) {
-  using C = Cfg<NW, CH>;
+  using C = Cfg<NW, CH, RF>;
   __shared__ SmemSearch<C> smem[C::SPC];
+  extern __shared__ __align__(16) unsigned char dsm[];
   const int sl = threadIdx.x / C::NT;
   // the launcher may use fewer searches per CTA than the maximum, so that the
   // CTAs spread over all SMs; the other warps of the CTA leave at once
   const int spc = single.spc > 0 ? single.spc : C::SPC;
+  // sparse rows (one instance per launch): the whole CTA copies the rows into
+  // shared memory (RF = ROWS_SPARSE_SMEM) and clears the scratch rows
+  int c16 = 0;  // 16-byte units before the scratch rows
+  if constexpr (RF != ROWS_DENSE) {
+    const int r16 = sparse_row16(single.n), e16 = sparse_ent16(single.sp_nnz);
+    uint4* d4 = reinterpret_cast<uint4*>(dsm);
+    if constexpr (RF == ROWS_SPARSE_SMEM) {
+      const uint4* gr = reinterpret_cast<const uint4*>(single.sp_row);
+      const uint4* ge = reinterpret_cast<const uint4*>(single.sp_ent);
+      for (int q = threadIdx.x; q < r16; q += blockDim.x) d4[q] = gr[q];
+      for (int q = threadIdx.x; q < e16; q += blockDim.x) d4[r16 + q] = ge[q];
+      c16 = r16 + e16;
+    }
+    const int z16 = spc * single.ld / 8;
+    for (int q = threadIdx.x; q < z16; q += blockDim.x) d4[c16 + q] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+  }
   if (sl >= spc) return;
   const uint32_t slot = blockIdx.x * spc + sl;
   // one instance (single) or several (multi: find the slot's instance)
@@ -796,9 +859,55 @@ __global__ void __launch_bounds__(Cfg<NW, CH>::CTA, 1)
   const DevCtrl* ctrl = a.ctrl;
   if (ctrl->done) return;
   Searcher<C> sr(a, &smem[sl], threadIdx.x % C::NT, s, ctrl->g, ctrl->seed);
+  if constexpr (RF == ROWS_SPARSE_SMEM) {
+    sr.srow = reinterpret_cast<const uint32_t*>(dsm);
+    sr.sent = sr.srow + 4 * sparse_row16(a.n);
+  } else if constexpr (RF == ROWS_SPARSE_GLOBAL) {
+    sr.srow = a.sp_row;
+    sr.sent = a.sp_ent;
+  }
+  if constexpr (RF != ROWS_DENSE)
+    sr.scr = reinterpret_cast<int16_t*>(dsm + 16 * (size_t)c16) + (size_t)sl * a.ld;
   sr.load(a);
   sr.run(a.algo[s], a.seed_mode, a.T, a.tau, a.B);
   sr.store(a);
+}
+
+template <int NW, int CH, int RF>
+void launch_rows(const SearchArgs& a, const MultiArgs& m, unsigned grid, cudaStream_t st) {
+  size_t dyn = 0;
+  if constexpr (RF != ROWS_DENSE) {
+    dyn = sparse_smem_bytes(RF, a.n, a.sp_nnz, a.ld, a.spc);
+    // a size above the device's limit makes the launch fail (the caller reads
+    // the error); the host only selects a sparse format that fits
+    cudaFuncSetAttribute(k_batch_search<NW, CH, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)dyn);
+  }
+  k_batch_search<NW, CH, RF><<<grid, Cfg<NW, CH, RF>::CTA, dyn, st>>>(a, m);
+}
+
+// Launches one variant over `slots` searches of one instance (m == nullptr)
+// or of the instances listed in *m.  A single instance whose arguments carry
+// sparse rows runs the sparse-row kernel of its format.
+template <int NW, int CH>
+bool launch_variant(const SearchArgs* a, cudaStream_t st, SearchVariant* v, const MultiArgs* m) {
+  using C = Cfg<NW, CH>;
+  if (v) *v = SearchVariant{NW, CH, C::CAP, C::CTA, C::SPC};
+  if (!a) return true;
+  const int slots = m ? m->total : a->S;
+  if (slots <= 0) return true;
+  SearchArgs a2 = *a;
+  a2.spc = spc_for(slots, C::SPC);
+  const unsigned grid = (unsigned)((slots + a2.spc - 1) / a2.spc);
+  const MultiArgs mm = m ? *m : MultiArgs{nullptr, nullptr, 0, 0};
+  const int mode = (m || !a2.sp_row) ? ROWS_DENSE : a2.sp_mode;
+  if (mode == ROWS_SPARSE_SMEM)
+    launch_rows<NW, CH, ROWS_SPARSE_SMEM>(a2, mm, grid, st);
+  else if (mode == ROWS_SPARSE_GLOBAL)
+    launch_rows<NW, CH, ROWS_SPARSE_GLOBAL>(a2, mm, grid, st);
+  else
+    launch_rows<NW, CH, ROWS_DENSE>(a2, mm, grid, st);
+  return true;
 }
 
 }  // namespace dabs

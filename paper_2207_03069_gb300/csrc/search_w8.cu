@@ -1,7 +1,7 @@
 // search_w8.cu -- batch-search kernel variants with 8 warp(s) per search
-// (one translation unit per warp count so the variants compile in parallel).
+// (one translation unit per warp count so the variants compile in parallel);
+// each variant is built for dense rows and for shared-memory sparse rows.
 #include "search.cuh"
-#include "kernels.cuh"
 
 namespace dabs {
 
@@ -10,48 +10,9 @@ namespace dabs {
 bool launch_search_w8(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
                        const MultiArgs* m) {
   switch (ch) {
-    case 1: {
-      using C = Cfg<8, 1>;
-      if (v) *v = SearchVariant{8, 1, C::CAP, C::CTA, C::SPC};
-      if (a) {
-        const int slots = m ? m->total : a->S;
-        SearchArgs a2 = *a;
-        a2.spc = spc_for(slots, C::SPC);
-        a = &a2;
-        if (slots > 0)
-          k_batch_search<8, 1><<<(slots + a->spc - 1) / a->spc, C::CTA, 0, st>>>(
-              *a, m ? *m : MultiArgs{nullptr, nullptr, 0, 0});
-      }
-      return true;
-    }
-    case 2: {
-      using C = Cfg<8, 2>;
-      if (v) *v = SearchVariant{8, 2, C::CAP, C::CTA, C::SPC};
-      if (a) {
-        const int slots = m ? m->total : a->S;
-        SearchArgs a2 = *a;
-        a2.spc = spc_for(slots, C::SPC);
-        a = &a2;
-        if (slots > 0)
-          k_batch_search<8, 2><<<(slots + a->spc - 1) / a->spc, C::CTA, 0, st>>>(
-              *a, m ? *m : MultiArgs{nullptr, nullptr, 0, 0});
-      }
-      return true;
-    }
-    case 4: {
-      using C = Cfg<8, 4>;
-      if (v) *v = SearchVariant{8, 4, C::CAP, C::CTA, C::SPC};
-      if (a) {
-        const int slots = m ? m->total : a->S;
-        SearchArgs a2 = *a;
-        a2.spc = spc_for(slots, C::SPC);
-        a = &a2;
-        if (slots > 0)
-          k_batch_search<8, 4><<<(slots + a->spc - 1) / a->spc, C::CTA, 0, st>>>(
-              *a, m ? *m : MultiArgs{nullptr, nullptr, 0, 0});
-      }
-      return true;
-    }
+    case 1: return launch_variant<8, 1>(a, st, v, m);
+    case 2: return launch_variant<8, 2>(a, st, v, m);
+    case 4: return launch_variant<8, 4>(a, st, v, m);
     default: return false;
   }
 }

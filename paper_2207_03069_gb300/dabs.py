@@ -24,6 +24,9 @@ N_MAX = 16384
 INT64_MAX = np.iinfo(np.int64).max
 INT64_MIN = np.iinfo(np.int64).min
 STAGE_OFFSPRING, STAGE_SEARCH, STAGE_MERGE, STAGE_FINALIZE = range(4)
+# row formats of the batch search (dabs_set_rows) and their variant-name suffixes
+ROWS_DENSE, ROWS_SPARSE_SMEM, ROWS_SPARSE_GLOBAL = range(3)
+ROW_SUFFIX = ("", "s", "g")
 
 
 class Params(C.Structure):
@@ -69,6 +72,8 @@ EXPORTS = {
     "dabs_write_results": (C.c_int, [C.c_void_p] * 6),
     "dabs_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
     "dabs_read_stats": (C.c_int, [C.c_void_p] * 5),
+    "dabs_set_rows": (C.c_int, [C.c_void_p, C.c_int32]),
+    "dabs_get_rows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dabs_solve_restarts": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dabs_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dabs_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
@@ -275,14 +280,39 @@ class Context:
     VARIANTS = ((1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (4, 1), (4, 2), (4, 4), (8, 1),
                 (8, 2), (8, 4), (16, 1), (16, 2), (16, 4))
 
+    def set_rows(self, mode: int):
+        """Row format of the batch search: ROWS_DENSE, ROWS_SPARSE_SMEM or
+        ROWS_SPARSE_GLOBAL."""
+        self._ck(lib().dabs_set_rows(self._h, int(mode)))
+
+    def rows(self):
+        """(row format, stored off-diagonal non-zeros or -1)"""
+        md, nnz = C.c_int32(), C.c_int32()
+        self._ck(lib().dabs_get_rows(self._h, C.byref(md), C.byref(nnz)))
+        return int(md.value), int(nnz.value)
+
+    def variant_name(self) -> str:
+        i = self.info()
+        return "%dx%d%s" % (i["warps"], i["chunks"], ROW_SUFFIX[self.rows()[0]])
+
+    def set_variant_name(self, name: str):
+        """'WxC' (dense rows), 'WxCs' (sparse rows in shared memory) or 'WxCg'
+        (sparse rows in global memory)"""
+        mode = ROW_SUFFIX.index(name[-1]) if name[-1] in "sg" else ROWS_DENSE
+        w, c = (int(x) for x in name.rstrip("sg").split("x"))
+        self.set_variant(w, c)
+        self.set_rows(mode)
+
     def autotune(self, generations: int = 2):
-        """Picks the fastest batch-search variant; resets the solve state.
-        Returns (warps, chunks, ns_per_flip, {"WxC": ns_per_flip})."""
+        """Picks the fastest batch-search variant and row format; resets the
+        solve state.  Returns (warps, chunks, ns_per_flip, {name: ns_per_flip})
+        with names as in variant_name()."""
         w, c, ns = C.c_int32(), C.c_int32(), C.c_float()
-        table = np.zeros(len(self.VARIANTS), np.float32)
+        names = ["%dx%d%s" % (v + (sfx,)) for sfx in ROW_SUFFIX for v in self.VARIANTS]
+        table = np.zeros(len(names), np.float32)
         self._ck(lib().dabs_autotune(self._h, generations, C.byref(w), C.byref(c), C.byref(ns),
                                      _ptr(table)))
-        per = {"%dx%d" % v: round(float(x), 4) for v, x in zip(self.VARIANTS, table) if x > 0}
+        per = {k: round(float(x), 4) for k, x in zip(names, table) if x > 0}
         return int(w.value), int(c.value), float(ns.value), per
 
     def set_stream(self, stream):

@@ -131,6 +131,49 @@ def random_ising(n: int, r: int, density: float, seed: int):
     return J, h
 
 
+def sparse_ising(n: int, edges: int, r: int, seed: int):
+    """Sparse random Ising model of resolution r on `edges` distinct random
+    edges (Section II-C; the quantum-annealer simulation problems use 5,627
+    nodes and 40,279 edges): interactions uniform over the non-zero integers
+    in [-r, r], biases over the non-zero integers in [-4r, 4r].
+    Returns (i, j, J, h) with i < j per edge."""
+    rng = np.random.default_rng(seed)
+    if edges > n * (n - 1) // 2:
+        raise ValueError("more edges than pairs")
+    seen: set = set()
+    I, Jx = [], []
+    while len(I) < edges:
+        a = rng.integers(0, n, size=2 * (edges - len(I)) + 16)
+        b = rng.integers(0, n, size=a.size)
+        for x, y in zip(a.tolist(), b.tolist()):
+            k = (min(x, y), max(x, y))
+            if x == y or k in seen:
+                continue
+            seen.add(k)
+            I.append(k[0]); Jx.append(k[1])
+            if len(I) == edges:
+                break
+    J = rng.integers(1, r + 1, size=edges) * np.where(rng.random(edges) < 0.5, -1, 1)
+    h = rng.integers(1, 4 * r + 1, size=n) * np.where(rng.random(n) < 0.5, -1, 1)
+    return np.asarray(I, np.int64), np.asarray(Jx, np.int64), J.astype(np.int64), h.astype(np.int64)
+
+
+def sparse_ising_qubo(n: int, edges: int, r: int, seed: int) -> np.ndarray:
+    """QUBO of sparse_ising(n, edges, r, seed), converted as in ising_to_qubo
+    (W_ij = 4 J_ij, W_ii = 2 h_i - 2 sum_j J_ij) without forming the dense J."""
+    I, Jx, J, h = sparse_ising(n, edges, r, seed)
+    W = np.zeros((n, n), np.int32)
+    W[I, Jx] = 4 * J
+    W[Jx, I] = 4 * J
+    rowJ = np.zeros(n, np.int64)
+    np.add.at(rowJ, I, J)
+    np.add.at(rowJ, Jx, J)
+    W[np.arange(n), np.arange(n)] = 2 * h - 2 * rowJ
+    if np.abs(W).max() > 32767:
+        raise ValueError("weights exceed int16")
+    return W.astype(np.int16)
+
+
 def batched_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """n drawn log-uniform in [lo, hi]: n = floor(lo * (hi/lo)^u), u ~ U[0,1)."""
     rng = np.random.default_rng(seed)

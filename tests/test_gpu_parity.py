@@ -68,12 +68,15 @@ def test_host_arguments_are_validated(D):
 
 
 def bulk_case(D, orc, W, algos, variant=None, seed=11, g=5, seed_mode=0, s=(1, 4), b=(2, 1),
-              tabu=8, S=None, dflip=None):
+              tabu=8, S=None, dflip=None, rows=None):
     n = W.shape[0]
     S = S or len(algos)
     ctx = ctx_for(D, W, searches=S, pools=1, pool_cap=4, s=s, b=b, tabu=tabu, seed_mode=seed_mode)
     if variant:
         ctx.set_variant(*variant)
+    if rows is not None:
+        ctx.set_rows(rows)
+        assert ctx.rows()[0] == rows
     rng = np.random.default_rng(seed + n)
     X0 = (rng.random((S, n)) < 0.5).astype(np.uint8)
     Dt = (rng.random((S, n)) < 0.5).astype(np.uint8)
@@ -101,7 +104,7 @@ def bulk_case(D, orc, W, algos, variant=None, seed=11, g=5, seed_mode=0, s=(1, 4
     gb = wl.unpack_bits(bX.cpu().numpy().view(np.uint32), n)
     for si in range(S):
         r = orc.batch_search(W, p, seed, g, si, X0[si], d0[si], int(E0[si]), Dt[si], int(algos[si]))
-        ctx_msg = f"n={n} slot={si} algo={algos[si]} variant={ctx.info()['warps'], ctx.info()['chunks']}"
+        ctx_msg = f"n={n} slot={si} algo={algos[si]} variant={ctx.variant_name()}"
         assert int(fl[si]) == r["flips"], ctx_msg
         assert int(bE[si]) == r["best_E"], ctx_msg
         assert np.array_equal(gb[si], r["best_X"]), ctx_msg
@@ -318,7 +321,7 @@ def test_autotune_keeps_results(D, orc):
               max_generations=3)
     ctx = D.Context(W, **kw)
     w, c, ns, table = ctx.autotune(1)
-    assert 256 * w * c >= n and ns > 0 and table["%dx%d" % (w, c)] == min(table.values())
+    assert 256 * w * c >= n and ns > 0 and table[ctx.variant_name()] == min(table.values())
     gx, ge, gf = ctx.solve(10**9, seed=2)
     ox, oe, of, _ = orc.solve(W, orc.make_params(**kw), 10**9, 2, threads=4)
     assert (ge, gf) == (oe, of) and np.array_equal(gx, ox)
@@ -358,3 +361,118 @@ def test_abs_mode_solve_at_size_matches_oracle(D, orc):
     gx, ge, gf = ctx.solve(10**9, seed=5)
     ox, oe, of, og = orc.solve(W, orc.make_params(**kw), 10**9, 5, threads=4)
     assert (ge, gf) == (oe, of) and np.array_equal(gx, ox)
+
+
+# ---------------------------------------------------------------- sparse rows
+SPARSE = [1, 2]  # ROWS_SPARSE_SMEM, ROWS_SPARSE_GLOBAL
+
+
+@pytest.mark.parametrize("rows", SPARSE)
+@pytest.mark.parametrize("n", [1, 2, 5, 31, 33, 64, 100, 257, 800])
+def test_sparse_rows_bulk_search_matches_oracle(D, orc, n, rows):
+    """Step 3 from sparse rows (shared-memory copy or global memory, scattered
+    into a scratch row) gives the oracle's trajectories: Max-Cut rows (+-2)
+    and a resolution-256 Ising model (weights up to 1024, diagonal larger)."""
+    bulk_case(D, orc, wl.maxcut_qubo(n, 0.06 if n > 50 else 0.3, seed=n), ALGOS, rows=rows)
+    if n >= 5:
+        m = min(2 * n, n * (n - 1) // 2)
+        bulk_case(D, orc, wl.sparse_ising_qubo(n, m, 256, seed=n), ALGOS, rows=rows, seed=12)
+
+
+@pytest.mark.parametrize("rows", SPARSE)
+@pytest.mark.parametrize("variant", [(1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (4, 1),
+                                     (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (16, 1), (16, 2),
+                                     (16, 4)])
+def test_sparse_rows_every_variant_matches_oracle(D, orc, variant, rows):
+    nw, ch = variant
+    cap = 256 * nw * ch
+    for n in sorted({max(5, cap // 3 + 5), cap - 7}):
+        W = wl.sparse_ising_qubo(n, 2 * n, 256, seed=n + 2)
+        ctx = ctx_for(D, W, searches=5, pools=1, pool_cap=4)
+        ctx.set_variant(nw, ch)
+        try:
+            ctx.set_rows(rows)
+        except D.DabsError as e:  # the shared-memory copy of a large instance does not fit
+            assert rows == 1 and e.code == D.E_TOO_LARGE and n > 4000
+            continue
+        bulk_case(D, orc, W, [0, 1, 2, 3, 4], variant=variant, s=(1, 32), b=(1, 4), dflip=0.02,
+                  rows=rows)
+
+
+def test_sparse_rows_extreme_and_dense_weights(D, orc):
+    """+-32767 weights through the scatter (both signs of sigma(x_i)), and a
+    fully dense W held as sparse rows (every entry non-zero)."""
+    n = 300
+    W = wl.sparse_ising_qubo(n, 500, 1, seed=3).astype(np.int32)
+    W[W != 0] = np.where(W[W != 0] > 0, 32767, -32767)
+    W = W.astype(np.int16)
+    for rows in SPARSE:
+        bulk_case(D, orc, W, ALGOS, rows=rows, s=(1, 8), b=(1, 1))
+    # n^2/4 off-diagonal non-zeros: the most that is stored; dense rows by default
+    Wd = wl.sparse_ising_qubo(120, 1800, 256, seed=1)
+    ctx = ctx_for(D, Wd, searches=4, pools=1)
+    assert ctx.rows() == (0, 120 * 120 // 4)
+    for rows in SPARSE:
+        bulk_case(D, orc, Wd, ALGOS, rows=rows, s=(1, 8), b=(1, 1))
+
+
+def test_row_format_defaults_and_limits(D):
+    kw = dict(searches=64, pools=4, pool_cap=16)
+    mc = D.Context(wl.maxcut_qubo(800, 0.06, seed=1), **kw)
+    assert mc.rows()[0] == D.ROWS_SPARSE_SMEM
+    qa = D.Context(wl.sparse_ising_qubo(5627, 40279, 256, seed=6), **kw)
+    assert qa.rows() == (D.ROWS_SPARSE_GLOBAL, 80558)  # 322 KB of entries: not in shared memory
+    with pytest.raises(D.DabsError) as e:
+        qa.set_rows(D.ROWS_SPARSE_SMEM)
+    assert e.value.code == D.E_TOO_LARGE
+    dn = D.Context(wl.dense_qubo(2000, -100, 100, seed=1), **kw)
+    assert dn.rows() == (D.ROWS_DENSE, -1)  # more than n^2/4 non-zeros: not stored
+    for mode in SPARSE:
+        with pytest.raises(D.DabsError):
+            dn.set_rows(mode)
+    with pytest.raises(D.DabsError):
+        mc.set_rows(3)
+    # new weights of the same size: a format that no longer applies falls back
+    mc.load_weights(wl.dense_qubo(800, -100, 100, seed=2))
+    assert mc.rows() == (D.ROWS_DENSE, -1)
+    mc.load_weights(wl.maxcut_qubo(800, 0.06, seed=1))
+    mc.set_rows(D.ROWS_SPARSE_GLOBAL)
+    assert mc.rows()[0] == D.ROWS_SPARSE_GLOBAL
+
+
+@pytest.mark.parametrize("n,gen", [(800, "maxcut"), (2000, "ising")])
+def test_sparse_rows_solve_equals_dense_and_oracle(D, orc, n, gen):
+    """Whole generations (pools, state, global best) do not depend on the row
+    format; the oracle agrees on sampled searches."""
+    W = (wl.maxcut_qubo(n, 0.06, seed=1) if gen == "maxcut"
+         else wl.sparse_ising_qubo(n, 6 * n, 16, seed=2))
+    kw = dict(searches=256, pools=4, pool_cap=32, tabu=8, s=(1, 10), b=(2, 1), seed_mode=0)
+    outs = []
+    for mode in (0, 1, 2):
+        ctx = D.Context(W, **kw)
+        try:
+            ctx.set_rows(mode)
+        except D.DabsError:
+            assert mode == 1
+            continue
+        ctx.solve_begin(7)
+        ctx.solve_generations(3)
+        outs.append((ctx.read_pools(), ctx.read_state(), ctx.solve_status(), ctx.solve_best(),
+                     ctx.read_generation()))
+    for o in outs[1:]:
+        assert o[2] == outs[0][2]
+        for a, b in zip(o[0] + o[1] + o[3] + o[4], outs[0][0] + outs[0][1] + outs[0][3] + outs[0][4]):
+            assert np.array_equal(np.asarray(a), np.asarray(b))
+    so = orc.Solver(W, orc.make_params(**kw), 7)
+    for _ in range(2):
+        so.generation(threads=16)
+    oD, oa, oo = so.offspring(2)
+    Dg, ag, og, bX, bE, fl = outs[-1][4]
+    assert np.array_equal(wl.unpack_bits(Dg, n), oD) and np.array_equal(ag, oa)
+    X2, d2, E2 = so.state()
+    p = orc.make_params(**kw)
+    gb = wl.unpack_bits(bX, n)
+    for s in np.random.default_rng(0).choice(256, 12, replace=False):
+        r = orc.batch_search(W, p, 7, 2, int(s), X2[s], d2[s], int(E2[s]), oD[s], int(oa[s]))
+        assert int(fl[s]) == r["flips"] and int(bE[s]) == r["best_E"]
+        assert np.array_equal(gb[s], r["best_X"])

@@ -66,6 +66,26 @@ def test_ising_qubo_identity(orc, seed):
         assert orc.energy(W16, X) == ising_H(J, h, 2 * X.astype(np.int64) - 1) + offset
 
 
+@pytest.mark.parametrize("r", [1, 16, 256])
+def test_sparse_ising_generator(orc, r):
+    """Section II-C resolution-r model on random edges: value sets, the edge
+    count, and E(X) = H(S) + offset over all 2^10 vectors."""
+    n, m = 10, 17
+    I, Jx, J, h = wl.sparse_ising(n, m, r, seed=r)
+    assert len(set(zip(I.tolist(), Jx.tolist()))) == m and (I < Jx).all()
+    assert (np.abs(J) >= 1).all() and (np.abs(J) <= r).all()
+    assert (np.abs(h) >= 1).all() and (np.abs(h) <= 4 * r).all()
+    Jd = np.zeros((n, n), np.int64)
+    Jd[I, Jx] = J
+    Jd = Jd + Jd.T
+    W = wl.sparse_ising_qubo(n, m, r, seed=r)
+    W2, offset = wl.ising_to_qubo(Jd, h)
+    assert np.array_equal(W, W2.astype(np.int16))
+    for bits in itertools.product([0, 1], repeat=n):
+        X = np.asarray(bits, np.uint8)
+        assert orc.energy(W, X) == ising_H(Jd, h, 2 * X.astype(np.int64) - 1) + offset
+
+
 @pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (7, 2), (33, 3)])
 def test_energy_matches_definition(orc, n, seed):
     W = wl.dense_qubo(n, -1000, 1000, seed)
