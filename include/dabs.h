@@ -251,7 +251,7 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
  *   DABS_ROWS_SPARSE_GLOBAL  the same entries read from global memory (L2).
  * With sparse rows a flip scatters row i into a zeroed per-search scratch row
  * in shared memory, so it reads 4 bytes per non-zero instead of 2n bytes.
- * Sparse rows are stored while the non-zeros are at most n^2/4; TOO_LARGE
+ * Sparse rows are stored while the non-zeros are at most max(n^2/4, 64); TOO_LARGE
  * when they are not, or when the format's shared memory (the copy, about
  * 56,000 entries at most on this GPU, and ld int16 per search of a CTA)
  * exceeds the device's opt-in size per block.  The default is shared-memory

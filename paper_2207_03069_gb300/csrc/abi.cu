@@ -88,8 +88,9 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
   CK(cudaMemcpy(ctx->Wneg, neg.data(), neg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->diag, dg.data(), dg.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   // sparse rows: the off-diagonal non-zeros of each row, column ascending,
-  // kept while they take at most half the bytes of the dense rows
-  const size_t limit = (size_t)n * n / 4;
+  // kept while they take at most half the bytes of the dense rows (or 64
+  // entries, for tiny instances)
+  const size_t limit = std::max<size_t>((size_t)n * n / 4, 64);
   std::vector<uint32_t> rp(4 * (size_t)sparse_row16(n), 0), ent;
   bool keep = true;
   for (int i = 0; i < n && keep; ++i) {
