@@ -373,7 +373,7 @@ def test_sparse_rows_bulk_search_matches_oracle(D, orc, n, rows):
     """Step 3 from sparse rows (shared-memory copy or global memory, scattered
     into a scratch row) gives the oracle's trajectories: Max-Cut rows (+-2)
     and a resolution-256 Ising model (weights up to 1024, diagonal larger)."""
-    bulk_case(D, orc, wl.maxcut_qubo(n, 0.06 if n > 50 else 0.3, seed=n), ALGOS, rows=rows)
+    bulk_case(D, orc, wl.maxcut_qubo(n, 0.06 if n > 50 else 0.15, seed=n), ALGOS, rows=rows)
     if n >= 5:
         m = min(2 * n, n * (n - 1) // 2)
         bulk_case(D, orc, wl.sparse_ising_qubo(n, m, 256, seed=n), ALGOS, rows=rows, seed=12)
