@@ -40,6 +40,9 @@ WORKLOADS = {
                     pool_cap=64, tabu=8, s=(1, 10), b=(1, 1), seed_mode=0),
     "tsp32": dict(desc="TSP one-hot 32 cities (1024 bits) grid 1000 seed 2", n=1024,
                   searches=2048, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=0),
+    "qasp5627": dict(desc="QASP-shaped sparse Ising r=256, 5627 nodes 40279 random edges, seed 6",
+                     n=5627, searches=1024, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1),
+                     seed_mode=0),
 }
 
 
@@ -50,6 +53,8 @@ def make_W(name):
         return wl.dense_qubo(64, -100, 100, seed=0)
     if name == "tsp32":
         return wl.tsp_qubo(32, 1000, seed=2)[0]
+    if name == "qasp5627":
+        return wl.sparse_ising_qubo(5627, 40279, 256, seed=6)
     raise ValueError(name)
 
 

@@ -254,11 +254,11 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
  * Sparse rows are stored while the non-zeros are at most max(n^2/4, 64); TOO_LARGE
  * when they are not, or when the format's shared memory (the copy, about
  * 56,000 entries at most on this GPU, and ld int16 per search of a CTA)
- * exceeds the device's opt-in size per block.  The default is shared-memory
- * sparse rows when they fit, else global sparse rows, for W with at most one
- * non-zero in eight entries, and dense rows otherwise.  Results do not depend
- * on the format.  Batched launches (dabs_batch_solve, the server) read dense
- * rows. */
+ * exceeds the device's opt-in size per block.  The default is dense rows
+ * (the fastest measured on Max-Cut n = 800 and a 5,627-node sparse Ising
+ * model: the flip loop is bound by its dependency chain, not by the row
+ * read); dabs_autotune times all three.  Results do not depend on the format.
+ * Batched launches (dabs_batch_solve, the server) read dense rows. */
 enum { DABS_ROWS_DENSE = 0, DABS_ROWS_SPARSE_SMEM = 1, DABS_ROWS_SPARSE_GLOBAL = 2 };
 int dabs_set_rows(dabs_ctx* ctx, int32_t mode);
 /* Current row format and the number of stored off-diagonal non-zeros (-1

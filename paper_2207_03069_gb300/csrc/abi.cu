@@ -133,13 +133,11 @@ bool rows_ok(const dabs_ctx* ctx, const SearchVariant& v, int mode) {
   return need <= (size_t)ctx->smem_optin;
 }
 
-// sparse rows in shared memory when they fit, else from global memory, for
-// instances with at most one non-zero in eight entries; dense rows otherwise
-int default_rows(const dabs_ctx* ctx) {
-  if (ctx->sp_nnz < 0 || (int64_t)ctx->sp_nnz * 8 > (int64_t)ctx->n * ctx->n) return ROWS_DENSE;
-  if (rows_ok(ctx, ctx->var, ROWS_SPARSE_SMEM)) return ROWS_SPARSE_SMEM;
-  return rows_ok(ctx, ctx->var, ROWS_SPARSE_GLOBAL) ? ROWS_SPARSE_GLOBAL : ROWS_DENSE;
-}
+// dense rows: measured on this GPU, the sparse formats save bytes but add a
+// scatter and two group barriers per flip, which the latency-bound flip loop
+// feels more than the (L2-resident) dense row read; dabs_set_rows or the
+// autotuner select them where they win
+int default_rows(const dabs_ctx*) { return ROWS_DENSE; }
 
 int tc_limbs(dabs_ctx* ctx) {
   const size_t total = (size_t)ctx->n_pad * ctx->n_pad;

@@ -419,9 +419,11 @@ def test_sparse_rows_extreme_and_dense_weights(D, orc):
 def test_row_format_defaults_and_limits(D):
     kw = dict(searches=64, pools=4, pool_cap=16)
     mc = D.Context(wl.maxcut_qubo(800, 0.06, seed=1), **kw)
-    assert mc.rows()[0] == D.ROWS_SPARSE_SMEM
+    assert mc.rows()[0] == D.ROWS_DENSE
+    mc.set_rows(D.ROWS_SPARSE_SMEM)
     qa = D.Context(wl.sparse_ising_qubo(5627, 40279, 256, seed=6), **kw)
-    assert qa.rows() == (D.ROWS_SPARSE_GLOBAL, 80558)  # 322 KB of entries: not in shared memory
+    assert qa.rows() == (D.ROWS_DENSE, 80558)
+    qa.set_rows(D.ROWS_SPARSE_GLOBAL)  # 322 KB of entries: not in shared memory
     with pytest.raises(D.DabsError) as e:
         qa.set_rows(D.ROWS_SPARSE_SMEM)
     assert e.value.code == D.E_TOO_LARGE
