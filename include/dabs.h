@@ -261,6 +261,16 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
  * Batched launches (dabs_batch_solve, the server) read dense rows. */
 enum { DABS_ROWS_DENSE = 0, DABS_ROWS_SPARSE_SMEM = 1, DABS_ROWS_SPARSE_GLOBAL = 2 };
 int dabs_set_rows(dabs_ctx* ctx, int32_t mode);
+/* Keyed form of the batch search: each thread keeps Delta_k * 2^kb +
+ * (k << 1 | x_k) instead of Delta_k, so that every minimum of Step 1 and of
+ * the selectors also yields the lowest winning index and x_k, with no second
+ * pass.  Available when (2R + 2) 2^kb < 2^31, kb = bitlen(n-1) + 1, R =
+ * max_k sum_j |W_kj| (every Delta lies in [-R, R]); on by default (enable = 1)
+ * and used for single-instance launches with dense rows.  Results do not
+ * depend on it.  dabs_get_keyed reports the switch and kb (0: the instance
+ * does not allow it). */
+int dabs_set_keyed(dabs_ctx* ctx, int32_t enable);
+int dabs_get_keyed(const dabs_ctx* ctx, int32_t* enabled, int32_t* key_bits);
 /* Current row format and the number of stored off-diagonal non-zeros (-1
  * when sparse rows are not stored). */
 int dabs_get_rows(const dabs_ctx* ctx, int32_t* mode, int32_t* nnz);

@@ -80,6 +80,20 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
     }
     dg[i] = W[(size_t)i * n + i];
   }
+  // keyed Delta: |Delta_k| <= R_k = sum_j |W_kj| in every state, and a key
+  // (Delta << kb | k << 1 | x_k) plus the diagonal term added to it before
+  // Eq. (5) overwrites it must stay inside int32
+  {
+    int64_t R = 0;
+    for (int i = 0; i < n; ++i) {
+      int64_t r = 0;
+      for (int k = 0; k < n; ++k) r += std::abs((int)W[(size_t)i * n + k]);
+      R = std::max(R, r);
+    }
+    int kb = 1;
+    while ((1 << (kb - 1)) < n) ++kb;  // bitlen(n - 1) + 1
+    ctx->key_bits = ((2 * R + 2) << kb) < (int64_t)INT32_MAX ? kb : 0;
+  }
   uint64_t h = 1469598103934665603ull;  // FNV-1a of W, ties checkpoints to their instance
   for (size_t q = 0; q < (size_t)n * n; ++q) h = (h ^ (uint16_t)W[q]) * 1099511628211ull;
   ctx->w_hash = h;
@@ -199,6 +213,7 @@ SearchArgs solve_search_args(dabs_ctx* ctx) {
   a.X = ctx->X; a.delta = ctx->delta; a.E = ctx->E; a.D = ctx->D; a.algo = ctx->algo;
   a.best_X = ctx->bestX; a.best_E = ctx->bestE; a.flips = ctx->flips;
   a.order = ctx->order;
+  a.key_bits = ctx->keyed ? ctx->key_bits : 0;
   if (ctx->rows_mode != ROWS_DENSE) {
     a.sp_mode = ctx->rows_mode;
     a.sp_row = ctx->sp_row;
@@ -652,6 +667,19 @@ int dabs_set_rows(dabs_ctx* ctx, int32_t mode) {
   if (!rows_ok(ctx, ctx->var, mode))
     return fail(ctx, DABS_E_TOO_LARGE, "row format %d unavailable (%d stored entries)", mode, ctx->sp_nnz);
   ctx->rows_mode = mode;
+  return DABS_OK;
+}
+
+int dabs_set_keyed(dabs_ctx* ctx, int32_t enable) {
+  if (!ctx || (enable != 0 && enable != 1)) return DABS_E_INVALID_ARG;
+  ctx->keyed = enable;
+  return DABS_OK;
+}
+
+int dabs_get_keyed(const dabs_ctx* ctx, int32_t* enabled, int32_t* key_bits) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  if (enabled) *enabled = ctx->keyed;
+  if (key_bits) *key_bits = ctx->key_bits;
   return DABS_OK;
 }
 

@@ -126,6 +126,10 @@ struct SearchArgs {
   const uint32_t* sp_row;
   const uint32_t* sp_ent;
   int32_t sp_nnz;
+  // keyed Delta (single-instance dense-row launches): 0 = off; else the bits
+  // of (k << 1 | x_k) below the Delta part of a key, bitlen(n - 1) + 1, valid
+  // when (2 R + 2) 2^key_bits < 2^31 for R = max_k sum_j |W_kj|
+  int32_t key_bits;
 };
 
 enum RowFormat : int { ROWS_DENSE = 0, ROWS_SPARSE_SMEM = 1, ROWS_SPARSE_GLOBAL = 2 };

@@ -52,6 +52,8 @@ struct dabs_ctx {
   SearchVariant var{};
   // sparse rows of the batch search (Max-Cut- and QASP-like instances)
   int rows_mode = 0;          // RowFormat the batch search reads
+  int key_bits = 0;           // keyed Delta bits when the instance allows it (0: not)
+  int keyed = 1;              // 1: use the keyed form when key_bits > 0
   int sp_nnz = -1;            // stored off-diagonal non-zeros; -1 when not stored (> n^2/4)
   size_t sp_cap = 0;          // capacity of sp_ent in entries
   int smem_optin = 0;         // opt-in shared memory per block of the device

@@ -15,6 +15,12 @@
 // a whole row is read with fully coalesced 16-byte accesses.  Bit k lives at
 // local position p = 8c + e of the thread's Delta array and bit masks.
 //
+// Keyed form (C::KEY, for instances whose Delta range allows it): d holds
+// Delta_k * 2^kb + (k << 1 | x_k) instead of Delta_k.  The update of Eq. (4)
+// is the same multiply-add (sigma scaled by 2^kb), and any minimum over d
+// then carries the winning bit's index (lowest on ties) and x_k, so no
+// second pass finds the arg-min.
+//
 // Reductions use the warp reduce instructions and, for NW > 1, one
 // shared-memory slot round per reduction (double-buffered, one barrier).
 // Ties resolve to the lowest bit index (CyclicMin: the first bit in cyclic
@@ -25,10 +31,11 @@
 
 namespace dabs {
 
-template <int NW_, int CH_, int RF_ = ROWS_DENSE>
+template <int NW_, int CH_, int RF_ = ROWS_DENSE, bool KEY_ = false>
 struct Cfg {
   static constexpr int NW = NW_, CH = CH_;
   static constexpr int RF = RF_;               // row format (RowFormat)
+  static constexpr bool KEY = KEY_;            // keyed Delta (see Searcher::run_key)
   static constexpr int NT = 32 * NW;           // threads per search
   static constexpr int EPT = 8 * CH;           // bits per thread
   static constexpr int SPAN = 8 * NT;          // bits per chunk
@@ -99,6 +106,7 @@ struct Searcher {
   int n, ld;
   int ring_len, ring_head;  // tabu ring (uniform); entry j lives in lane j's ringv
   int ringv;
+  int kb = 0;               // keyed form: bits below the Delta part of a key
   // sparse rows (C::RF != ROWS_DENSE): offsets and entries (shared or global
   // memory), and this search's scratch row in shared memory, all zero between
   // flips
@@ -109,7 +117,8 @@ struct Searcher {
   __device__ __forceinline__ Searcher(const SearchArgs& a, SmemSearch<C>* smem, int tid,
                                       uint32_t sidx, uint32_t gen, uint64_t sd)
       : sm(smem), t(tid), lane(tid & 31), warp(tid >> 5), buf(0), s(sidx), g(gen), seed(sd),
-        W(a.W), Wneg(a.Wneg), n(a.n), ld(a.ld), ring_len(0), ring_head(0), ringv(0) {}
+        W(a.W), Wneg(a.Wneg), n(a.n), ld(a.ld), ring_len(0), ring_head(0), ringv(0),
+        kb(C::KEY ? a.key_bits : 0) {}
 
   // ------------------------------------------------------------ bit helpers
   __device__ __forceinline__ static bool bit_at(const uint32_t (&m)[NMW], int p) {
@@ -255,7 +264,7 @@ struct Searcher {
       rv[c] = off < ld ? __ldg(reinterpret_cast<const uint4*>(row + off)) : make_uint4(0, 0, 0, 0);
     }
   }
-  __device__ __forceinline__ void row_apply(const uint4 (&rv)[CH], int i, int di) {
+  __device__ __forceinline__ void row_apply(const uint4 (&rv)[CH], int i, int di, int xi) {
     i = min(max(i, 0), n - 1);
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -267,7 +276,8 @@ struct Searcher {
     }
     if (t == owner_t(i)) {
       const int pi = local_p(i);
-      set_flipped(pi, -di);  // Eq. (5)
+      // Eq. (5): Delta_i = -Delta_i (and x_i, in the keyed form's low bits)
+      set_flipped(pi, C::KEY ? -di * (1 << kb) + ((i << 1) | (xi ^ 1)) : -di);
       xb[0] ^= 1u << pi;
     }
     E += di;
@@ -724,7 +734,7 @@ struct Searcher {
           rr_ready = true;
         }
       }
-      row_apply(rv, i, di);
+      row_apply(rv, i, di, xi);
       if (phase == PH_MAIN && ++it == Tmain) {
         phase = PH_GREEDY;
         ++runs;
@@ -734,12 +744,230 @@ struct Searcher {
   }
 
   __device__ __forceinline__ void run(int algo, int seed_mode, int T, int tau, uint32_t B) {
-    switch (algo) {
-      case MAXMIN: run_algo<MAXMIN>(seed_mode, T, tau, B); break;
-      case CYCLICMIN: run_algo<CYCLICMIN>(seed_mode, T, tau, B); break;
-      case RANDOMMIN: run_algo<RANDOMMIN>(seed_mode, T, tau, B); break;
-      case POSITIVEMIN: run_algo<POSITIVEMIN>(seed_mode, T, tau, B); break;
-      default: run_algo<TWONEIGHBOR>(seed_mode, T, tau, B); break;
+    if constexpr (C::KEY) {
+      switch (algo) {
+        case MAXMIN: run_key<MAXMIN>(seed_mode, T, tau, B); break;
+        case CYCLICMIN: run_key<CYCLICMIN>(seed_mode, T, tau, B); break;
+        case RANDOMMIN: run_key<RANDOMMIN>(seed_mode, T, tau, B); break;
+        case POSITIVEMIN: run_key<POSITIVEMIN>(seed_mode, T, tau, B); break;
+        default: run_key<TWONEIGHBOR>(seed_mode, T, tau, B); break;
+      }
+    } else {
+      switch (algo) {
+        case MAXMIN: run_algo<MAXMIN>(seed_mode, T, tau, B); break;
+        case CYCLICMIN: run_algo<CYCLICMIN>(seed_mode, T, tau, B); break;
+        case RANDOMMIN: run_algo<RANDOMMIN>(seed_mode, T, tau, B); break;
+        case POSITIVEMIN: run_algo<POSITIVEMIN>(seed_mode, T, tau, B); break;
+        default: run_algo<TWONEIGHBOR>(seed_mode, T, tau, B); break;
+      }
+    }
+  }
+
+  // ------------------------------------------------------------ keyed batch search
+  // The same sequence and selectors as run_algo on keys: every arg-min is the
+  // minimum key itself, whose low kb bits are (k << 1 | x_k).
+  template <int ALGO>
+  __device__ __forceinline__ void run_key(int seed_mode, int T, int tau, uint32_t B) {
+    int phase = seed_mode == 0 ? PH_STRAIGHT : PH_GREEDY;
+    int runs = 0, it = 0, ws = 0;
+    const int Tmain = ALGO == TWONEIGHBOR ? 2 * n - 1 : T;
+    const uint32_t Kq = (1u << 21) / (uint32_t)T, Kr = (1u << 21) % (uint32_t)T;
+    uint32_t fup = 0, rup = 0, fdn = 1u << 21;
+    int rdn = 0;
+    uint32_t rnd0 = 0, rnd1 = 0;  // 32 MaxMin/PositiveMin draws, one per lane
+    uint2 rr[CH];                 // RandomMin draws of the current iteration
+    bool rr_ready = false;
+    const int cwin = n < 32 ? n : 32;
+    const uint32_t c8 = ((1u << 13) + (uint32_t)n - 1) / (uint32_t)n;
+    const int low = (1 << kb) - 1;  // (k << 1 | x_k) part of a key
+    const int unit = 1 << kb;       // Delta = 1 in key units
+    for (;;) {
+      int sk;  // key of the bit to flip
+      int cma[CH];
+      chunk_min_all(cma);  // Step 1: every one-bit neighbour
+      int mk;              // its minimum key
+      if (phase != PH_MAIN) {
+        // ---------------- Straight / Greedy
+        const bool st = phase == PH_STRAIGHT;
+        const uint32_t Ms = (xb[0] ^ db[0]) & vb[0];
+        int cms[CH];
+        if (st) chunk_min(Ms, cms);
+        int v[2] = {min_of(cma), st ? min_of(cms) : INT_MAX};
+        gmin(v);
+        mk = v[0];
+        if (st && v[1] == INT_MAX) {  // X == D: Straight ends
+          phase = PH_GREEDY;
+          continue;
+        }
+        const int m = mk >> kb;
+        if (E + m < Ebest) take_best((uint32_t)(mk & low), m);
+        if (!st && m >= 0) {  // local minimum: Greedy ends after Step 1
+          if (flips < B && !(ALGO == TWONEIGHBOR && runs >= 1)) {
+            phase = PH_MAIN;
+            it = 0;
+            ws = 0;
+            fup = 0;
+            rup = 0;
+            fdn = 1u << 21;
+            rdn = 0;
+            tb[0] = 0;
+            ring_len = 0;
+            ring_head = 0;
+            continue;
+          }
+          break;
+        }
+        sk = st ? v[1] : mk;
+      } else {
+        // ---------------- main search iteration t = it + 1
+        fup += Kq;
+        rup += Kr;
+        if (rup >= (uint32_t)T) { ++fup; rup -= (uint32_t)T; }
+        fdn -= Kq;
+        rdn -= (int)Kr;
+        if (rdn < 0) { --fdn; rdn += T; }
+        const uint32_t F = vb[0] & ~tb[0];  // free (non-tabu) bits
+        if (ALGO == TWONEIGHBOR) {
+          int v[1] = {min_of(cma)};
+          gmin(v);
+          mk = v[0];
+          const int i = it == 0 ? 0 : ((it & 1) ? (it + 1) >> 1 : (it >> 1) - 1);
+          int dk;
+          fetch(i, &dk);
+          sk = dk;
+        } else if (ALGO == MAXMIN || ALGO == POSITIVEMIN) {
+          if ((it & 31) == 0) {
+            const uint4 u = draw(seed, flips + (uint32_t)lane, g, s,
+                                 ALGO == MAXMIN ? RNG_MAXMIN : RNG_POSMIN);
+            rnd0 = u.x;
+            rnd1 = u.y;
+          }
+          const uint32_t u0 = __shfl_sync(FULL, rnd0, it & 31);
+          uint32_t Cm = 0, ukth = 0;
+          if (ALGO == MAXMIN) {
+            int cmn[CH], cmx[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+              int vn[8], vx[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const bool f = (F >> (8 * c + e)) & 1u;
+                vn[e] = f ? d[8 * c + e] : INT_MAX;
+                vx[e] = f ? d[8 * c + e] : INT_MIN;
+              }
+              cmn[c] = min8(vn);
+              cmx[c] = ~max8(vx);
+            }
+            int v[3] = {min_of(cma), min_of(cmn), min_of(cmx)};
+            gmin(v);
+            mk = v[0];
+            const int mn = v[1] >> kb, mx = (~v[2]) >> kb;
+            const uint64_t q = cube_of(fdn);
+            const uint64_t span = (uint64_t)((int64_t)mx - (int64_t)mn);
+            const uint64_t R = (q * span) >> 32;
+            const int thr = (int)((int64_t)mn + (int64_t)(((uint64_t)u0 * (R + 1)) >> 32));
+            const int lim = (thr + 1) * unit;  // Delta <= thr  <=>  key < lim
+#pragma unroll
+            for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)(d[p] < lim) << p;
+            Cm &= F;
+            ukth = __shfl_sync(FULL, rnd1, it & 31);
+          } else {
+            int cmp[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+              int vp[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e)
+                vp[e] = (((F >> (8 * c + e)) & 1u) && d[8 * c + e] >= unit) ? d[8 * c + e] : INT_MAX;
+              cmp[c] = min8(vp);
+            }
+            int v[2] = {min_of(cma), min_of(cmp)};
+            gmin(v);
+            mk = v[0];
+            if (v[1] != INT_MAX) {
+              const int lim = ((v[1] >> kb) + 1) * unit;
+#pragma unroll
+              for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)(d[p] < lim) << p;
+              Cm &= F;
+            } else {
+              Cm = F;
+            }
+            ukth = u0;
+          }
+          int dk;
+          kth(Cm, ukth, &dk);
+          sk = dk;
+        } else if (ALGO == CYCLICMIN) {
+          const uint64_t wl = (cube_of(fup) * (uint64_t)n) >> 32;
+          const int wsz = (int)(wl < (uint64_t)cwin ? (uint64_t)cwin : (wl > (uint64_t)n ? (uint64_t)n : wl));
+          const int hi1 = min(ws + wsz, n), hi2 = ws + wsz - n;
+          uint32_t M1 = 0, M2 = 0;
+#pragma unroll
+          for (int c = 0; c < CH; ++c) {
+            const int b0 = c * SPAN + 8 * t;
+            M1 |= run_mask(b0, ws, hi1) << (8 * c);
+            M2 |= run_mask(b0, 0, hi2) << (8 * c);
+          }
+          M1 &= F;
+          M2 &= F;
+          int cm1[CH], cm2[CH];
+          chunk_min(M1, cm1);
+          chunk_min(M2, cm2);
+          int v[3] = {min_of(cma), min_of(cm1), min_of(cm2)};
+          gmin(v);
+          mk = v[0];
+          // first in cyclic order from ws: [ws, n) before [0, ws + wsz - n)
+          sk = (v[2] == INT_MAX || (v[1] != INT_MAX && (v[1] >> kb) <= (v[2] >> kb))) ? v[1] : v[2];
+          ws += wsz;
+          if (ws >= n) ws -= n;
+        } else {  // RANDOMMIN
+          uint32_t thr = (uint32_t)(cube_of(fup) >> 24);
+          thr = thr < c8 ? c8 : (thr > 256u ? 256u : thr);
+          if (!rr_ready) randmin_draw(flips, rr);
+          rr_ready = false;
+          uint32_t Cm = 0;
+#pragma unroll
+          for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const uint32_t u8 = ((e < 4 ? rr[c].x : rr[c].y) >> (8 * (e & 3))) & 0xFFu;
+              Cm |= (uint32_t)(u8 < thr) << (8 * c + e);
+            }
+          Cm &= F;
+          int cmc[CH];
+          chunk_min(Cm, cmc);
+          int v[2] = {min_of(cma), min_of(cmc)};
+          gmin(v);
+          mk = v[0];
+          sk = v[1];
+          if (sk == INT_MAX) {  // no candidate: arg-min over the free bits (rare)
+            int cmf[CH];
+            chunk_min(F, cmf);
+            int vf[1] = {min_of(cmf)};
+            gmin(vf);
+            sk = vf[0];
+          }
+        }
+        const int m = mk >> kb;
+        if (E + m < Ebest) take_best((uint32_t)(mk & low), m);
+      }
+      const int i = (sk & low) >> 1, xi = sk & 1, di = sk >> kb;
+      uint4 rv[CH];
+      row_load(i, xi, rv);
+      // independent of row i: overlaps its load latency
+      if (phase == PH_MAIN) {
+        if (ALGO != TWONEIGHBOR) tabu_push(i, tau);
+        if (ALGO == RANDOMMIN && it + 1 < Tmain) {
+          randmin_draw(flips + 1, rr);  // draws of the next iteration
+          rr_ready = true;
+        }
+      }
+      row_apply(rv, i, di, xi);
+      if (phase == PH_MAIN && ++it == Tmain) {
+        phase = PH_GREEDY;
+        ++runs;
+        tb[0] = 0;
+      }
     }
   }
 
@@ -766,8 +994,12 @@ struct Searcher {
       for (int e = 0; e < 8; ++e) {
         const int p = 8 * c + e;
         const bool valid = base + e < n;
-        d[p] = valid ? vals[e] : INT_MAX;
-        sg[p] = ((xbyte >> e) & 1u) && valid ? 1 : -1;
+        const int xk = (int)((xbyte >> e) & 1u);
+        if constexpr (C::KEY)
+          d[p] = valid ? vals[e] * (1 << kb) + (((base + e) << 1) | xk) : INT_MAX;
+        else
+          d[p] = valid ? vals[e] : INT_MAX;
+        sg[p] = (xk && valid ? 1 : -1) * (C::KEY ? (1 << kb) : 1);
         if (valid) {
           vb[0] |= 1u << p;
           xb[0] |= ((xbyte >> e) & 1u) << p;
@@ -791,7 +1023,8 @@ struct Searcher {
       if (base < ld) {
         int vals[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) vals[e] = (base + e < n) ? d[8 * c + e] : 0;
+        for (int e = 0; e < 8; ++e)
+          vals[e] = (base + e < n) ? (C::KEY ? d[8 * c + e] >> kb : d[8 * c + e]) : 0;
         *reinterpret_cast<int4*>(dl + base) = make_int4(vals[0], vals[1], vals[2], vals[3]);
         *reinterpret_cast<int4*>(dl + base + 4) = make_int4(vals[4], vals[5], vals[6], vals[7]);
       }
@@ -809,10 +1042,10 @@ struct Searcher {
   }
 };
 
-template <int NW, int CH, int RF>
-__global__ void __launch_bounds__(Cfg<NW, CH, RF>::CTA, 1)
+template <int NW, int CH, int RF, bool KEY>
+__global__ void __launch_bounds__(Cfg<NW, CH, RF, KEY>::CTA, 1)
     k_batch_search(const SearchArgs single, const MultiArgs multi) {
-  using C = Cfg<NW, CH, RF>;
+  using C = Cfg<NW, CH, RF, KEY>;
   __shared__ SmemSearch<C> smem[C::SPC];
   extern __shared__ __align__(16) unsigned char dsm[];
   const int sl = threadIdx.x / C::NT;
@@ -873,17 +1106,17 @@ __global__ void __launch_bounds__(Cfg<NW, CH, RF>::CTA, 1)
   sr.store(a);
 }
 
-template <int NW, int CH, int RF>
+template <int NW, int CH, int RF, bool KEY = false>
 void launch_rows(const SearchArgs& a, const MultiArgs& m, unsigned grid, cudaStream_t st) {
   size_t dyn = 0;
   if constexpr (RF != ROWS_DENSE) {
     dyn = sparse_smem_bytes(RF, a.n, a.sp_nnz, a.ld, a.spc);
     // a size above the device's limit makes the launch fail (the caller reads
     // the error); the host only selects a sparse format that fits
-    cudaFuncSetAttribute(k_batch_search<NW, CH, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)dyn);
+    cudaFuncSetAttribute(k_batch_search<NW, CH, RF, KEY>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   }
-  k_batch_search<NW, CH, RF><<<grid, Cfg<NW, CH, RF>::CTA, dyn, st>>>(a, m);
+  k_batch_search<NW, CH, RF, KEY><<<grid, Cfg<NW, CH, RF, KEY>::CTA, dyn, st>>>(a, m);
 }
 
 // Launches one variant over `slots` searches of one instance (m == nullptr)
@@ -900,11 +1133,14 @@ bool launch_variant(const SearchArgs* a, cudaStream_t st, SearchVariant* v, cons
   a2.spc = spc_for(slots, C::SPC);
   const unsigned grid = (unsigned)((slots + a2.spc - 1) / a2.spc);
   const MultiArgs mm = m ? *m : MultiArgs{nullptr, nullptr, 0, 0};
+  // the keyed form runs for single-instance launches with dense rows
   const int mode = (m || !a2.sp_row) ? ROWS_DENSE : a2.sp_mode;
   if (mode == ROWS_SPARSE_SMEM)
     launch_rows<NW, CH, ROWS_SPARSE_SMEM>(a2, mm, grid, st);
   else if (mode == ROWS_SPARSE_GLOBAL)
     launch_rows<NW, CH, ROWS_SPARSE_GLOBAL>(a2, mm, grid, st);
+  else if (!m && a2.key_bits > 0)
+    launch_rows<NW, CH, ROWS_DENSE, true>(a2, mm, grid, st);
   else
     launch_rows<NW, CH, ROWS_DENSE>(a2, mm, grid, st);
   return true;

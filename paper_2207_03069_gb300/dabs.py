@@ -73,6 +73,8 @@ EXPORTS = {
     "dabs_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
     "dabs_read_stats": (C.c_int, [C.c_void_p] * 5),
     "dabs_set_rows": (C.c_int, [C.c_void_p, C.c_int32]),
+    "dabs_set_keyed": (C.c_int, [C.c_void_p, C.c_int32]),
+    "dabs_get_keyed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dabs_get_rows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dabs_solve_restarts": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dabs_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
@@ -290,6 +292,16 @@ class Context:
         md, nnz = C.c_int32(), C.c_int32()
         self._ck(lib().dabs_get_rows(self._h, C.byref(md), C.byref(nnz)))
         return int(md.value), int(nnz.value)
+
+    def set_keyed(self, enable: bool):
+        """Keyed Delta form of the batch search (used when the instance allows it)."""
+        self._ck(lib().dabs_set_keyed(self._h, int(bool(enable))))
+
+    def keyed(self):
+        """(enabled, key bits; 0 when the instance does not allow the keyed form)"""
+        en, kb = C.c_int32(), C.c_int32()
+        self._ck(lib().dabs_get_keyed(self._h, C.byref(en), C.byref(kb)))
+        return bool(en.value), int(kb.value)
 
     def variant_name(self) -> str:
         i = self.info()

@@ -68,12 +68,15 @@ def test_host_arguments_are_validated(D):
 
 
 def bulk_case(D, orc, W, algos, variant=None, seed=11, g=5, seed_mode=0, s=(1, 4), b=(2, 1),
-              tabu=8, S=None, dflip=None, rows=None):
+              tabu=8, S=None, dflip=None, rows=None, keyed=None):
     n = W.shape[0]
     S = S or len(algos)
     ctx = ctx_for(D, W, searches=S, pools=1, pool_cap=4, s=s, b=b, tabu=tabu, seed_mode=seed_mode)
     if variant:
         ctx.set_variant(*variant)
+    if keyed is not None:  # True: the instance must allow the keyed form
+        ctx.set_keyed(keyed)
+        assert not keyed or ctx.keyed()[1] > 0
     if rows is not None:
         ctx.set_rows(rows)
         assert ctx.rows()[0] == rows
@@ -117,34 +120,43 @@ def bulk_case(D, orc, W, algos, variant=None, seed=11, g=5, seed_mode=0, s=(1, 4
 ALGOS = [0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 2, 3]
 
 
+@pytest.mark.parametrize("keyed", [True, False])
 @pytest.mark.parametrize("n", [1, 2, 5, 31, 33, 64, 100, 257, 800])
-def test_bulk_search_matches_oracle(D, orc, n):
+def test_bulk_search_matches_oracle(D, orc, n, keyed):
     W = wl.dense_qubo(n, -100, 100, seed=3 * n)
-    bulk_case(D, orc, W, ALGOS)
+    bulk_case(D, orc, W, ALGOS, keyed=keyed)
 
 
 @pytest.mark.parametrize("variant", [(1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (4, 1),
                                      (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (16, 1), (16, 2),
                                      (16, 4)])
 def test_every_variant_matches_oracle(D, orc, variant):
+    """Both forms of the flip loop on every variant: wide weights (plain
+    Delta) and weights small enough for the keyed form at the same n."""
     nw, ch = variant
     cap = 256 * nw * ch
     for n in sorted({max(1, cap // 3 + 5), cap - 7}):
         W = wl.dense_qubo(n, -1000, 1000, seed=n + 1)
-        bulk_case(D, orc, W, [0, 1, 2, 3, 4], variant=variant, s=(1, 32), b=(1, 4), dflip=0.02)
+        bulk_case(D, orc, W, [0, 1, 2, 3, 4], variant=variant, s=(1, 32), b=(1, 4), dflip=0.02,
+                  keyed=False)
+        W = wl.dense_qubo(n, -2, 2, seed=n + 1)
+        bulk_case(D, orc, W, [0, 1, 2, 3, 4], variant=variant, s=(1, 32), b=(1, 4), dflip=0.02,
+                  keyed=True)
 
 
 @pytest.mark.parametrize("n", [33, 300])
 def test_bulk_search_recompute_seeding(D, orc, n):
     W = wl.dense_qubo(n, -100, 100, seed=n)
-    bulk_case(D, orc, W, ALGOS, seed_mode=1)
+    for keyed in (True, False):
+        bulk_case(D, orc, W, ALGOS, seed_mode=1, keyed=keyed)
 
 
 @pytest.mark.parametrize("tabu,s,b", [(0, (1, 4), (2, 1)), (31, (1, 2), (3, 1)),
                                       (8, (0, 1), (1, 1)), (8, (1, 4), (0, 1))])
 def test_bulk_search_parameter_edges(D, orc, tabu, s, b):
     W = wl.dense_qubo(70, -100, 100, seed=9)
-    bulk_case(D, orc, W, ALGOS, tabu=tabu, s=s, b=b)
+    for keyed in (True, False):
+        bulk_case(D, orc, W, ALGOS, tabu=tabu, s=s, b=b, keyed=keyed)
 
 
 def test_bulk_search_extreme_weights(D, orc):
@@ -152,7 +164,11 @@ def test_bulk_search_extreme_weights(D, orc):
     W = wl.dense_qubo(n, -32767, 32767, seed=1)
     bulk_case(D, orc, W, ALGOS, s=(1, 8), b=(1, 1))
     Z = np.zeros((n, n), np.int16)  # all Delta zero: ties everywhere
-    bulk_case(D, orc, Z, ALGOS, s=(1, 8), b=(1, 1))
+    bulk_case(D, orc, Z, ALGOS, s=(1, 8), b=(1, 1), keyed=True)
+    bulk_case(D, orc, Z, ALGOS, s=(1, 8), b=(1, 1), keyed=False)
+    # +-32767 at n = 64 still fits the keyed form (|Delta| < 2^21 = 2^31 / 2^7 / 2^3)
+    W64 = wl.dense_qubo(64, -32767, 32767, seed=2)
+    bulk_case(D, orc, W64, ALGOS, s=(1, 8), b=(1, 1), keyed=True)
 
 
 def compare_generation(ctx, so, n, tag):
