@@ -389,6 +389,57 @@ struct Searcher {
     return key;
   }
 
+  // Keyed form, one warp: the key of the ((u * count) >> 32)-th set bit of
+  // Cm in ascending bit order (chunk, then lane, then bit).  Bit-sliced
+  // ballots of the per-chunk counts (0..8) give every chunk's warp total and
+  // each lane's exclusive prefix at once; the lane holding the pick selects
+  // its bit by rank inside the byte, and a masked minimum returns its key.
+  __device__ __forceinline__ int kth_key(uint32_t Cm, uint32_t u) {
+    static_assert(NW == 1, "single-warp form");
+    const unsigned below = (1u << lane) - 1u;
+    int cnt[CH], tot[CH], excl[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) cnt[c] = __popc((Cm >> (8 * c)) & 0xFFu);
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      tot[c] = 0;
+      excl[c] = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const unsigned bl = __ballot_sync(FULL, (cnt[c] >> b) & 1);
+        tot[c] += __popc(bl) << b;
+        excl[c] += __popc(bl & below) << b;
+      }
+    }
+    int total = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) total += tot[c];
+    const int kk = (int)uniform_below(u, (uint32_t)total);
+    // this lane's chunk holding rank kk, if any, and the rank inside it
+    int base = 0, csel = -1, r = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int q = kk - base - excl[c];
+      if (q >= 0 && q < cnt[c]) { csel = c; r = q; }
+      base += tot[c];
+    }
+    uint32_t byte = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+      if (c == csel) byte = (Cm >> (8 * c)) & 0xFFu;
+    // position of the (r+1)-th set bit of the byte: halves, quarters, bits
+    int pos = 0;
+    const int c4 = __popc(byte & 0xFu);
+    if (r >= c4) { pos += 4; r -= c4; byte >>= 4; }
+    const int c2 = __popc(byte & 0x3u);
+    if (r >= c2) { pos += 2; r -= c2; byte >>= 2; }
+    if (r >= (int)(byte & 1u)) pos += 1;
+    const uint32_t OH = csel >= 0 ? 1u << (8 * csel + pos) : 0u;
+    int cq[CH];
+    chunk_min(OH, cq);
+    return __reduce_min_sync(FULL, min_of(cq));
+  }
+
   // Delta_i and x_i of a bit chosen without a reduction (TwoNeighbor)
   __device__ __forceinline__ uint32_t fetch(int i, int* di) {
     const int pi = local_p(i), ot = owner_t(i);
@@ -894,9 +945,13 @@ struct Searcher {
             }
             ukth = u0;
           }
-          int dk;
-          kth(Cm, ukth, &dk);
-          sk = dk;
+          if constexpr (NW == 1) {
+            sk = kth_key(Cm, ukth);
+          } else {
+            int dk;
+            kth(Cm, ukth, &dk);
+            sk = dk;
+          }
         } else if (ALGO == CYCLICMIN) {
           const uint64_t wl = (cube_of(fup) * (uint64_t)n) >> 32;
           const int wsz = (int)(wl < (uint64_t)cwin ? (uint64_t)cwin : (wl > (uint64_t)n ? (uint64_t)n : wl));
