@@ -389,57 +389,6 @@ struct Searcher {
     return key;
   }
 
-  // Keyed form, one warp: the key of the ((u * count) >> 32)-th set bit of
-  // Cm in ascending bit order (chunk, then lane, then bit).  Bit-sliced
-  // ballots of the per-chunk counts (0..8) give every chunk's warp total and
-  // each lane's exclusive prefix at once; the lane holding the pick selects
-  // its bit by rank inside the byte, and a masked minimum returns its key.
-  __device__ __forceinline__ int kth_key(uint32_t Cm, uint32_t u) {
-    static_assert(NW == 1, "single-warp form");
-    const unsigned below = (1u << lane) - 1u;
-    int cnt[CH], tot[CH], excl[CH];
-#pragma unroll
-    for (int c = 0; c < CH; ++c) cnt[c] = __popc((Cm >> (8 * c)) & 0xFFu);
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      tot[c] = 0;
-      excl[c] = 0;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const unsigned bl = __ballot_sync(FULL, (cnt[c] >> b) & 1);
-        tot[c] += __popc(bl) << b;
-        excl[c] += __popc(bl & below) << b;
-      }
-    }
-    int total = 0;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) total += tot[c];
-    const int kk = (int)uniform_below(u, (uint32_t)total);
-    // this lane's chunk holding rank kk, if any, and the rank inside it
-    int base = 0, csel = -1, r = 0;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int q = kk - base - excl[c];
-      if (q >= 0 && q < cnt[c]) { csel = c; r = q; }
-      base += tot[c];
-    }
-    uint32_t byte = 0;
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-      if (c == csel) byte = (Cm >> (8 * c)) & 0xFFu;
-    // position of the (r+1)-th set bit of the byte: halves, quarters, bits
-    int pos = 0;
-    const int c4 = __popc(byte & 0xFu);
-    if (r >= c4) { pos += 4; r -= c4; byte >>= 4; }
-    const int c2 = __popc(byte & 0x3u);
-    if (r >= c2) { pos += 2; r -= c2; byte >>= 2; }
-    if (r >= (int)(byte & 1u)) pos += 1;
-    const uint32_t OH = csel >= 0 ? 1u << (8 * csel + pos) : 0u;
-    int cq[CH];
-    chunk_min(OH, cq);
-    return __reduce_min_sync(FULL, min_of(cq));
-  }
-
   // Delta_i and x_i of a bit chosen without a reduction (TwoNeighbor)
   __device__ __forceinline__ uint32_t fetch(int i, int* di) {
     const int pi = local_p(i), ot = owner_t(i);
@@ -473,6 +422,23 @@ struct Searcher {
     if (lane == ring_head) ringv = i;
     ring_head = ring_head + 1 == tau ? 0 : ring_head + 1;
     if (t == owner_t(i)) tb[0] ^= 1u << local_p(i);
+  }
+
+  // ------------------------------------------------------------ bit masks
+  // bit p set where pred(p) holds, ORed as a balanced tree (independent terms)
+  template <class P>
+  __device__ __forceinline__ static uint32_t mask_of(P pred) {
+    uint32_t m8[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      uint32_t b[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) b[e] = (uint32_t)pred(8 * c + e) << e;
+      m8[c] = ((b[0] | b[1]) | (b[2] | b[3])) | ((b[4] | b[5]) | (b[6] | b[7]));
+    }
+    if constexpr (CH == 1) return m8[0];
+    else if constexpr (CH == 2) return m8[0] | (m8[CH > 1 ? 1 : 0] << 8);
+    else return (m8[0] | (m8[CH > 1 ? 1 : 0] << 8)) | ((m8[CH > 2 ? 2 : 0] << 16) | (m8[CH > 3 ? 3 : 0] << 24));
   }
 
   // ------------------------------------------------------------ chunk minima
@@ -918,9 +884,7 @@ struct Searcher {
             const uint64_t R = (q * span) >> 32;
             const int thr = (int)((int64_t)mn + (int64_t)(((uint64_t)u0 * (R + 1)) >> 32));
             const int lim = (thr + 1) * unit;  // Delta <= thr  <=>  key < lim
-#pragma unroll
-            for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)(d[p] < lim) << p;
-            Cm &= F;
+            Cm = mask_of([&](int p) { return d[p] < lim; }) & F;
             ukth = __shfl_sync(FULL, rnd1, it & 31);
           } else {
             int cmp[CH];
@@ -937,21 +901,15 @@ struct Searcher {
             mk = v[0];
             if (v[1] != INT_MAX) {
               const int lim = ((v[1] >> kb) + 1) * unit;
-#pragma unroll
-              for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)(d[p] < lim) << p;
-              Cm &= F;
+              Cm = mask_of([&](int p) { return d[p] < lim; }) & F;
             } else {
               Cm = F;
             }
             ukth = u0;
           }
-          if constexpr (NW == 1) {
-            sk = kth_key(Cm, ukth);
-          } else {
-            int dk;
-            kth(Cm, ukth, &dk);
-            sk = dk;
-          }
+          int dk;
+          kth(Cm, ukth, &dk);
+          sk = dk;
         } else if (ALGO == CYCLICMIN) {
           const uint64_t wl = (cube_of(fup) * (uint64_t)n) >> 32;
           const int wsz = (int)(wl < (uint64_t)cwin ? (uint64_t)cwin : (wl > (uint64_t)n ? (uint64_t)n : wl));
@@ -980,15 +938,10 @@ struct Searcher {
           thr = thr < c8 ? c8 : (thr > 256u ? 256u : thr);
           if (!rr_ready) randmin_draw(flips, rr);
           rr_ready = false;
-          uint32_t Cm = 0;
-#pragma unroll
-          for (int c = 0; c < CH; ++c)
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const uint32_t u8 = ((e < 4 ? rr[c].x : rr[c].y) >> (8 * (e & 3))) & 0xFFu;
-              Cm |= (uint32_t)(u8 < thr) << (8 * c + e);
-            }
-          Cm &= F;
+          const uint32_t Cm = mask_of([&](int p) {
+            const int c = p >> 3, e = p & 7;
+            return (((e < 4 ? rr[c].x : rr[c].y) >> (8 * (e & 3))) & 0xFFu) < thr;
+          }) & F;
           int cmc[CH];
           chunk_min(Cm, cmc);
           int v[2] = {min_of(cma), min_of(cmc)};
