@@ -250,6 +250,36 @@ def batched_vs_plain(dabs, count=64, generations=3):
             "speedup": tp / tb, "identical_results": bool(same), "flips": fl}
 
 
+def small_graphs(dabs, generations=200, reps=3):
+    """The small dense workload (n = 64, W ~ U[-100, 100] seed 0, 32 searches,
+    4 pools x 64, b = 1, s = 1/10) solved for 200 generations through
+    dabs_solve, with generations replayed from the captured CUDA graph and
+    launched kernel by kernel; best of `reps`, same seed, identical results."""
+    W = wl.dense_qubo(64, -100, 100, seed=0)
+    kw = dict(searches=32, pools=4, pool_cap=64, tabu=8, s=(1, 10), b=(1, 1), seed_mode=0,
+              max_generations=generations)
+    out, res = {}, {}
+    for graphs in (True, False):
+        ctx = dabs.Context(W, **kw)
+        ctx.set_graphs(graphs)
+        ctx.solve(10**12, seed=0)  # warm (and capture)
+        best = None
+        for _ in range(reps):
+            torch_sync()
+            t0 = time.perf_counter()
+            X, E, f = ctx.solve(10**12, seed=1)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        res[graphs] = (X.tobytes(), E, f)
+        out["graphs" if graphs else "kernel_by_kernel"] = {"flips_per_s": f / best,
+                                                           "ms_per_generation": best * 1e3 / generations}
+        ctx.close()
+    out["identical_results"] = res[True] == res[False]
+    out["speedup"] = out["kernel_by_kernel"]["ms_per_generation"] / out["graphs"]["ms_per_generation"]
+    out["workload"] = "dense n=64, 32 searches, 200 generations x >= 64 flips per search"
+    return out
+
+
 def serving(dabs, seconds=4.0, rate=50.0, generations=20, sizes=(512, 1024, 2048, 4096, 8192),
             budget_gb=60, plain=True):
     """Poisson arrivals (seed 4) of dense QUBOs, n uniform in `sizes`, 256
@@ -516,6 +546,7 @@ def main():
     rec = recompute_rate(torch, dabs, dev) if not args.no_recompute else None
     extra = {}
     if not args.no_extra and ws == 1:
+        extra["small_graphs"] = small_graphs(dabs)
         extra["time_to_target"] = tsp_ttt(dabs)
         extra["batched"] = batched_vs_plain(dabs)
         extra["serving"] = serving(dabs, seconds=args.trace_seconds)

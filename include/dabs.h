@@ -185,8 +185,14 @@ int dabs_server_set_limits(dabs_server* s, int64_t max_warps);
 /* Resets pools, search state and counters for a new solve.  Asynchronous. */
 int dabs_solve_begin(dabs_ctx* ctx, uint64_t seed, uint64_t budget, int64_t target);
 /* Enqueues `count` generations; generations after the stop condition are
- * no-ops on the device.  Asynchronous. */
+ * no-ops on the device.  By default the four kernels of a generation are
+ * captured once as a CUDA graph (on the context's stream) and the graph is
+ * launched `count` times; a change of variant, row format, keyed form,
+ * recompute mode, stream or weights captures it again.  Asynchronous. */
 int dabs_solve_generations(dabs_ctx* ctx, int32_t count);
+/* 1 (default): generations run as CUDA graph launches; 0: kernel by kernel.
+ * Results are the same. */
+int dabs_set_graphs(dabs_ctx* ctx, int32_t enable);
 /* Waits for the stream, then reports the counters. */
 int dabs_solve_status(dabs_ctx* ctx, uint64_t* flips, uint32_t* generations, int64_t* best_E,
                       int32_t* done);
@@ -248,7 +254,11 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
  *   DABS_ROWS_SPARSE_SMEM    every CTA keeps the off-diagonal non-zeros of all
  *                            rows (column << 16 | 16-bit weight, 4 bytes each,
  *                            plus n+1 row offsets) in shared memory;
- *   DABS_ROWS_SPARSE_GLOBAL  the same entries read from global memory (L2).
+ *   DABS_ROWS_SPARSE_GLOBAL  the same entries read from global memory (L2);
+ *   DABS_ROWS_DENSE_SMEM     every CTA keeps all of W (n x ld int16) in shared
+ *                            memory (one-warp variants, n up to about 330 on
+ *                            this GPU) and reads row i with 128-bit shared
+ *                            loads, negating it when x_i = 0.
  * With sparse rows a flip scatters row i into a zeroed per-search scratch row
  * in shared memory, so it reads 4 bytes per non-zero instead of 2n bytes.
  * Sparse rows are stored while the non-zeros are at most max(n^2/4, 64); TOO_LARGE
@@ -259,7 +269,8 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
  * model: the flip loop is bound by its dependency chain, not by the row
  * read); dabs_autotune times all three.  Results do not depend on the format.
  * Batched launches (dabs_batch_solve, the server) read dense rows. */
-enum { DABS_ROWS_DENSE = 0, DABS_ROWS_SPARSE_SMEM = 1, DABS_ROWS_SPARSE_GLOBAL = 2 };
+enum { DABS_ROWS_DENSE = 0, DABS_ROWS_SPARSE_SMEM = 1, DABS_ROWS_SPARSE_GLOBAL = 2,
+       DABS_ROWS_DENSE_SMEM = 3 };
 int dabs_set_rows(dabs_ctx* ctx, int32_t mode);
 /* Keyed form of the batch search: each thread keeps Delta_k * 2^kb +
  * (k << 1 | x_k) instead of Delta_k, so that every minimum of Step 1 and of
@@ -281,12 +292,12 @@ int dabs_get_rows(const dabs_ctx* ctx, int32_t* mode, int32_t* nnz);
  * (results never depend on the variant).
  * table (may be NULL) receives DABS_N_VARIANTS nanoseconds-per-flip entries
  * in the order (warps x chunks) 1x1 1x2 1x4 2x1 2x2 2x4 4x1 4x2 4x4 8x1 8x2
- * 8x4 16x1 16x2 16x4 with dense rows, then the same 15 with sparse rows in
- * shared memory and 15 with sparse rows in global memory (dabs_set_rows), 0
- * where a variant cannot hold n or the row format is unavailable.  Sets the
- * fastest variant and row format.  Resets the solve state; call before
- * dabs_solve_begin.  Synchronous. */
-#define DABS_N_VARIANTS 45
+ * 8x4 16x1 16x2 16x4 with dense rows, then the same 15 for each other row
+ * format in the order of their codes (dabs_set_rows), 0 where a variant
+ * cannot hold n or the row format is unavailable.  Sets the fastest variant
+ * and row format.  Resets the solve state; call before dabs_solve_begin.
+ * Synchronous. */
+#define DABS_N_VARIANTS 60
 int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* chunks,
                   float* ns_per_flip, float* table);
 /* Counters of the running solve (the paper's Tables V and VI): runs of each

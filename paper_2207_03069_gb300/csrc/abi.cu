@@ -132,6 +132,7 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
     ctx->sp_nnz = nnz;
   }
   if (!rows_ok(ctx, ctx->var, ctx->rows_mode)) ctx->rows_mode = ROWS_DENSE;
+  graph_stale(ctx);  // key bits, sparse-row arrays and the row format may have changed
   if (ctx->tc_ready) return tc_limbs(ctx);
   return DABS_OK;
 }
@@ -142,6 +143,8 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
 // the kernel's static arrays
 bool rows_ok(const dabs_ctx* ctx, const SearchVariant& v, int mode) {
   if (mode == ROWS_DENSE) return true;
+  if (mode == ROWS_DENSE_SMEM)  // one-warp variants; W and 2 KiB fit a block
+    return v.nw == 1 && sparse_smem_bytes(mode, ctx->n, 0, ctx->ld, v.spc) + 2048 <= (size_t)ctx->smem_optin;
   if (ctx->sp_nnz < 0 || (mode != ROWS_SPARSE_SMEM && mode != ROWS_SPARSE_GLOBAL)) return false;
   const size_t need = sparse_smem_bytes(mode, ctx->n, ctx->sp_nnz, ctx->ld, v.spc) + 2048;
   return need <= (size_t)ctx->smem_optin;
@@ -214,8 +217,8 @@ SearchArgs solve_search_args(dabs_ctx* ctx) {
   a.best_X = ctx->bestX; a.best_E = ctx->bestE; a.flips = ctx->flips;
   a.order = ctx->order;
   a.key_bits = ctx->keyed ? ctx->key_bits : 0;
-  if (ctx->rows_mode != ROWS_DENSE) {
-    a.sp_mode = ctx->rows_mode;
+  a.sp_mode = ctx->rows_mode;
+  if (ctx->rows_mode == ROWS_SPARSE_SMEM || ctx->rows_mode == ROWS_SPARSE_GLOBAL) {
     a.sp_row = ctx->sp_row;
     a.sp_ent = ctx->sp_ent;
     a.sp_nnz = ctx->sp_nnz;
@@ -361,6 +364,7 @@ const char* dabs_last_error(const dabs_ctx* ctx) { return ctx ? ctx->err.c_str()
 void dabs_destroy(dabs_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->sp_ent) cudaFree(ctx->sp_ent);
   if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
@@ -465,6 +469,7 @@ int dabs_set_stream(dabs_ctx* ctx, void* stream) {
   if (!ctx) return DABS_E_INVALID_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->stream = stream ? static_cast<cudaStream_t>(stream) : ctx->own;
+  graph_stale(ctx);
   return DABS_OK;
 }
 
@@ -545,13 +550,56 @@ int dabs_run_stage(dabs_ctx* ctx, int32_t which) {
   return stage(ctx, which);
 }
 
+// Captures one generation (the four stages) on the context's stream as a
+// CUDA graph.  Every kernel reads the generation index, seed and stop flag
+// from the device control block, so the same graph serves every generation.
+static int capture_generation(dabs_ctx* ctx) {
+  if (ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  ctx->graph_ok = false;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = DABS_OK;
+  for (int st = 0; st < 4 && rc == DABS_OK; ++st) rc = stage(ctx, st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  if (rc != DABS_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc != DABS_OK ? rc : fail(ctx, DABS_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    ctx->gexec = nullptr;
+    return fail(ctx, DABS_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+  }
+  ctx->graph_ok = true;
+  return DABS_OK;
+}
+
 int dabs_solve_generations(dabs_ctx* ctx, int32_t count) {
   if (!ctx || count < 0) return DABS_E_INVALID_ARG;
+  if (ctx->graphs && count > 0) {
+    if (!ctx->graph_ok) {
+      const int rc = capture_generation(ctx);
+      if (rc) return rc;
+    }
+    for (int32_t q = 0; q < count; ++q) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    return DABS_OK;
+  }
   for (int32_t q = 0; q < count; ++q)
     for (int st = 0; st < 4; ++st) {
       const int rc = stage(ctx, st);
       if (rc) return rc;
     }
+  return DABS_OK;
+}
+
+int dabs_set_graphs(dabs_ctx* ctx, int32_t enable) {
+  if (!ctx || (enable != 0 && enable != 1)) return DABS_E_INVALID_ARG;
+  ctx->graphs = enable;
   return DABS_OK;
 }
 
@@ -659,20 +707,23 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks) {
   if (v.cap < ctx->n) return fail(ctx, DABS_E_TOO_LARGE, "variant holds %d < n", v.cap);
   ctx->var = v;
   if (!rows_ok(ctx, v, ctx->rows_mode)) ctx->rows_mode = ROWS_DENSE;
+  graph_stale(ctx);
   return DABS_OK;
 }
 
 int dabs_set_rows(dabs_ctx* ctx, int32_t mode) {
-  if (!ctx || mode < DABS_ROWS_DENSE || mode > DABS_ROWS_SPARSE_GLOBAL) return DABS_E_INVALID_ARG;
+  if (!ctx || mode < DABS_ROWS_DENSE || mode > DABS_ROWS_DENSE_SMEM) return DABS_E_INVALID_ARG;
   if (!rows_ok(ctx, ctx->var, mode))
     return fail(ctx, DABS_E_TOO_LARGE, "row format %d unavailable (%d stored entries)", mode, ctx->sp_nnz);
   ctx->rows_mode = mode;
+  graph_stale(ctx);
   return DABS_OK;
 }
 
 int dabs_set_keyed(dabs_ctx* ctx, int32_t enable) {
   if (!ctx || (enable != 0 && enable != 1)) return DABS_E_INVALID_ARG;
   ctx->keyed = enable;
+  graph_stale(ctx);
   return DABS_OK;
 }
 
@@ -693,7 +744,7 @@ int dabs_get_rows(const dabs_ctx* ctx, int32_t* mode, int32_t* nnz) {
 int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* chunks,
                   float* ns_per_flip, float* table) {
   if (!ctx || generations < 1) return DABS_E_INVALID_ARG;
-  constexpr int NV = DABS_N_VARIANTS / 3;  // dense rows, sparse in shared, sparse in global
+  constexpr int NV = DABS_N_VARIANTS / 4;  // per RowFormat: dense, sparse shared, sparse global, dense shared
   static const int cand[NV][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {4, 1}, {4, 2},
                                   {4, 4}, {8, 1}, {8, 2}, {8, 4}, {16, 1}, {16, 2}, {16, 4}};
   if (table)
@@ -760,6 +811,7 @@ int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* c
   if (rc != DABS_OK) { ctx->var = keep; ctx->rows_mode = keep_rows; return rc; }
   ctx->var = best;
   ctx->rows_mode = best_rows;
+  graph_stale(ctx);
   if (warps) *warps = best.nw;
   if (chunks) *chunks = best.ch;
   if (ns_per_flip) *ns_per_flip = best_ns;
@@ -773,6 +825,7 @@ int dabs_set_recompute(dabs_ctx* ctx, int32_t mode) {
     if (rc) return rc;
   }
   ctx->recompute_mode = mode;
+  graph_stale(ctx);
   return DABS_OK;
 }
 

@@ -117,7 +117,8 @@ struct SearchArgs {
   uint32_t* flips;   // [S]
   const int32_t* order; // launch order of the slots (grouped by algorithm), or null
   int32_t spc;          // searches per CTA actually used (<= the variant's maximum; 0 = maximum)
-  // row format (single-instance launches only): 0 dense rows of W; sparse
+  // row format (single-instance launches only): 0 dense rows of W; 3 the same
+  // rows from a shared-memory copy of W (one-warp variants, small n); sparse
   // rows, where row i holds the entries sp_ent[sp_row[i] .. sp_row[i+1]), each
   // (k << 16) | (uint16) W_ik for k != i with W_ik != 0, k ascending, both
   // arrays padded with zeros to a multiple of four entries, read from a
@@ -132,7 +133,8 @@ struct SearchArgs {
   int32_t key_bits;
 };
 
-enum RowFormat : int { ROWS_DENSE = 0, ROWS_SPARSE_SMEM = 1, ROWS_SPARSE_GLOBAL = 2 };
+enum RowFormat : int { ROWS_DENSE = 0, ROWS_SPARSE_SMEM = 1, ROWS_SPARSE_GLOBAL = 2,
+                       ROWS_DENSE_SMEM = 3 };
 
 // Dynamic shared memory of the sparse-row batch search: with the shared-memory
 // copy, the row offsets and the entries (each section padded to 16 bytes);
@@ -140,6 +142,7 @@ enum RowFormat : int { ROWS_DENSE = 0, ROWS_SPARSE_SMEM = 1, ROWS_SPARSE_GLOBAL 
 __host__ __device__ inline int sparse_row16(int n) { return (n + 1 + 3) / 4; }
 __host__ __device__ inline int sparse_ent16(int nnz) { return (nnz + 3) / 4; }
 __host__ __device__ inline size_t sparse_smem_bytes(int mode, int n, int nnz, int ld, int spc) {
+  if (mode == ROWS_DENSE_SMEM) return (size_t)n * ld * 2;  // W itself, no scratch rows
   const size_t copy = mode == ROWS_SPARSE_SMEM ? 16 * ((size_t)sparse_row16(n) + sparse_ent16(nnz)) : 0;
   return copy + (size_t)spc * ld * 2;
 }

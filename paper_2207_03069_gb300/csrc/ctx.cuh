@@ -54,6 +54,10 @@ struct dabs_ctx {
   int rows_mode = 0;          // RowFormat the batch search reads
   int key_bits = 0;           // keyed Delta bits when the instance allows it (0: not)
   int keyed = 1;              // 1: use the keyed form when key_bits > 0
+  // one generation captured as a CUDA graph and replayed per generation
+  int graphs = 1;             // 1: dabs_solve_generations replays the graph
+  bool graph_ok = false;      // gexec matches the current launch configuration
+  cudaGraphExec_t gexec = nullptr;
   int sp_nnz = -1;            // stored off-diagonal non-zeros; -1 when not stored (> n^2/4)
   size_t sp_cap = 0;          // capacity of sp_ent in entries
   int smem_optin = 0;         // opt-in shared memory per block of the device
@@ -92,4 +96,6 @@ SearchArgs solve_search_args(dabs_ctx* ctx);
 // 3 finalise, 4 launch order only
 int stage(dabs_ctx* ctx, int which);
 int read_ctrl(dabs_ctx* ctx, DevCtrl* out);
+// the captured generation no longer matches (variant, rows, stream, ...)
+inline void graph_stale(dabs_ctx* ctx) { ctx->graph_ok = false; }
 }  // namespace dabs_internal

@@ -113,6 +113,7 @@ struct Searcher {
   const uint32_t* srow = nullptr;
   const uint32_t* sent = nullptr;
   int16_t* scr = nullptr;
+  const int16_t* sw = nullptr;  // C::RF == ROWS_DENSE_SMEM: W in shared memory
 
   __device__ __forceinline__ Searcher(const SearchArgs& a, SmemSearch<C>* smem, int tid,
                                       uint32_t sidx, uint32_t gen, uint64_t sd)
@@ -224,6 +225,18 @@ struct Searcher {
     // every selector yields 0 <= i < n; the clamp only keeps a logic error
     // from turning into an out-of-bounds read (parity tests would flag it)
     i = min(max(i, 0), n - 1);
+    if constexpr (C::RF == ROWS_DENSE_SMEM) {
+      // row i of W from shared memory; sigma(x_i) = -1 negates both halves
+      const uint4* row = reinterpret_cast<const uint4*>(sw + (size_t)i * ld);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int off = c * SPAN + 8 * t;
+        uint4 v = off < ld ? row[off >> 3] : make_uint4(0, 0, 0, 0);
+        if (!xi) v = make_uint4(__vneg2(v.x), __vneg2(v.y), __vneg2(v.z), __vneg2(v.w));
+        rv[c] = v;
+      }
+      return;
+    }
     if constexpr (C::RF != ROWS_DENSE) {
       // scatter sigma(x_i) W_ik of the stored entries into the zeroed scratch
       // row, then every thread reads its chunks exactly as from a dense row
@@ -1060,10 +1073,17 @@ __global__ void __launch_bounds__(Cfg<NW, CH, RF, KEY>::CTA, 1)
   // the launcher may use fewer searches per CTA than the maximum, so that the
   // CTAs spread over all SMs; the other warps of the CTA leave at once
   const int spc = single.spc > 0 ? single.spc : C::SPC;
-  // sparse rows (one instance per launch): the whole CTA copies the rows into
-  // shared memory (RF = ROWS_SPARSE_SMEM) and clears the scratch rows
+  // shared-memory W or sparse rows (one instance per launch): the whole CTA
+  // copies them into shared memory and clears the scratch rows
+  if constexpr (RF == ROWS_DENSE_SMEM) {
+    const int w16 = single.n * single.ld / 8;
+    uint4* d4 = reinterpret_cast<uint4*>(dsm);
+    const uint4* gw = reinterpret_cast<const uint4*>(single.W);
+    for (int q = threadIdx.x; q < w16; q += blockDim.x) d4[q] = gw[q];
+    __syncthreads();
+  }
   int c16 = 0;  // 16-byte units before the scratch rows
-  if constexpr (RF != ROWS_DENSE) {
+  if constexpr (RF == ROWS_SPARSE_SMEM || RF == ROWS_SPARSE_GLOBAL) {
     const int r16 = sparse_row16(single.n), e16 = sparse_ent16(single.sp_nnz);
     uint4* d4 = reinterpret_cast<uint4*>(dsm);
     if constexpr (RF == ROWS_SPARSE_SMEM) {
@@ -1107,8 +1127,9 @@ __global__ void __launch_bounds__(Cfg<NW, CH, RF, KEY>::CTA, 1)
     sr.srow = a.sp_row;
     sr.sent = a.sp_ent;
   }
-  if constexpr (RF != ROWS_DENSE)
+  if constexpr (RF == ROWS_SPARSE_SMEM || RF == ROWS_SPARSE_GLOBAL)
     sr.scr = reinterpret_cast<int16_t*>(dsm + 16 * (size_t)c16) + (size_t)sl * a.ld;
+  if constexpr (RF == ROWS_DENSE_SMEM) sr.sw = reinterpret_cast<const int16_t*>(dsm);
   sr.load(a);
   sr.run(a.algo[s], a.seed_mode, a.T, a.tau, a.B);
   sr.store(a);
@@ -1118,7 +1139,7 @@ template <int NW, int CH, int RF, bool KEY = false>
 void launch_rows(const SearchArgs& a, const MultiArgs& m, unsigned grid, cudaStream_t st) {
   size_t dyn = 0;
   if constexpr (RF != ROWS_DENSE) {
-    dyn = sparse_smem_bytes(RF, a.n, a.sp_nnz, a.ld, a.spc);
+    dyn = sparse_smem_bytes(RF, a.n, a.sp_nnz, a.ld, a.spc);  // also W for ROWS_DENSE_SMEM
     // a size above the device's limit makes the launch fail (the caller reads
     // the error); the host only selects a sparse format that fits
     cudaFuncSetAttribute(k_batch_search<NW, CH, RF, KEY>,
@@ -1141,8 +1162,18 @@ bool launch_variant(const SearchArgs* a, cudaStream_t st, SearchVariant* v, cons
   a2.spc = spc_for(slots, C::SPC);
   const unsigned grid = (unsigned)((slots + a2.spc - 1) / a2.spc);
   const MultiArgs mm = m ? *m : MultiArgs{nullptr, nullptr, 0, 0};
-  // the keyed form runs for single-instance launches with dense rows
-  const int mode = (m || !a2.sp_row) ? ROWS_DENSE : a2.sp_mode;
+  // the keyed form runs for single-instance launches with dense rows (from
+  // global or, one-warp variants, shared memory)
+  const int mode = m ? ROWS_DENSE
+                     : (a2.sp_mode == ROWS_DENSE_SMEM ? (NW == 1 ? ROWS_DENSE_SMEM : ROWS_DENSE)
+                                                      : (a2.sp_row ? a2.sp_mode : ROWS_DENSE));
+  if constexpr (NW == 1) {
+    if (mode == ROWS_DENSE_SMEM) {
+      if (a2.key_bits > 0) launch_rows<NW, CH, ROWS_DENSE_SMEM, true>(a2, mm, grid, st);
+      else launch_rows<NW, CH, ROWS_DENSE_SMEM>(a2, mm, grid, st);
+      return true;
+    }
+  }
   if (mode == ROWS_SPARSE_SMEM)
     launch_rows<NW, CH, ROWS_SPARSE_SMEM>(a2, mm, grid, st);
   else if (mode == ROWS_SPARSE_GLOBAL)

@@ -25,8 +25,8 @@ INT64_MAX = np.iinfo(np.int64).max
 INT64_MIN = np.iinfo(np.int64).min
 STAGE_OFFSPRING, STAGE_SEARCH, STAGE_MERGE, STAGE_FINALIZE = range(4)
 # row formats of the batch search (dabs_set_rows) and their variant-name suffixes
-ROWS_DENSE, ROWS_SPARSE_SMEM, ROWS_SPARSE_GLOBAL = range(3)
-ROW_SUFFIX = ("", "s", "g")
+ROWS_DENSE, ROWS_SPARSE_SMEM, ROWS_SPARSE_GLOBAL, ROWS_DENSE_SMEM = range(4)
+ROW_SUFFIX = ("", "s", "g", "w")
 
 
 class Params(C.Structure):
@@ -74,6 +74,7 @@ EXPORTS = {
     "dabs_read_stats": (C.c_int, [C.c_void_p] * 5),
     "dabs_set_rows": (C.c_int, [C.c_void_p, C.c_int32]),
     "dabs_set_keyed": (C.c_int, [C.c_void_p, C.c_int32]),
+    "dabs_set_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
     "dabs_get_keyed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dabs_get_rows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dabs_solve_restarts": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -283,8 +284,8 @@ class Context:
                 (8, 2), (8, 4), (16, 1), (16, 2), (16, 4))
 
     def set_rows(self, mode: int):
-        """Row format of the batch search: ROWS_DENSE, ROWS_SPARSE_SMEM or
-        ROWS_SPARSE_GLOBAL."""
+        """Row format of the batch search: ROWS_DENSE, ROWS_SPARSE_SMEM,
+        ROWS_SPARSE_GLOBAL or ROWS_DENSE_SMEM."""
         self._ck(lib().dabs_set_rows(self._h, int(mode)))
 
     def rows(self):
@@ -297,6 +298,10 @@ class Context:
         """Keyed Delta form of the batch search (used when the instance allows it)."""
         self._ck(lib().dabs_set_keyed(self._h, int(bool(enable))))
 
+    def set_graphs(self, enable: bool):
+        """Generations as CUDA graph launches (default) or kernel by kernel."""
+        self._ck(lib().dabs_set_graphs(self._h, int(bool(enable))))
+
     def keyed(self):
         """(enabled, key bits; 0 when the instance does not allow the keyed form)"""
         en, kb = C.c_int32(), C.c_int32()
@@ -308,10 +313,10 @@ class Context:
         return "%dx%d%s" % (i["warps"], i["chunks"], ROW_SUFFIX[self.rows()[0]])
 
     def set_variant_name(self, name: str):
-        """'WxC' (dense rows), 'WxCs' (sparse rows in shared memory) or 'WxCg'
-        (sparse rows in global memory)"""
-        mode = ROW_SUFFIX.index(name[-1]) if name[-1] in "sg" else ROWS_DENSE
-        w, c = (int(x) for x in name.rstrip("sg").split("x"))
+        """'WxC' (dense rows), 'WxCs' (sparse rows in shared memory), 'WxCg'
+        (sparse rows in global memory) or 'WxCw' (W in shared memory)"""
+        mode = ROW_SUFFIX.index(name[-1]) if name[-1] in "sgw" else ROWS_DENSE
+        w, c = (int(x) for x in name.rstrip("sgw").split("x"))
         self.set_variant(w, c)
         self.set_rows(mode)
 

@@ -214,6 +214,29 @@ def test_generations_match_oracle(D, orc, n, S, P, C, seed_mode):
         assert np.array_equal(got, want)
 
 
+def test_graph_generations_equal_kernel_by_kernel(D):
+    """Generations replayed from the captured CUDA graph equal generations
+    launched kernel by kernel, across a variant change (re-capture) and the
+    stop condition (replays after it are no-ops)."""
+    n = 300
+    W = wl.dense_qubo(n, -100, 100, seed=12)
+    kw = dict(searches=64, pools=4, pool_cap=16, tabu=8, s=(1, 10), b=(1, 1), max_generations=9)
+    outs = []
+    for graphs in (True, False):
+        ctx = D.Context(W, **kw)
+        ctx.set_graphs(graphs)
+        ctx.solve_begin(21)
+        ctx.solve_generations(3)
+        ctx.set_variant(2, 4)
+        ctx.solve_generations(3)
+        ctx.set_variant(1, 2)
+        ctx.solve_generations(6)  # stops after 9
+        outs.append((ctx.read_pools(), ctx.read_state(), ctx.solve_status(), ctx.solve_best()))
+    assert outs[0][2] == outs[1][2] and outs[0][2]["generations"] == 9 and outs[0][2]["done"]
+    for a, b in zip(outs[0][0] + outs[0][1] + outs[0][3], outs[1][0] + outs[1][1] + outs[1][3]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
 def test_checkpoint_restore_continues_exactly(D, orc):
     n, S = 90, 48
     W = wl.dense_qubo(n, -100, 100, seed=6)
@@ -432,6 +455,16 @@ def test_sparse_rows_extreme_and_dense_weights(D, orc):
         bulk_case(D, orc, Wd, ALGOS, rows=rows, s=(1, 8), b=(1, 1))
 
 
+@pytest.mark.parametrize("keyed", [True, False])
+@pytest.mark.parametrize("variant,n", [((1, 1), 1), ((1, 1), 5), ((1, 1), 64), ((1, 2), 257),
+                                       ((1, 4), 300), ((1, 2), 320)])
+def test_w_in_shared_memory_matches_oracle(D, orc, variant, n, keyed):
+    """Rows of W from the shared-memory copy (negated for x_i = 0) give the
+    oracle's trajectories, keyed and plain."""
+    W = wl.dense_qubo(n, -100, 100, seed=n + 40) if keyed else wl.dense_qubo(n, -32767, 32767, seed=n)
+    bulk_case(D, orc, W, ALGOS, variant=variant, rows=3, keyed=keyed)
+
+
 def test_row_format_defaults_and_limits(D):
     kw = dict(searches=64, pools=4, pool_cap=16)
     mc = D.Context(wl.maxcut_qubo(800, 0.06, seed=1), **kw)
@@ -445,11 +478,20 @@ def test_row_format_defaults_and_limits(D):
     assert e.value.code == D.E_TOO_LARGE
     dn = D.Context(wl.dense_qubo(2000, -100, 100, seed=1), **kw)
     assert dn.rows() == (D.ROWS_DENSE, -1)  # more than n^2/4 non-zeros: not stored
+    with pytest.raises(D.DabsError):
+        dn.set_rows(D.ROWS_DENSE_SMEM)  # 8 MB of W
+    sm = D.Context(wl.dense_qubo(330, -100, 100, seed=1), **kw)
+    with pytest.raises(D.DabsError):
+        sm.set_rows(D.ROWS_DENSE_SMEM)  # ld = 384: 253 KB
+    sm = D.Context(wl.dense_qubo(320, -100, 100, seed=1), **kw)
+    sm.set_rows(D.ROWS_DENSE_SMEM)  # 200 KB
+    sm.set_variant(2, 2)  # one-warp variants only: falls back to dense rows
+    assert sm.rows()[0] == D.ROWS_DENSE
     for mode in SPARSE:
         with pytest.raises(D.DabsError):
             dn.set_rows(mode)
     with pytest.raises(D.DabsError):
-        mc.set_rows(3)
+        mc.set_rows(4)
     # new weights of the same size: a format that no longer applies falls back
     mc.load_weights(wl.dense_qubo(800, -100, 100, seed=2))
     assert mc.rows() == (D.ROWS_DENSE, -1)
