@@ -131,19 +131,19 @@ struct Searcher {
   __device__ __forceinline__ uint32_t key_of(int lp) const {
     return lp < 0 ? UINT_MAX : (((uint32_t)kidx(lp) << 1) | (uint32_t)bit_at(xb, lp));
   }
-  // value of d at a run-time position (a switch, no local memory)
+  // value of d at a run-time position 0 <= p < EPT: a binary select tree on
+  // the bits of p (no branch, no local memory)
   __device__ __forceinline__ int get_at(int p) const {
-    int v = 0;
-    switch (p) {
-#define DABS_GET(q) \
-  case q:           \
-    if constexpr (q < EPT) v = d[q < EPT ? q : 0]; \
-    break;
-      DABS_CASES(DABS_GET)
-#undef DABS_GET
-      default: break;
+    int v[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) v[q] = d[q];
+#pragma unroll
+    for (int w = 1; w < EPT; w <<= 1) {
+      const bool hi = (p & w) != 0;
+#pragma unroll
+      for (int q = 0; q < EPT; q += 2 * w) v[q] = hi ? v[q + w] : v[q];
     }
-    return v;
+    return v[0];
   }
   // Eq. (5) at a run-time position: Delta_i = -Delta_i (given), sigma flips
   __device__ __forceinline__ void set_flipped(int p, int v) {
@@ -378,9 +378,16 @@ struct Searcher {
       for (int b = 0; b < 4; ++b) excl += __popc(__ballot_sync(FULL, (mycnt >> b) & 1) & below) << b;
       const int incl = excl + mycnt;
       const bool mine = excl <= rel && rel < incl;
+      // position of the (r+1)-th set bit of this lane's byte (r = rank in
+      // it): halves, quarters, bits, without a loop
       uint32_t byte = (Cm >> (8 * csel)) & 0xFFu;
-      for (int r = rel - excl; r > 0 && byte; --r) byte &= byte - 1;  // drop r lowest set bits
-      const int p = 8 * csel + (byte ? __ffs(byte) - 1 : 0);
+      int r = mine ? rel - excl : 0, pos = 0;
+      const int c4 = __popc(byte & 0xFu);
+      if (r >= c4) { pos += 4; r -= c4; byte >>= 4; }
+      const int c2 = __popc(byte & 0x3u);
+      if (r >= c2) { pos += 2; r -= c2; byte >>= 2; }
+      if (r >= (int)(byte & 1u)) pos += 1;
+      const int p = 8 * csel + pos;
       if (mine) {
         key = key_of(p);
         dv = get_at(p);
