@@ -246,8 +246,15 @@ int dabs_bulk_search_noalloc(const int16_t* W, int32_t n, int32_t ld, const dabs
  * kernel variant (warps per search, 8-bit chunks per thread). */
 int dabs_info(const dabs_ctx* ctx, int32_t* n, int32_t* ld, int32_t* words, int32_t* searches,
               int32_t* pools, int32_t* pool_cap, int32_t* warps, int32_t* chunks);
-/* Chooses the batch-search variant; returns TOO_LARGE if it cannot hold n.
- * Sparse rows stay selected only if they fit the new variant. */
+/* Chooses the batch-search variant: `warps` warps per search with `chunks`
+ * 8-bit chunks per thread and Delta in registers (n up to 256 warps chunks),
+ * or (1, 0): one warp per search with Delta in shared memory, one search per
+ * CTA (n up to DABS_N_MAX; every Delta must stay below 2^29 in magnitude,
+ * i.e. max_k sum_j |W_kj| < 2^29; it reads dense rows, fetched per lane block
+ * by bulk copies into shared memory, and its waits are bounded: a wait that
+ * runs out sets the flag dabs_kernel_status reports).  Returns TOO_LARGE if
+ * the variant cannot run the instance.  Sparse rows stay selected only if
+ * they fit the new variant. */
 int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks);
 /* Row format of the batch search (Step 3, Eq. (4) reads row i of W):
  *   DABS_ROWS_DENSE          the dense int16 rows of W in global memory;
@@ -292,12 +299,12 @@ int dabs_get_rows(const dabs_ctx* ctx, int32_t* mode, int32_t* nnz);
  * (results never depend on the variant).
  * table (may be NULL) receives DABS_N_VARIANTS nanoseconds-per-flip entries
  * in the order (warps x chunks) 1x1 1x2 1x4 2x1 2x2 2x4 4x1 4x2 4x4 8x1 8x2
- * 8x4 16x1 16x2 16x4 with dense rows, then the same 15 for each other row
+ * 8x4 16x1 16x2 16x4 1x0 with dense rows, then the same 16 for each other row
  * format in the order of their codes (dabs_set_rows), 0 where a variant
  * cannot hold n or the row format is unavailable.  Sets the fastest variant
  * and row format.  Resets the solve state; call before dabs_solve_begin.
  * Synchronous. */
-#define DABS_N_VARIANTS 60
+#define DABS_N_VARIANTS 64
 int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* chunks,
                   float* ns_per_flip, float* table);
 /* Counters of the running solve (the paper's Tables V and VI): runs of each

@@ -93,6 +93,9 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
     int kb = 1;
     while ((1 << (kb - 1)) < n) ++kb;  // bitlen(n - 1) + 1
     ctx->key_bits = ((2 * R + 2) << kb) < (int64_t)INT32_MAX ? kb : 0;
+    // the shared-memory Delta variant marks tabu bits with +2^30: |Delta| < 2^29
+    ctx->smem_ok = R < (1 << 29) - 1 &&
+                   smem_search_bytes(n) + 1024 <= (size_t)std::max(ctx->smem_optin, 0);
   }
   uint64_t h = 1469598103934665603ull;  // FNV-1a of W, ties checkpoints to their instance
   for (size_t q = 0; q < (size_t)n * n; ++q) h = (h ^ (uint16_t)W[q]) * 1099511628211ull;
@@ -142,6 +145,7 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
 // search of a CTA) fits the opt-in size of a block with 2 KiB to spare for
 // the kernel's static arrays
 bool rows_ok(const dabs_ctx* ctx, const SearchVariant& v, int mode) {
+  if (v.ch == 0) return mode == ROWS_DENSE;  // the shared-memory Delta variant reads dense rows
   if (mode == ROWS_DENSE) return true;
   if (mode == ROWS_DENSE_SMEM)  // one-warp variants; W and 2 KiB fit a block
     return v.nw == 1 && sparse_smem_bytes(mode, ctx->n, 0, ctx->ld, v.spc) + 2048 <= (size_t)ctx->smem_optin;
@@ -217,6 +221,7 @@ SearchArgs solve_search_args(dabs_ctx* ctx) {
   a.best_X = ctx->bestX; a.best_E = ctx->bestE; a.flips = ctx->flips;
   a.order = ctx->order;
   a.key_bits = ctx->keyed ? ctx->key_bits : 0;
+  a.serr = ctx->serr;
   a.sp_mode = ctx->rows_mode;
   if (ctx->rows_mode == ROWS_SPARSE_SMEM || ctx->rows_mode == ROWS_SPARSE_GLOBAL) {
     a.sp_row = ctx->sp_row;
@@ -325,6 +330,7 @@ int spc_for(int slots, int maxspc) {
 
 bool launch_search(int nw, int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
                    const MultiArgs* m) {
+  if (nw == 1 && ch == 0) return launch_search_smem(a, st, v, m);  // Delta in shared memory
   switch (nw) {
     case 1: return launch_search_w1(ch, a, st, v, m);
     case 2: return launch_search_w2(ch, a, st, v, m);
@@ -440,6 +446,7 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
   TRY(dalloc(ctx, &ctx->gbestX, nw));
   TRY(dalloc(ctx, &ctx->stats, kStats));
   TRY(dalloc(ctx, &ctx->rflag, 1));
+  TRY(dalloc(ctx, &ctx->serr, 1));
   TRY(dalloc(ctx, &ctx->one_X, nw));
   TRY(dalloc(ctx, &ctx->one_d, ld));
   TRY(dalloc(ctx, &ctx->one_E, 1));
@@ -705,6 +712,8 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks) {
   if (!launch_search(warps, chunks, nullptr, nullptr, &v))
     return fail(ctx, DABS_E_INVALID_ARG, "variant %d/%d not built", warps, chunks);
   if (v.cap < ctx->n) return fail(ctx, DABS_E_TOO_LARGE, "variant holds %d < n", v.cap);
+  if (v.ch == 0 && !ctx->smem_ok)
+    return fail(ctx, DABS_E_TOO_LARGE, "Delta range or size does not fit the shared-memory variant");
   ctx->var = v;
   if (!rows_ok(ctx, v, ctx->rows_mode)) ctx->rows_mode = ROWS_DENSE;
   graph_stale(ctx);
@@ -746,7 +755,7 @@ int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* c
   if (!ctx || generations < 1) return DABS_E_INVALID_ARG;
   constexpr int NV = DABS_N_VARIANTS / 4;  // per RowFormat: dense, sparse shared, sparse global, dense shared
   static const int cand[NV][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {4, 1}, {4, 2},
-                                  {4, 4}, {8, 1}, {8, 2}, {8, 4}, {16, 1}, {16, 2}, {16, 4}};
+                                  {4, 4}, {8, 1}, {8, 2}, {8, 4}, {16, 1}, {16, 2}, {16, 4}, {1, 0}};
   if (table)
     for (int q = 0; q < DABS_N_VARIANTS; ++q) table[q] = 0.f;
   // warm a throwaway solve for `generations` generations, breed the next
@@ -780,6 +789,7 @@ int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* c
       const int rows = ci / NV;  // RowFormat
       if (!launch_search(cand[ci % NV][0], cand[ci % NV][1], nullptr, nullptr, &v) || v.cap < ctx->n)
         continue;
+      if (v.ch == 0 && !ctx->smem_ok) continue;
       if (!rows_ok(ctx, v, rows)) continue;
       cudaMemcpyAsync(ctx->X, sp, xb, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaMemcpyAsync(ctx->delta, sp + xb, db, cudaMemcpyDeviceToDevice, ctx->stream);
@@ -843,12 +853,14 @@ int dabs_recompute_dev(dabs_ctx* ctx, const uint32_t* X, int32_t count, int64_t*
 int dabs_kernel_status(dabs_ctx* ctx) {
   if (!ctx) return DABS_E_INVALID_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
-  if (!ctx->kerr) return DABS_OK;
-  int e = 0;
-  CK(cudaMemcpy(&e, ctx->kerr, sizeof e, cudaMemcpyDeviceToHost));
-  if (e) {
-    CK(cudaMemset(ctx->kerr, 0, sizeof(int)));
-    return fail(ctx, DABS_E_TIMEOUT, "a device wait ran out (kernel error %d)", e);
+  for (int* flag : {ctx->kerr, ctx->serr}) {
+    if (!flag) continue;
+    int e = 0;
+    CK(cudaMemcpy(&e, flag, sizeof e, cudaMemcpyDeviceToHost));
+    if (e) {
+      CK(cudaMemset(flag, 0, sizeof(int)));
+      return fail(ctx, DABS_E_TIMEOUT, "a device wait ran out (kernel error %d)", e);
+    }
   }
   return DABS_OK;
 }

@@ -145,7 +145,9 @@ struct Batcher {
     for (dabs_ctx* c : active)
       if ((rc = stage(c, 0)) || (rc = stage(c, 4))) return rc;
     for (auto& g : groups) {
-      const MultiArgs m{g.d_insts, g.d_prefix, (int32_t)g.ctxs.size(), g.total};
+      int32_t max_n = 0;
+      for (const dabs_ctx* c : g.ctxs) max_n = std::max(max_n, (int32_t)c->n);
+      const MultiArgs m{g.d_insts, g.d_prefix, (int32_t)g.ctxs.size(), g.total, max_n};
       const SearchArgs first = solve_search_args(g.ctxs[0]);
       if (!launch_search(g.var.nw, g.var.ch, &first, stream, nullptr, &m)) return DABS_E_INVALID_ARG;
       if ((rc = check(cudaGetLastError()))) return rc;

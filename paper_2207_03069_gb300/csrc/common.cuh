@@ -131,6 +131,7 @@ struct SearchArgs {
   // of (k << 1 | x_k) below the Delta part of a key, bitlen(n - 1) + 1, valid
   // when (2 R + 2) 2^key_bits < 2^31 for R = max_k sum_j |W_kj|
   int32_t key_bits;
+  int* serr;  // error flag of the kernels with bounded waits (may be null)
 };
 
 enum RowFormat : int { ROWS_DENSE = 0, ROWS_SPARSE_SMEM = 1, ROWS_SPARSE_GLOBAL = 2,
@@ -154,6 +155,7 @@ struct MultiArgs {
   const int32_t* prefix;    // [ninst + 1] slot offsets
   int32_t ninst;
   int32_t total;            // prefix[ninst]
+  int32_t max_n;            // largest n among the instances
 };
 
 }  // namespace dabs

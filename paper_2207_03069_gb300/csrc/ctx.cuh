@@ -54,6 +54,8 @@ struct dabs_ctx {
   int rows_mode = 0;          // RowFormat the batch search reads
   int key_bits = 0;           // keyed Delta bits when the instance allows it (0: not)
   int keyed = 1;              // 1: use the keyed form when key_bits > 0
+  bool smem_ok = false;       // the shared-memory Delta variant (1, 0) can run this instance
+  int* serr = nullptr;        // error flag of the batch-search kernels with bounded waits
   // one generation captured as a CUDA graph and replayed per generation
   int graphs = 1;             // 1: dabs_solve_generations replays the graph
   bool graph_ok = false;      // gexec matches the current launch configuration

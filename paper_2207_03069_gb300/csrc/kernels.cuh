@@ -126,5 +126,9 @@ bool launch_search_w8(int ch, const SearchArgs* a, cudaStream_t st, SearchVarian
                        const MultiArgs* m = nullptr);
 bool launch_search_w16(int ch, const SearchArgs* a, cudaStream_t st, SearchVariant* v,
                        const MultiArgs* m = nullptr);
+// variant (1, 0): one warp per search with Delta in shared memory (search_smem.cu)
+bool launch_search_smem(const SearchArgs* a, cudaStream_t st, SearchVariant* v,
+                        const MultiArgs* m = nullptr);
+size_t smem_search_bytes(int n);  // its shared memory per search
 
 }  // namespace dabs

@@ -280,8 +280,9 @@ class Context:
     def set_variant(self, warps: int, chunks: int):
         self._ck(lib().dabs_set_variant(self._h, warps, chunks))
 
+    # (warps, chunks); (1, 0) is one warp per search with Delta in shared memory
     VARIANTS = ((1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (4, 1), (4, 2), (4, 4), (8, 1),
-                (8, 2), (8, 4), (16, 1), (16, 2), (16, 4))
+                (8, 2), (8, 4), (16, 1), (16, 2), (16, 4), (1, 0))
 
     def set_rows(self, mode: int):
         """Row format of the batch search: ROWS_DENSE, ROWS_SPARSE_SMEM,

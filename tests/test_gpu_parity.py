@@ -536,3 +536,56 @@ def test_sparse_rows_solve_equals_dense_and_oracle(D, orc, n, gen):
         r = orc.batch_search(W, p, 7, 2, int(s), X2[s], d2[s], int(E2[s]), oD[s], int(oa[s]))
         assert int(fl[s]) == r["flips"] and int(bE[s]) == r["best_E"]
         assert np.array_equal(gb[s], r["best_X"])
+
+
+# ---------------------------------------------------------------- Delta in shared memory
+@pytest.mark.parametrize("n", [1, 2, 5, 31, 33, 64, 100, 257, 800, 1025, 2047, 3001])
+def test_smem_delta_variant_matches_oracle(D, orc, n):
+    """Variant (1, 0): one warp per search with the stored Delta (tabu bits
+    offset by 2^30) in shared memory and rows fetched by bulk copies."""
+    W = wl.dense_qubo(n, -1000, 1000, seed=n + 7)
+    bulk_case(D, orc, W, ALGOS, variant=(1, 0), s=(1, 4), b=(2, 1))
+
+
+@pytest.mark.parametrize("n", [8192, 16384])
+def test_smem_delta_variant_at_large_n(D, orc, n):
+    W = wl.dense_qubo(n, -100, 100, seed=n)
+    bulk_case(D, orc, W, [0, 1, 2, 3, 4], variant=(1, 0), s=(1, 64), b=(1, 16), dflip=0.005)
+
+
+def test_smem_delta_variant_generations_and_batch(D, orc):
+    n = 1500
+    W = wl.sparse_ising_qubo(n, 6 * n, 16, seed=3)
+    kw = dict(searches=64, pools=4, pool_cap=16, tabu=8, s=(1, 10), b=(1, 1), seed_mode=0)
+    ctx = D.Context(W, **kw)
+    ctx.set_variant(1, 0)
+    so = orc.Solver(W, orc.make_params(**kw), 5)
+    ctx.solve_begin(5)
+    for g in range(3):
+        ctx.solve_generations(1)
+        so.generation(threads=16)
+        compare_generation(ctx, so, n, f"generation {g}")
+    ctx.kernel_status()
+    # batched with instances of other sizes on the same variant
+    kw2 = dict(kw, max_generations=3)
+    Ws = [W, wl.dense_qubo(700, -500, 500, seed=1), wl.dense_qubo(2100, -50, 50, seed=2)]
+    ctxs = [D.Context(Wi, **kw2) for Wi in Ws]
+    for c in ctxs:
+        c.set_variant(1, 0)
+    out = D.batch_solve(ctxs, [10**9] * 3, [1, 2, 3])
+    for k, Wi in enumerate(Ws):
+        alone = D.Context(Wi, **kw2)
+        alone.set_variant(1, 0)
+        a = alone.solve(10**9, k + 1)
+        assert out[k][1] == a[1] and out[k][2] == a[2] and np.array_equal(out[k][0], a[0])
+        plain = D.Context(Wi, **kw2).solve(10**9, k + 1)  # register variant, same result
+        assert plain[1] == a[1] and plain[2] == a[2] and np.array_equal(plain[0], a[0])
+
+
+def test_smem_delta_variant_range_limit(D):
+    n = 16384
+    W = np.full((n, n), 32767, np.int16)  # every row sums to n * 32767 > 2^29
+    ctx = D.Context(W, searches=4, pools=1, pool_cap=4)
+    with pytest.raises(D.DabsError) as e:
+        ctx.set_variant(1, 0)
+    assert e.value.code == D.E_TOO_LARGE
