@@ -582,10 +582,11 @@ def test_smem_delta_variant_generations_and_batch(D, orc):
         assert plain[1] == a[1] and plain[2] == a[2] and np.array_equal(plain[0], a[0])
 
 
-def test_smem_delta_variant_range_limit(D):
+def test_smem_delta_variant_at_the_delta_range_limit(D, orc):
+    """int16 weights and n <= 16384 bound every Delta by 16384 * 32767 < 2^29,
+    so the variant accepts every instance; at n = 16384 with weights near
+    32767 the stored values (tabu offset 2^30 included) come within 2^14 of
+    that bound and must still match the oracle."""
     n = 16384
-    W = np.full((n, n), 32767, np.int16)  # every row sums to n * 32767 > 2^29
-    ctx = D.Context(W, searches=4, pools=1, pool_cap=4)
-    with pytest.raises(D.DabsError) as e:
-        ctx.set_variant(1, 0)
-    assert e.value.code == D.E_TOO_LARGE
+    W = wl.dense_qubo(n, 32000, 32767, seed=5)
+    bulk_case(D, orc, W, [0, 1, 2, 3, 4], variant=(1, 0), s=(1, 256), b=(1, 256), dflip=0.001, S=5)
