@@ -15,8 +15,10 @@
 //                which also ranges over the tabu bits, adds the tabu ring's
 //                entries (LP = L + 4 spreads the lanes over the banks);
 //   sS[32][LP]   sigma(x_k) (0 for k >= n);
-//   rS[32][RS]   row i of sigma(x_i) W: every lane fetches its block with one
-//                cp.async.bulk copy completing on an mbarrier (bounded wait);
+//   rS[32 L]     row i of sigma(x_i) W, fetched by one cp.async.bulk copy
+//                completing on an mbarrier (bounded wait); lane l walks its
+//                block starting at group l, which keeps the row, Delta and
+//                sigma reads of a quarter-warp on distinct banks;
 //   xS, tS, bS   X, target D and BEST bits, LW words per lane.
 // Eq. (4) is one multiply-add per owned bit; Eq. (5) and the tabu penalties
 // are single shared-memory stores.  Requires |Delta_k| < 2^29 in every state
@@ -60,7 +62,7 @@ __device__ __forceinline__ int at4(const int4& v, int e) {
 
 struct SmemSearch {
   // layout
-  int n, ld, LW, L, LP, LWP, RS, lane, base;
+  int n, ld, LW, L, LP, LWP, lane, base;
   int* dS;
   int* sS;
   int16_t* rS;
@@ -275,23 +277,21 @@ struct SmemSearch {
   }
 
   // ---------------------------------------------------------------- row i
-  // Each lane copies its block of row i of sigma(x_i) W into rS.
+  // One bulk copy of row i of sigma(x_i) W (ld int16, 16-byte multiple) into rS.
   __device__ void row_fetch(int i, int xi) {
     const int16_t* row = (xi ? W : Wneg) + (size_t)i * ld;
     __syncwarp();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads of rS before the copy
-    if (lane == 0)
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads of rS before the copy
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
                    "r"((uint32_t)ld * 2u)
                    : "memory");
-    __syncwarp();
-    const int cnt = min(L, ld - base);
-    if (cnt > 0)
       asm volatile(
           "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-              su32(rS + lane * RS)),
-          "l"(row + base), "r"((uint32_t)cnt * 2u), "r"(su32(bar))
+              su32(rS)),
+          "l"(row), "r"((uint32_t)ld * 2u), "r"(su32(bar))
           : "memory");
+    }
   }
   // bounded wait for the current row; false (and the error flag) on timeout
   __device__ bool row_wait() {
@@ -314,12 +314,17 @@ struct SmemSearch {
     parity ^= 1u;
     return true;
   }
-  // Eq. (4) on this lane's block: Delta_k += W_ik sigma(x_i) sigma(x_k)
+  // Eq. (4) on this lane's block: Delta_k += W_ik sigma(x_i) sigma(x_k),
+  // eight bits at a time, starting at group `lane` (bank spread)
   __device__ void row_apply() {
-    const int16_t* rr = rS + lane * RS;
+    const int16_t* rr = rS + base;
     int* dd = dS + lane * LP;
     const int* ss = sS + lane * LP;
-    for (int q2 = 0; q2 < L / 8 && base + 8 * q2 < ld; ++q2) {
+    const int G = L / 8;
+    for (int t = 0; t < G; ++t) {
+      int q2 = t + lane;
+      q2 = q2 >= G ? q2 % G : q2;
+      if (base + 8 * q2 >= ld) continue;  // past the row: sigma is 0 there
       const uint4 w = *reinterpret_cast<const uint4*>(rr + 8 * q2);
       int4 d0 = *reinterpret_cast<const int4*>(dd + 8 * q2);
       int4 d1 = *reinterpret_cast<const int4*>(dd + 8 * q2 + 4);
@@ -511,7 +516,7 @@ struct SmemSearch {
 // Shared memory of one search (16-byte aligned sections, see the file comment).
 __host__ __device__ inline void smem_search_layout(int n, int* LW, uint32_t* off_d, uint32_t* off_s,
                                                    uint32_t* off_r, uint32_t* off_x, uint32_t* bytes) {
-  const int lw = n > 1024 ? (n + 1023) / 1024 : 1, L = 32 * lw, LP = L + 4, RS = L + 8;
+  const int lw = n > 1024 ? (n + 1023) / 1024 : 1, L = 32 * lw, LP = L + 4;
   const int LWP = lw | 1;
   const uint32_t bits = (uint32_t)(((32 * LWP * 4) + 15) / 16 * 16);
   uint32_t o = 16;  // mbarrier
@@ -520,7 +525,7 @@ __host__ __device__ inline void smem_search_layout(int n, int* LW, uint32_t* off
   *off_s = o;
   o += 32u * LP * 4u;
   *off_r = o;
-  o += 32u * RS * 2u;
+  o += 32u * L * 2u;
   *off_x = o;
   o += 3u * bits;
   *LW = lw;
@@ -564,7 +569,6 @@ __global__ void __launch_bounds__(32) k_batch_search_smem(const SearchArgs singl
   sr.L = 32 * sr.LW;
   sr.LP = sr.L + 4;
   sr.LWP = sr.LW | 1;
-  sr.RS = sr.L + 8;
   sr.lane = lane;
   sr.base = lane * sr.L;
   sr.bar = reinterpret_cast<uint64_t*>(sm);
