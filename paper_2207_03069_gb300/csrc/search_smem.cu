@@ -4,8 +4,9 @@
 // per SM (as many as their shared memory allows) instead of spreading one
 // search over many warps that meet at a barrier for every reduction.
 //
-// Lane l owns the L = 32 LW consecutive bits k = l L .. l L + L - 1 (LW =
-// ceil(n / 1024)), so ascending bit order is lane order, then position: a
+// Lane l owns the L = 32 LW consecutive bits k = l L .. l L + L - 1 (LW the
+// power of two >= ceil(n / 1024), so that owner and position are shifts and
+// masks), so ascending bit order is lane order, then position: a
 // minimum with the lowest index is a (value, index) pair reduced over lanes,
 // and the k-th candidate of MaxMin / PositiveMin is one prefix over lanes.
 // Each search's shared memory holds
@@ -63,6 +64,7 @@ __device__ __forceinline__ int at4(const int4& v, int e) {
 struct SmemSearch {
   // layout
   int n, ld, LW, L, LP, LWP, lane, base;
+  int lsh;  // log2 L
   int* dS;
   int* sS;
   int16_t* rS;
@@ -83,11 +85,12 @@ struct SmemSearch {
   uint32_t flips;
   int ring_len, ring_head, ringv;
 
-  __device__ int* dptr(int k) const { return dS + (k / L) * LP + (k % L); }
-  __device__ int* sptr(int k) const { return sS + (k / L) * LP + (k % L); }
-  __device__ uint32_t xbit(int k) const {
-    return (xS[(k / L) * LWP + (k % L) / 32] >> (k % 32)) & 1u;
+  __device__ int* dptr(int k) const { return dS + (k >> lsh) * LP + (k & (L - 1)); }
+  __device__ int* sptr(int k) const { return sS + (k >> lsh) * LP + (k & (L - 1)); }
+  __device__ uint32_t* xword(uint32_t* bits, int k) const {
+    return bits + (k >> lsh) * LWP + ((k & (L - 1)) >> 5);
   }
+  __device__ uint32_t xbit(int k) const { return (*xword(xS, k) >> (k & 31)) & 1u; }
   __device__ int4 ld4(int q) const { return *reinterpret_cast<const int4*>(dS + lane * LP + 4 * q); }
 
   // (value, index) of the warp's minimum, lowest index on ties
@@ -271,7 +274,7 @@ struct SmemSearch {
   __device__ void take_best(int j, int m) {
     for (int w = 0; w < LW; ++w) bS[lane * LWP + w] = xS[lane * LWP + w];
     __syncwarp();
-    if (lane == 0) bS[(j / L) * LWP + (j % L) / 32] ^= 1u << (j % 32);
+    if (lane == 0) *xword(bS, j) ^= 1u << (j & 31);
     __syncwarp();
     Ebest = E + m;
   }
@@ -322,8 +325,7 @@ struct SmemSearch {
     const int* ss = sS + lane * LP;
     const int G = L / 8;
     for (int t = 0; t < G; ++t) {
-      int q2 = t + lane;
-      q2 = q2 >= G ? q2 % G : q2;
+      const int q2 = (t + lane) & (G - 1);  // G is a power of two
       if (base + 8 * q2 >= ld) continue;  // past the row: sigma is 0 there
       const uint4 w = *reinterpret_cast<const uint4*>(rr + 8 * q2);
       int4 d0 = *reinterpret_cast<const int4*>(dd + 8 * q2);
@@ -493,7 +495,7 @@ struct SmemSearch {
       if (lane == 0) {
         *dptr(i) = -di + (phase == P_MAIN && use_tabu ? kPen : 0);  // Eq. (5)
         *sptr(i) = -*sptr(i);
-        xS[(i / L) * LWP + (i % L) / 32] ^= 1u << (i % 32);
+        *xword(xS, i) ^= 1u << (i & 31);
         if (leave >= 0) *dptr(leave) -= kPen;
       }
       __syncwarp();
@@ -516,7 +518,9 @@ struct SmemSearch {
 // Shared memory of one search (16-byte aligned sections, see the file comment).
 __host__ __device__ inline void smem_search_layout(int n, int* LW, uint32_t* off_d, uint32_t* off_s,
                                                    uint32_t* off_r, uint32_t* off_x, uint32_t* bytes) {
-  const int lw = n > 1024 ? (n + 1023) / 1024 : 1, L = 32 * lw, LP = L + 4;
+  int lw = 1;
+  while (1024 * lw < n) lw <<= 1;
+  const int L = 32 * lw, LP = L + 4;
   const int LWP = lw | 1;
   const uint32_t bits = (uint32_t)(((32 * LWP * 4) + 15) / 16 * 16);
   uint32_t o = 16;  // mbarrier
@@ -567,6 +571,7 @@ __global__ void __launch_bounds__(32) k_batch_search_smem(const SearchArgs singl
   sr.n = a.n;
   sr.ld = a.ld;
   sr.L = 32 * sr.LW;
+  sr.lsh = 31 - __clz(sr.L);
   sr.LP = sr.L + 4;
   sr.LWP = sr.LW | 1;
   sr.lane = lane;
