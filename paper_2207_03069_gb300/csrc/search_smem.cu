@@ -91,7 +91,10 @@ struct SmemSearch {
     return bits + (k >> lsh) * LWP + ((k & (L - 1)) >> 5);
   }
   __device__ uint32_t xbit(int k) const { return (*xword(xS, k) >> (k & 31)) & 1u; }
-  __device__ int4 ld4(int q) const { return *reinterpret_cast<const int4*>(dS + lane * LP + 4 * q); }
+  __device__ int4 ld4(int q) const {
+    const int* __restrict__ p = dS + lane * LP + 4 * q;
+    return *reinterpret_cast<const int4*>(p);
+  }
 
   // (value, index) of the warp's minimum, lowest index on ties
   __device__ static void wmin(int& v, int& k) {
@@ -115,6 +118,7 @@ struct SmemSearch {
   // minimum over all stored values (= over the free bits)
   __device__ void scan_plain(int& fv, int& fk) const {
     int mv = INT_MAX, mq = 0;
+#pragma unroll 8
     for (int q = 0; q < L / 4; ++q) track(min4(ld4(q)), q, mv, mq);
     fv = mv;
     fk = locate(mv, mq);
@@ -200,6 +204,7 @@ struct SmemSearch {
   // MaxMin: also the maximum over the free bits
   __device__ void scan_maxmin(int& fv, int& fk, int& mx) const {
     int mv = INT_MAX, mq = 0, xm = INT_MIN;
+#pragma unroll 8
     for (int q = 0; q < L / 4; ++q) {
       const int4 v = ld4(q);
       track(min4(v), q, mv, mq);
@@ -216,6 +221,7 @@ struct SmemSearch {
   __device__ void scan_posmin(int& fv, int& fk, uint32_t& um) const {
     int mv = INT_MAX, mq = 0;
     uint32_t u = UINT_MAX;
+#pragma unroll 8
     for (int q = 0; q < L / 4; ++q) {
       const int4 v = ld4(q);
       track(min4(v), q, mv, mq);
@@ -231,6 +237,7 @@ struct SmemSearch {
   // lane walks its groups
   __device__ void kth(int thr, uint32_t u, int& kv, int& kk) const {
     int cnt = 0;
+#pragma unroll 8
     for (int q = 0; q < L / 4; ++q) {
       const int4 v = ld4(q);
       cnt += (v.x <= thr) + (v.y <= thr) + (v.z <= thr) + (v.w <= thr);
@@ -320,10 +327,11 @@ struct SmemSearch {
   // Eq. (4) on this lane's block: Delta_k += W_ik sigma(x_i) sigma(x_k),
   // eight bits at a time, starting at group `lane` (bank spread)
   __device__ void row_apply() {
-    const int16_t* rr = rS + base;
-    int* dd = dS + lane * LP;
-    const int* ss = sS + lane * LP;
+    const int16_t* __restrict__ rr = rS + base;
+    int* __restrict__ dd = dS + lane * LP;
+    const int* __restrict__ ss = sS + lane * LP;
     const int G = L / 8;
+#pragma unroll 4
     for (int t = 0; t < G; ++t) {
       const int q2 = (t + lane) & (G - 1);  // G is a power of two
       if (base + 8 * q2 >= ld) continue;  // past the row: sigma is 0 there
