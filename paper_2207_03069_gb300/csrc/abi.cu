@@ -181,9 +181,9 @@ int tc_setup(dabs_ctx* ctx) {
   if ((rc = dalloc(ctx, &ctx->E2, (size_t)ctx->rows_pad)) != DABS_OK) return rc;
   if ((rc = dalloc(ctx, &ctx->kerr, 1)) != DABS_OK) return rc;
   CK(cudaMemsetAsync(ctx->kerr, 0, sizeof(int), ctx->stream));
-  if (!make_tmap_bf16(&ctx->mapA, ctx->Abf, ctx->rows_pad, ctx->n_pad) ||
-      !make_tmap_bf16(&ctx->mapHi, ctx->Whi, ctx->n_pad, ctx->n_pad) ||
-      !make_tmap_bf16(&ctx->mapLo, ctx->Wlo, ctx->n_pad, ctx->n_pad))
+  if (!make_tmap_bf16(&ctx->mapA, ctx->Abf, ctx->rows_pad, ctx->n_pad, bm) ||
+      !make_tmap_bf16(&ctx->mapHi, ctx->Whi, ctx->n_pad, ctx->n_pad, bn) ||
+      !make_tmap_bf16(&ctx->mapLo, ctx->Wlo, ctx->n_pad, ctx->n_pad, bn))
     return fail(ctx, DABS_E_CUDA, "cuTensorMapEncodeTiled failed");
   CK(cudaFuncSetAttribute(k_recompute_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)umma_smem_bytes()));

@@ -9,11 +9,13 @@
 // fp32 accumulator stays exact while |partial sum| < 2^24, i.e. for
 // n <= 65,793 (n * 255 < 2^24).  F = 256 * F_hi + F_lo is then exact in int32.
 //
-// Kernel: one CTA per 128 x 128 output tile, 4 warps.  Thread 0 streams
-// K-blocks of 64 (128 bytes) of D and of both limbs into a 4-stage
-// shared-memory ring with TMA (128-byte swizzle) and issues
-// tcgen05.mma.kind::f16 (M = 128, N = 128, K = 16) into two fp32 TMEM
-// accumulators (hi, lo); each stage is released by tcgen05.commit.  All four
+// Kernel: one CTA per 128 x 64 output tile (128 vectors x 64 columns of W:
+// twice the CTAs of square tiles, so a batch of 256 vectors at n = 4096
+// covers 128 of the 152 SMs), 4 warps.  Thread 0 streams K-blocks of 64
+// (128 bytes) of D and of both limbs into a 4-stage shared-memory ring with
+// TMA (128-byte swizzle) and issues tcgen05.mma.kind::f16 (M = 128, N = 64,
+// K = 16) into two fp32 TMEM accumulators (hi, lo); each stage is released
+// by tcgen05.commit.  All four
 // warps then read their 32 TMEM lanes (rows) with tcgen05.ld and write Delta
 // and the energy partial sums.  Every mbarrier wait is bounded; on expiry the
 // kernel records an error code and returns after releasing its TMEM.
@@ -25,10 +27,11 @@
 namespace dabs {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
-constexpr uint32_t TILE_BYTES = BM * BK * 2;           // 16 KiB per operand tile
-constexpr uint32_t STAGE_BYTES = 3 * TILE_BYTES;       // D, W_hi, W_lo
-constexpr uint32_t TMEM_COLS = 256;                    // hi: [0,128), lo: [128,256)
+constexpr int BM = 128, BN = 64, BK = 64, STAGES = 4;
+constexpr uint32_t A_BYTES = BM * BK * 2;              // 16 KiB: D tile
+constexpr uint32_t B_BYTES = BN * BK * 2;              // 8 KiB: one limb tile
+constexpr uint32_t STAGE_BYTES = A_BYTES + 2 * B_BYTES;  // D, W_hi, W_lo
+constexpr uint32_t TMEM_COLS = 2 * BN;                 // hi: [0,BN), lo: [BN,2BN)
 constexpr uint64_t WAIT_NS = 2000000000ull;            // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -196,8 +199,8 @@ __global__ void __launch_bounds__(128, 1)
         const uint32_t s0 = base + st * STAGE_BYTES;
         mbar_expect_tx(&full[st], STAGE_BYTES);
         tma_load_2d(s0, &mapA, kb * BK, m0, &full[st]);
-        tma_load_2d(s0 + TILE_BYTES, &mapHi, kb * BK, n0, &full[st]);
-        tma_load_2d(s0 + 2 * TILE_BYTES, &mapLo, kb * BK, n0, &full[st]);
+        tma_load_2d(s0 + A_BYTES, &mapHi, kb * BK, n0, &full[st]);
+        tma_load_2d(s0 + A_BYTES + B_BYTES, &mapLo, kb * BK, n0, &full[st]);
       }
       const int kc = kb - (STAGES - 1);
       if (kc >= 0) {
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(128, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t s0 = base + st * STAGE_BYTES;
-        const uint64_t da = sdesc(s0), dh = sdesc(s0 + TILE_BYTES), dl = sdesc(s0 + 2 * TILE_BYTES);
+        const uint64_t da = sdesc(s0), dh = sdesc(s0 + A_BYTES), dl = sdesc(s0 + A_BYTES + B_BYTES);
 #pragma unroll
         for (int ks = 0; ks < BK / 16; ++ks) {
           const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
@@ -289,7 +292,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-bool make_tmap_bf16(CUtensorMap* map, void* ptr, uint64_t rows, uint64_t cols) {
+bool make_tmap_bf16(CUtensorMap* map, void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -302,7 +305,7 @@ bool make_tmap_bf16(CUtensorMap* map, void* ptr, uint64_t rows, uint64_t cols) {
   }
   const cuuint64_t dims[2] = {cols, rows};
   const cuuint64_t strides[1] = {cols * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)umma_tile_k(), (cuuint32_t)umma_tile_m()};
+  const cuuint32_t box[2] = {(cuuint32_t)umma_tile_k(), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,

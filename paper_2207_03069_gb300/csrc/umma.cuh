@@ -33,7 +33,8 @@ size_t umma_smem_bytes();
 int umma_tile_m();
 int umma_tile_n();
 int umma_tile_k();
-// 2-D bf16 tensor map (rows x cols, row-major) with a 64 x 128 box and 128-byte swizzle
-bool make_tmap_bf16(CUtensorMap* map, void* ptr, uint64_t rows, uint64_t cols);
+// 2-D bf16 tensor map (rows x cols, row-major) with a box of 64 columns x
+// box_rows rows and 128-byte swizzle
+bool make_tmap_bf16(CUtensorMap* map, void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows);
 
 }  // namespace dabs
