@@ -12,7 +12,7 @@
 // Kernel: one CTA per 128 x 64 output tile (128 vectors x 64 columns of W:
 // twice the CTAs of square tiles, so a batch of 256 vectors at n = 4096
 // covers 128 of the 152 SMs), 4 warps.  Thread 0 streams K-blocks of 64
-// (128 bytes) of D and of both limbs into a 4-stage shared-memory ring with
+// (128 bytes) of D and of both limbs into a 6-stage shared-memory ring with
 // TMA (128-byte swizzle) and issues tcgen05.mma.kind::f16 (M = 128, N = 64,
 // K = 16) into two fp32 TMEM accumulators (hi, lo); each stage is released
 // by tcgen05.commit.  All four
@@ -27,7 +27,7 @@
 namespace dabs {
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 64, BK = 64, STAGES = 6;
 constexpr uint32_t A_BYTES = BM * BK * 2;              // 16 KiB: D tile
 constexpr uint32_t B_BYTES = BN * BK * 2;              // 8 KiB: one limb tile
 constexpr uint32_t STAGE_BYTES = A_BYTES + 2 * B_BYTES;  // D, W_hi, W_lo
