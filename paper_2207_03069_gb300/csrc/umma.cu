@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
+  __shared__ int sdiag[BN];  // W_kk of the tile's columns (0 past n)
   if (a.ctrl && a.ctrl->done) return;
   // 1024-byte aligned operand ring
   const uint32_t base = (smem_u32(smraw) + 1023u) & ~1023u;
@@ -182,10 +183,20 @@ __global__ void __launch_bounds__(128, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  if (threadIdx.x < BN) sdiag[threadIdx.x] = n0 + (int)threadIdx.x < a.n ? a.diag[n0 + threadIdx.x] : 0;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tm = tmem_base;
+  // this thread's epilogue row and its D words, fetched before the MMAs finish
+  const int row = m0 + 32 * warp + lane;
+  const bool row_ok = row < a.count;
+  uint32_t dwords[BN / 32];
+#pragma unroll
+  for (int c = 0; c < BN / 32; ++c) {
+    const int kb0 = n0 + 32 * c;
+    dwords[c] = (row_ok && kb0 < a.n) ? a.D[(size_t)row * a.nw + (kb0 >> 5)] : 0u;
+  }
 
   if (warp == 0 && lane == 0) {
     // producer (TMA) and MMA issue in one thread, STAGES-1 blocks ahead
@@ -236,12 +247,12 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
   if (!abort_flag) {
-    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
-    const int row = m0 + 32 * warp + lane;
-    const bool row_ok = row < a.count;
-    const uint32_t* drow = a.D + (size_t)(row_ok ? row : 0) * a.nw;
+    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31; Delta written
+    // four columns per 16-byte store where the row allows it
     int64_t epart = 0;
-#pragma unroll 1
+    int32_t* drow = a.delta ? a.delta + (size_t)(row_ok ? row : 0) * a.ld_delta : nullptr;
+    const bool vec = drow && (a.ld_delta & 3) == 0 && (reinterpret_cast<uintptr_t>(a.delta) & 15) == 0;
+#pragma unroll
     for (int c0 = 0; c0 < BN; c0 += 32) {
       uint32_t rh[32], rl[32];
       const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
@@ -249,16 +260,27 @@ __global__ void __launch_bounds__(128, 1)
       tmem_ld32(tm + lane_off + (uint32_t)(BN + c0), rl);
       const int kbase = n0 + c0;
       if (row_ok && kbase < a.n) {
-        const uint32_t dword = drow[kbase >> 5];
+        const uint32_t dword = dwords[c0 >> 5];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int k = kbase + j;
-          if (k < a.n) {
+        for (int j4 = 0; j4 < 32; j4 += 4) {
+          int v[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int j = j4 + e;
             const int F = 256 * __float2int_rn(__uint_as_float(rh[j])) + __float2int_rn(__uint_as_float(rl[j]));
-            const int wkk = a.diag[k];
+            const int wkk = sdiag[c0 + j];
             const bool dk = (dword >> j) & 1u;
-            if (a.delta) a.delta[(size_t)row * a.ld_delta + k] = dk ? -F : F + wkk;  // Eq. (3)
-            if (dk) epart += (int64_t)F + wkk;
+            v[e] = dk ? -F : F + wkk;  // Eq. (3)
+            if (dk && kbase + j < a.n) epart += (int64_t)F + wkk;
+          }
+          const int k0 = kbase + j4;
+          if (!drow || k0 >= a.n) continue;
+          if (vec && k0 + 3 < a.n) {
+            *reinterpret_cast<int4*>(drow + k0) = make_int4(v[0], v[1], v[2], v[3]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (k0 + e < a.n) drow[k0 + e] = v[e];
           }
         }
       }

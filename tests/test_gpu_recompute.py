@@ -43,6 +43,15 @@ def test_recompute_matches_cuda_cores_and_oracle(D, orc, n, count):
     for v in sorted(set([0, count - 1, count // 2])):
         assert int(Etc[v]) == orc.energy(W, Xs[v])
         assert np.array_equal(dtc[v, :n].cpu().numpy(), orc.delta(W, Xs[v]))
+    # a row stride that is a multiple of 4 takes the 16-byte-store epilogue
+    ld4 = (n + 3) // 4 * 4 + 4
+    dv = torch.full((count, ld4), -7, dtype=torch.int32, device="cuda")
+    Ev = torch.zeros(count, dtype=torch.int64, device="cuda")
+    ctx.recompute_dev(Xd, Ev, dv)
+    ctx.kernel_status()
+    torch.cuda.synchronize()
+    assert torch.equal(Ev, Ecc) and torch.equal(dv[:, :n], dcc[:, :n])
+    assert bool((dv[:, n:] == -7).all())  # nothing written past n
 
 
 def test_solve_with_tensor_core_seeding_matches_oracle(D, orc):
