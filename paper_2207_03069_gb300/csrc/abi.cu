@@ -172,7 +172,8 @@ int tc_limbs(dabs_ctx* ctx) {
 int tc_setup(dabs_ctx* ctx) {
   if (ctx->tc_ready) return DABS_OK;
   const int bm = umma_tile_m(), bn = umma_tile_n();
-  ctx->n_pad = (ctx->n + bn - 1) / bn * bn;
+  const int bnk = std::max(bn, umma_tile_k());  // both tile widths divide the padding (powers of two)
+  ctx->n_pad = (ctx->n + bnk - 1) / bnk * bnk;
   ctx->rows_pad = (std::max(ctx->S, 1) + bm - 1) / bm * bm;
   int rc;
   if ((rc = dalloc(ctx, &ctx->Whi, (size_t)ctx->n_pad * ctx->n_pad)) != DABS_OK) return rc;
