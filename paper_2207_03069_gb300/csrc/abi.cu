@@ -64,32 +64,43 @@ bool rows_ok(const dabs_ctx* ctx, const SearchVariant& v, int mode);
 
 int upload_weights(dabs_ctx* ctx, const int16_t* W) {
   const int n = ctx->n, ld = ctx->ld;
-  for (int i = 0; i < n; ++i)
-    for (int j = i; j < n; ++j) {
-      if (W[(size_t)i * n + j] != W[(size_t)j * n + i])
-        return fail(ctx, DABS_E_NOT_SYMMETRIC, "W[%d][%d] != W[%d][%d]", i, j, j, i);
-      if (W[(size_t)i * n + j] == INT16_MIN)
-        return fail(ctx, DABS_E_INVALID_ARG, "W[%d][%d] = -32768 (weights must lie in [-32767, 32767])", i, j);
-    }
-  std::vector<int16_t> pad((size_t)n * ld, 0), neg((size_t)n * ld, 0);
+  // symmetry and the -32768 check over the upper triangle, in 64 x 64 tiles
+  // (the transposed reads of a tile stay in cache)
+  constexpr int TB = 64;
+  for (int bi = 0; bi < n; bi += TB)
+    for (int bj = bi; bj < n; bj += TB)
+      for (int i = bi; i < std::min(bi + TB, n); ++i)
+        for (int j = std::max(bj, i); j < std::min(bj + TB, n); ++j) {
+          const int16_t w = W[(size_t)i * n + j];
+          if (w != W[(size_t)j * n + i])
+            return fail(ctx, DABS_E_NOT_SYMMETRIC, "W[%d][%d] != W[%d][%d]", i, j, j, i);
+          if (w == INT16_MIN)
+            return fail(ctx, DABS_E_INVALID_ARG, "W[%d][%d] = -32768 (weights must lie in [-32767, 32767])", i, j);
+        }
+  // one row-major pass: the padded W and -W, the diagonal, the largest row sum
+  // of |W| and the off-diagonal non-zero count
+  std::vector<int16_t> pad((size_t)n * ld, 0);
   std::vector<int32_t> dg(n);
+  int64_t R = 0;
+  size_t nnz_all = 0;
   for (int i = 0; i < n; ++i) {
+    const int16_t* wr = W + (size_t)i * n;
+    int64_t r = 0;
+    size_t z = 0;
     for (int j = 0; j < n; ++j) {
-      pad[(size_t)i * ld + j] = W[(size_t)i * n + j];
-      neg[(size_t)i * ld + j] = (int16_t)-W[(size_t)i * n + j];
+      const int16_t w = wr[j];
+      pad[(size_t)i * ld + j] = w;
+      r += w < 0 ? -(int)w : (int)w;
+      z += w != 0;
     }
-    dg[i] = W[(size_t)i * n + i];
+    dg[i] = wr[i];
+    R = std::max(R, r);
+    nnz_all += z - (wr[i] != 0);
   }
   // keyed Delta: |Delta_k| <= R_k = sum_j |W_kj| in every state, and a key
   // (Delta << kb | k << 1 | x_k) plus the diagonal term added to it before
   // Eq. (5) overwrites it must stay inside int32
   {
-    int64_t R = 0;
-    for (int i = 0; i < n; ++i) {
-      int64_t r = 0;
-      for (int k = 0; k < n; ++k) r += std::abs((int)W[(size_t)i * n + k]);
-      R = std::max(R, r);
-    }
     int kb = 1;
     while ((1 << (kb - 1)) < n) ++kb;  // bitlen(n - 1) + 1
     ctx->key_bits = ((2 * R + 2) << kb) < (int64_t)INT32_MAX ? kb : 0;
@@ -97,29 +108,50 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
     ctx->smem_ok = R < (1 << 29) - 1 &&
                    smem_search_bytes(n) + 1024 <= (size_t)std::max(ctx->smem_optin, 0);
   }
-  uint64_t h = 1469598103934665603ull;  // FNV-1a of W, ties checkpoints to their instance
-  for (size_t q = 0; q < (size_t)n * n; ++q) h = (h ^ (uint16_t)W[q]) * 1099511628211ull;
-  ctx->w_hash = h;
+  // hash of W (ties checkpoints to their instance): four independent
+  // xor-multiply chains over 64-bit words, then the tail bytes
+  {
+    const unsigned char* by = reinterpret_cast<const unsigned char*>(W);
+    const size_t nb = (size_t)n * n * sizeof(int16_t);
+    const uint64_t P = 1099511628211ull;
+    uint64_t ln[4] = {1469598103934665603ull, 0x9E3779B97F4A7C15ull, 0xC2B2AE3D27D4EB4Full,
+                      0x165667B19E3779F9ull};
+    size_t q = 0;
+    for (; q + 32 <= nb; q += 32)
+      for (int l = 0; l < 4; ++l) {
+        uint64_t w;
+        memcpy(&w, by + q + 8 * l, 8);
+        ln[l] = (ln[l] ^ w) * P;
+      }
+    for (; q < nb; ++q) ln[0] = (ln[0] ^ by[q]) * P;
+    uint64_t h = ln[0];
+    for (int l = 1; l < 4; ++l) h = (h ^ ((ln[l] << (16 * l)) | (ln[l] >> (64 - 16 * l)))) * P;
+    ctx->w_hash = h ^ (uint64_t)nb;
+  }
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaMemcpy(ctx->W, pad.data(), pad.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->Wneg, neg.data(), neg.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+  {  // -W on the device (the flip kernels read row i of sigma(x_i) W directly)
+    const size_t cnt = pad.size();
+    k_negate<<<(unsigned)std::min<size_t>((cnt / 8 + 255) / 256 + 1, 4096), 256, 0, ctx->stream>>>(ctx->W, ctx->Wneg, cnt);
+    CKLAUNCH();
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
   CK(cudaMemcpy(ctx->diag, dg.data(), dg.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   // sparse rows: the off-diagonal non-zeros of each row, column ascending,
   // kept while they take at most half the bytes of the dense rows (or 64
   // entries, for tiny instances)
   const size_t limit = std::max<size_t>((size_t)n * n / 4, 64);
-  std::vector<uint32_t> rp(4 * (size_t)sparse_row16(n), 0), ent;
-  bool keep = true;
-  for (int i = 0; i < n && keep; ++i) {
-    rp[i] = (uint32_t)ent.size();
-    for (int k = 0; k < n; ++k) {
-      const int16_t w = W[(size_t)i * n + k];
-      if (k != i && w != 0) ent.push_back(((uint32_t)k << 16) | (uint16_t)w);
-    }
-    keep = ent.size() <= limit;
-  }
   ctx->sp_nnz = -1;
-  if (keep) {
+  if (nnz_all <= limit) {
+    std::vector<uint32_t> rp(4 * (size_t)sparse_row16(n), 0), ent;
+    ent.reserve(nnz_all);
+    for (int i = 0; i < n; ++i) {
+      rp[i] = (uint32_t)ent.size();
+      for (int k = 0; k < n; ++k) {
+        const int16_t w = W[(size_t)i * n + k];
+        if (k != i && w != 0) ent.push_back(((uint32_t)k << 16) | (uint16_t)w);
+      }
+    }
     rp[n] = (uint32_t)ent.size();
     const int nnz = (int)ent.size();
     ent.resize(4 * (size_t)sparse_ent16(nnz), 0u);
@@ -923,7 +955,7 @@ int dabs_checkpoint(dabs_ctx* ctx, void* buf, size_t cap, size_t* size) {
   CK(cudaStreamSynchronize(ctx->stream));
   CkptHeader h{};
   memcpy(h.magic, "DABSCKP1", 8);
-  h.version = 1;
+  h.version = 2;
   h.n = ctx->n; h.S = ctx->S; h.P = ctx->P; h.C = ctx->C;
   h.p = ctx->p;
   h.w_hash = ctx->w_hash;
@@ -942,7 +974,7 @@ int dabs_restore(dabs_ctx* ctx, const void* buf, size_t size) {
   if (!ctx || !buf || size < sizeof(CkptHeader)) return DABS_E_INVALID_ARG;
   CkptHeader h;
   memcpy(&h, buf, sizeof h);
-  if (memcmp(h.magic, "DABSCKP1", 8) != 0 || h.version != 1 || h.bytes != size || h.n != ctx->n ||
+  if (memcmp(h.magic, "DABSCKP1", 8) != 0 || h.version != 2 || h.bytes != size || h.n != ctx->n ||
       h.S != ctx->S || h.P != ctx->P || h.C != ctx->C || h.w_hash != ctx->w_hash ||
       memcmp(&h.p, &ctx->p, sizeof h.p) != 0)
     return fail(ctx, DABS_E_INVALID_ARG, "checkpoint does not match this context");

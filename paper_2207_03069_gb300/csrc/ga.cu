@@ -38,6 +38,18 @@ __global__ void k_pool_init(const PoolArgs a) {
   }
 }
 
+// Wneg = -W, element by element (weights lie in [-32767, 32767])
+__global__ void k_negate(const int16_t* W, int16_t* Wneg, size_t count) {
+  const size_t v = count / 8;  // 8 int16 per 16-byte vector
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < v; q += (size_t)gridDim.x * blockDim.x) {
+    const uint4 w = reinterpret_cast<const uint4*>(W)[q];
+    reinterpret_cast<uint4*>(Wneg)[q] = make_uint4(__vneg2(w.x), __vneg2(w.y), __vneg2(w.z), __vneg2(w.w));
+  }
+  for (size_t q = 8 * v + blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < count;
+       q += (size_t)gridDim.x * blockDim.x)
+    Wneg[q] = (int16_t)-W[q];
+}
+
 // X = 0, E = 0, Delta_k = W_kk for every search slot (Section III-B start).
 __global__ void k_state_init(const StateArgs a) {
   if (a.cond && *a.cond != 0) return;

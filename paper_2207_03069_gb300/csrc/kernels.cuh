@@ -95,6 +95,7 @@ struct EDArgs {
   const DevCtrl* ctrl; // optional: skip when a solve has stopped
 };
 
+__global__ void k_negate(const int16_t* W, int16_t* Wneg, size_t count);
 __global__ void k_pool_init(const PoolArgs a);
 __global__ void k_state_init(const StateArgs a);
 __global__ void k_offspring(const OffArgs a);
