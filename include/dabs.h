@@ -136,7 +136,9 @@ int dabs_kernel_status(dabs_ctx* ctx);
  * reaches `budget`, the best energy is <= `target` (INT64_MIN: no target),
  * or max_generations is reached.  Writes the best vector (host, n bytes),
  * its energy and the flips made.  Deterministic in (W, params, budget, seed,
- * target).                                                                   */
+ * target).  DABS_E_TIMEOUT (as dabs_kernel_status) if a kernel's bounded
+ * device wait ran out during the solve; dabs_batch_solve checks every
+ * instance the same way.                                                     */
 int dabs_solve(dabs_ctx* ctx, uint64_t budget, uint64_t seed, int64_t target, uint8_t* best_X,
                int64_t* best_E, uint64_t* flips);
 

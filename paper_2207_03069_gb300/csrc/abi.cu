@@ -694,6 +694,7 @@ int dabs_solve(dabs_ctx* ctx, uint64_t budget, uint64_t seed, int64_t target, ui
     if (done) break;
     if (chunk < 64) chunk <<= 1;
   }
+  if ((rc = dabs_kernel_status(ctx))) return rc;  // a bounded device wait that ran out
   return dabs_solve_best(ctx, best_X, best_E);
 }
 

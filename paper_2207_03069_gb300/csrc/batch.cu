@@ -213,7 +213,9 @@ extern "C" int dabs_batch_solve(dabs_ctx* const* ctxs, int32_t k, const uint64_t
     if (chunk < 16) chunk <<= 1;
   }
   for (int i = 0; i < k && !rc; ++i) {
-    if (best_X || best_E) rc = dabs_solve_best(ctxs[i], best_X ? best_X[i] : nullptr, best_E ? &best_E[i] : nullptr);
+    rc = dabs_kernel_status(ctxs[i]);  // a bounded device wait that ran out
+    if (!rc && (best_X || best_E))
+      rc = dabs_solve_best(ctxs[i], best_X ? best_X[i] : nullptr, best_E ? &best_E[i] : nullptr);
     if (!rc && flips) rc = dabs_solve_status(ctxs[i], &flips[i], nullptr, nullptr, nullptr);
   }
   restore();
