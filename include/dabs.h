@@ -129,6 +129,12 @@ int dabs_set_recompute(dabs_ctx* ctx, int32_t mode);
 /* Waits for the context's stream; DABS_E_TIMEOUT if a kernel's bounded wait
  * ran out since the last call (the flag is then cleared). */
 int dabs_kernel_status(dabs_ctx* ctx);
+/* Test hook (no counterpart in the paper): the next dabs_bulk_search_dev of a
+ * context on variant (1, 0) issues no copy for its first row, so that row's
+ * bounded wait runs out (about 4 s: the wait, then the wait for a copy in
+ * flight), the search stops without storing, and dabs_kernel_status reports
+ * DABS_E_TIMEOUT; the context stays usable.  INVALID_ARG on other variants. */
+int dabs_test_stall_next_search(dabs_ctx* ctx);
 
 /* Whole solve (Sections III and IV): pools initialised with random vectors,
  * every search starting at X = 0; generations of (offspring, batch search,

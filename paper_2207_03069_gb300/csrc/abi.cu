@@ -720,9 +720,18 @@ int dabs_bulk_search_dev(dabs_ctx* ctx, uint64_t seed, uint32_t g, int32_t count
   }
   a.X = X; a.delta = delta; a.E = E; a.D = D; a.algo = algo;
   a.best_X = best_X; a.best_E = best_E; a.flips = flips;
+  a.stall_test = ctx->stall_test;
   if (!launch_search(ctx->var.nw, ctx->var.ch, &a, ctx->stream, nullptr))
     return fail(ctx, DABS_E_INVALID_ARG, "no batch-search variant");
+  ctx->stall_test = 0;  // the hook covers one launch
   CKLAUNCH();
+  return DABS_OK;
+}
+
+int dabs_test_stall_next_search(dabs_ctx* ctx) {
+  if (!ctx) return DABS_E_INVALID_ARG;
+  if (ctx->var.ch != 0) return fail(ctx, DABS_E_INVALID_ARG, "the hook needs variant (1, 0)");
+  ctx->stall_test = 1;
   return DABS_OK;
 }
 

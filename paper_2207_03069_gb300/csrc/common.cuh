@@ -132,6 +132,7 @@ struct SearchArgs {
   // when (2 R + 2) 2^key_bits < 2^31 for R = max_k sum_j |W_kj|
   int32_t key_bits;
   int* serr;  // error flag of the kernels with bounded waits (may be null)
+  int32_t stall_test;  // 1: the shared-memory variant's first row wait gets no copy (test hook)
 };
 
 enum RowFormat : int { ROWS_DENSE = 0, ROWS_SPARSE_SMEM = 1, ROWS_SPARSE_GLOBAL = 2,

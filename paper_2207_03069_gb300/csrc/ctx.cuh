@@ -56,6 +56,7 @@ struct dabs_ctx {
   int keyed = 1;              // 1: use the keyed form when key_bits > 0
   bool smem_ok = false;       // the shared-memory Delta variant (1, 0) can run this instance
   int* serr = nullptr;        // error flag of the batch-search kernels with bounded waits
+  int stall_test = 0;         // test hook for the bounded waits (dabs_test_stall_next_search)
   // one generation captured as a CUDA graph and replayed per generation
   int graphs = 1;             // 1: dabs_solve_generations replays the graph
   bool graph_ok = false;      // gexec matches the current launch configuration

@@ -80,6 +80,7 @@ struct SmemSearch {
   uint32_t s, g;
   int* err;
   bool failed;
+  bool stall;  // test hook: issue no copy for the next row, so its wait runs out
   // state
   int64_t E, Ebest;
   uint32_t flips;
@@ -291,6 +292,7 @@ struct SmemSearch {
   __device__ void row_fetch(int i, int xi) {
     const int16_t* row = (xi ? W : Wneg) + (size_t)i * ld;
     __syncwarp();
+    if (stall) return;  // nothing arrives on the mbarrier: row_wait runs out
     if (lane == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads of rS before the copy
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
@@ -600,6 +602,7 @@ __global__ void __launch_bounds__(32) k_batch_search_smem(const SearchArgs singl
   sr.g = ctrl->g;
   sr.err = a.serr;
   sr.failed = false;
+  sr.stall = a.stall_test != 0;
   sr.ring_len = 0;
   sr.ring_head = 0;
   sr.ringv = 0;

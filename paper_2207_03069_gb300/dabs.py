@@ -75,6 +75,7 @@ EXPORTS = {
     "dabs_set_rows": (C.c_int, [C.c_void_p, C.c_int32]),
     "dabs_set_keyed": (C.c_int, [C.c_void_p, C.c_int32]),
     "dabs_set_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
+    "dabs_test_stall_next_search": (C.c_int, [C.c_void_p]),
     "dabs_get_keyed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dabs_get_rows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dabs_solve_restarts": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -371,6 +372,11 @@ class Context:
 
     def kernel_status(self):
         self._ck(lib().dabs_kernel_status(self._h))
+
+    def test_stall_next_search(self):
+        """Test hook: the next bulk_search_dev on variant (1, 0) lets a bounded
+        device wait run out (reported by kernel_status)."""
+        self._ck(lib().dabs_test_stall_next_search(self._h))
 
     # ---------------------------------------------------------------- solve
     def solve(self, budget: int, seed: int, target: int | None = None):

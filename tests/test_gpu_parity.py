@@ -590,3 +590,37 @@ def test_smem_delta_variant_at_the_delta_range_limit(D, orc):
     n = 16384
     W = wl.dense_qubo(n, 32000, 32767, seed=5)
     bulk_case(D, orc, W, [0, 1, 2, 3, 4], variant=(1, 0), s=(1, 256), b=(1, 256), dflip=0.001, S=5)
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(D, orc):
+    """Variant (1, 0) waits for each row copy with a bounded mbarrier wait.
+    The test hook withholds one copy: the wait runs out, the kernel sets the
+    flag and returns, dabs_kernel_status reports DABS_E_TIMEOUT, and the same
+    context then runs a batch search that matches the oracle."""
+    n, S = 300, 2
+    W = wl.dense_qubo(n, -100, 100, seed=31)
+    ctx = ctx_for(D, W, searches=S, pools=1, pool_cap=4)
+    ctx.set_variant(1, 0)
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).view(dt)).cuda()
+    X0 = np.zeros((S, n), np.uint8)
+    dpad = np.zeros((S, ctx.ld), np.int32)
+    dpad[:, :n] = np.diag(W)
+    args = [t(wl.pack_bits(X0), np.int32), t(dpad, np.int32), t(np.zeros(S, np.int64), np.int64),
+            t(wl.pack_bits(X0), np.int32), t(np.array([1, 2], np.uint8), np.uint8),
+            torch.zeros((S, ctx.words), dtype=torch.int32, device="cuda"),
+            torch.zeros(S, dtype=torch.int64, device="cuda"),
+            torch.zeros(S, dtype=torch.int32, device="cuda")]
+    ctx.test_stall_next_search()
+    ctx.bulk_search_dev(3, 0, *args)
+    with pytest.raises(D.DabsError) as e:
+        ctx.kernel_status()
+    assert e.value.code == D.E_TIMEOUT
+    ctx.kernel_status()  # the flag was cleared
+    ctx.bulk_search_dev(3, 0, *args)  # the same context, no hook: a normal batch search
+    ctx.kernel_status()
+    p = orc.make_params(searches=1, pools=1, pool_cap=4, tabu=8, s=(1, 4), b=(2, 1))
+    for s in range(S):
+        r = orc.batch_search(W, p, 3, 0, s, X0[s], np.diag(W).astype(np.int32), 0, X0[s], [1, 2][s])
+        assert int(args[7][s]) == r["flips"] and int(args[6][s]) == r["best_E"]
+    with pytest.raises(D.DabsError):
+        D.Context(W, searches=4, pools=1).test_stall_next_search()  # register variants: no hook
