@@ -480,6 +480,7 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
   TRY(dalloc(ctx, &ctx->stats, kStats));
   TRY(dalloc(ctx, &ctx->rflag, 1));
   TRY(dalloc(ctx, &ctx->serr, 1));
+  TRY(cudaMemset(ctx->serr, 0, sizeof(int)) == cudaSuccess ? DABS_OK : DABS_E_CUDA);
   TRY(dalloc(ctx, &ctx->one_X, nw));
   TRY(dalloc(ctx, &ctx->one_d, ld));
   TRY(dalloc(ctx, &ctx->one_E, 1));
