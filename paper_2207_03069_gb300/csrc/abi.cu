@@ -47,8 +47,11 @@ bool params_ok(const dabs_params* p) {
          (p->restart == 0 || p->restart == 1) && (p->abs_mode == 0 || p->abs_mode == 1);
 }
 
+// the smallest variant that holds n, in the order measured fastest per size
+// band on this GPU (n <= 256, 512, 1024, 2048, 4096, 8192, 16384); the same
+// order sizes server admission (batch.cu) and the allocation-free search
 bool default_variant(int n, SearchVariant* v) {
-  static const int order[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 4}, {4, 4}, {8, 4}, {16, 4}};
+  static const int order[][2] = {{1, 1}, {1, 2}, {1, 4}, {4, 2}, {4, 4}, {8, 4}, {16, 4}};
   for (auto& o : order) {
     SearchVariant q;
     if (launch_search(o[0], o[1], nullptr, nullptr, &q) && q.cap >= n) {

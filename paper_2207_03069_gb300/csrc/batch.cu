@@ -313,7 +313,7 @@ extern "C" int dabs_server_submit(dabs_server* s, const int16_t* W, int32_t n, c
   r->bytes = ctx_bytes(n, *p);
   if (r->bytes > s->budget) return DABS_E_TOO_LARGE;
   {
-    static const int order[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 4}, {4, 4}, {8, 4}, {16, 4}};
+    static const int order[][2] = {{1, 1}, {1, 2}, {1, 4}, {4, 2}, {4, 4}, {8, 4}, {16, 4}};
     int nwarp = 1;
     for (auto& o : order) {
       SearchVariant v;

@@ -85,7 +85,7 @@ extern "C" int dabs_bulk_search_noalloc(const int16_t* W, int32_t n, int32_t ld,
   DevCtrl* ctrl = reinterpret_cast<DevCtrl*>(base + kOffCtrl);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-  static const int pick[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 4}, {4, 4}, {8, 4}, {16, 4}};
+  static const int pick[][2] = {{1, 1}, {1, 2}, {1, 4}, {4, 2}, {4, 4}, {8, 4}, {16, 4}};
   SearchVariant var{};
   bool ok = false;
   for (auto& o : pick)
