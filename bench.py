@@ -309,14 +309,17 @@ def small_graphs(dabs, generations=200, reps=3):
 
 
 def serving(dabs, seconds=4.0, rate=50.0, generations=20, sizes=(512, 1024, 2048, 4096, 8192),
-            budget_gb=60, plain=True):
-    """Poisson arrivals (seed 4) of dense QUBOs, n uniform in `sizes`, 256
-    searches, 20 generations each, recompute seeding; served with continuous
-    batching under an HBM budget, and (plain) one request at a time on the
-    same trace.  Latency = completion - arrival."""
+            budget_gb=60, plain=True, big=16384):
+    """Poisson arrivals (seed 4) of dense QUBOs, n uniform in `sizes`, plus one
+    n = `big` instance mid-trace, 256 searches, 20 generations each, recompute
+    seeding; served with continuous batching under an HBM budget, and (plain)
+    one request at a time on the same trace.  Latency = completion - arrival."""
     rng = np.random.default_rng(4)
     arr = wl.poisson_arrivals(rate, seconds, seed=4)
     reqs = [(float(t), int(rng.choice(sizes)), 5000 + i) for i, t in enumerate(arr)]
+    if big:  # the one n = 16384 instance (512 MB of int16 W), arriving mid-trace
+        reqs.append((seconds / 2, big, 9999))
+        reqs.sort()
     kw = dict(searches=256, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=1,
               max_generations=generations)
     params = dabs.default_params(**kw)
@@ -330,8 +333,10 @@ def serving(dabs, seconds=4.0, rate=50.0, generations=20, sizes=(512, 1024, 2048
 
     for _, n, sd in reqs:  # instances are prepared before the clock starts
         W_of(n, sd)
-    out = {"workload": f"Poisson {rate}/s for {seconds}s, n in {list(sizes)}, 256 searches, "
-                       f"{generations} generations, recompute seeding", "requests": len(reqs)}
+    out = {"workload": f"Poisson {rate}/s for {seconds}s, n in {list(sizes)}"
+                       + (f" plus one n={big} instance" if big else "")
+                       + f", 256 searches, {generations} generations, recompute seeding",
+           "requests": len(reqs)}
     srv = dabs.Server(budget_gb << 30)
     t0 = time.perf_counter()
     tickets, i, pending = [], 0, 0
@@ -348,10 +353,12 @@ def serving(dabs, seconds=4.0, rate=50.0, generations=20, sizes=(512, 1024, 2048
         pending = srv.step(1)
     wall = time.perf_counter() - t0
     lat, fl = [], 0
-    for t in tickets:
+    for t, (_, n, _) in zip(tickets, reqs):
         st, X, E, F, L = srv.poll(t)
         lat.append(L)
         fl += F
+        if n == big:
+            out["served_big_latency_s"] = L
     srv.close()
     out.update({"served_p50_s": pct(lat, 50), "served_p99_s": pct(lat, 99),
                 "served_flips_per_s": fl / wall, "served_wall_s": wall})
