@@ -80,9 +80,8 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
           if (w == INT16_MIN)
             return fail(ctx, DABS_E_INVALID_ARG, "W[%d][%d] = -32768 (weights must lie in [-32767, 32767])", i, j);
         }
-  // one row-major pass: the padded W and -W, the diagonal, the largest row sum
-  // of |W| and the off-diagonal non-zero count
-  std::vector<int16_t> pad((size_t)n * ld, 0);
+  // one row-major pass: the diagonal, the largest row sum of |W| and the
+  // off-diagonal non-zero count
   std::vector<int32_t> dg(n);
   int64_t R = 0;
   size_t nnz_all = 0;
@@ -92,7 +91,6 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
     size_t z = 0;
     for (int j = 0; j < n; ++j) {
       const int16_t w = wr[j];
-      pad[(size_t)i * ld + j] = w;
       r += w < 0 ? -(int)w : (int)w;
       z += w != 0;
     }
@@ -132,9 +130,12 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
     ctx->w_hash = h ^ (uint64_t)nb;
   }
   CK(cudaStreamSynchronize(ctx->stream));
-  CK(cudaMemcpy(ctx->W, pad.data(), pad.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+  // rows of n entries into rows of ld (the padding columns stay zero from creation),
+  // straight from the caller's buffer (a DMA when it is pinned)
+  CK(cudaMemcpy2D(ctx->W, (size_t)ld * sizeof(int16_t), W, (size_t)n * sizeof(int16_t),
+                  (size_t)n * sizeof(int16_t), (size_t)n, cudaMemcpyHostToDevice));
   {  // -W on the device (the flip kernels read row i of sigma(x_i) W directly)
-    const size_t cnt = pad.size();
+    const size_t cnt = (size_t)n * ld;
     k_negate<<<(unsigned)std::min<size_t>((cnt / 8 + 255) / 256 + 1, 4096), 256, 0, ctx->stream>>>(ctx->W, ctx->Wneg, cnt);
     CKLAUNCH();
     CK(cudaStreamSynchronize(ctx->stream));
@@ -459,6 +460,7 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
   }
   TRY(dalloc(ctx, &ctx->sp_row, 4 * (size_t)sparse_row16(n)));
   TRY(dalloc(ctx, &ctx->W, (size_t)n * ld));
+  TRY(cudaMemset(ctx->W, 0, (size_t)n * ld * sizeof(int16_t)) == cudaSuccess ? DABS_OK : DABS_E_CUDA);
   TRY(dalloc(ctx, &ctx->Wneg, (size_t)n * ld));
   TRY(dalloc(ctx, &ctx->diag, (size_t)n));
   TRY(dalloc(ctx, &ctx->ctrl, 1));
