@@ -67,6 +67,10 @@ bool rows_ok(const dabs_ctx* ctx, const SearchVariant& v, int mode);
 
 int upload_weights(dabs_ctx* ctx, const int16_t* W) {
   const int n = ctx->n, ld = ctx->ld;
+  // launch arguments that depend on W's values (a captured generation stays
+  // valid while they do not change: W itself is read through fixed pointers)
+  const int old_kb = ctx->key_bits, old_nnz = ctx->sp_nnz, old_rows = ctx->rows_mode;
+  const uint32_t* old_ent = ctx->sp_ent;
   // symmetry and the -32768 check over the upper triangle, in 64 x 64 tiles
   // (the transposed reads of a tile stay in cache)
   constexpr int TB = 64;
@@ -171,7 +175,9 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
     ctx->sp_nnz = nnz;
   }
   if (!rows_ok(ctx, ctx->var, ctx->rows_mode)) ctx->rows_mode = ROWS_DENSE;
-  graph_stale(ctx);  // key bits, sparse-row arrays and the row format may have changed
+  if (ctx->key_bits != old_kb || ctx->sp_nnz != old_nnz || ctx->rows_mode != old_rows ||
+      ctx->sp_ent != old_ent)
+    graph_stale(ctx);
   if (ctx->tc_ready) return tc_limbs(ctx);
   return DABS_OK;
 }

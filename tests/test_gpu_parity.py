@@ -237,6 +237,22 @@ def test_graph_generations_equal_kernel_by_kernel(D):
         assert np.array_equal(np.asarray(a), np.asarray(b))
 
 
+def test_graph_survives_new_weights_of_the_same_shape(D):
+    """dabs_load_weights keeps the captured generation when no launch argument
+    changes (same key bits, no sparse rows): the replay must read the new W."""
+    n = 200
+    W1, W2 = wl.dense_qubo(n, -100, 100, seed=41), wl.dense_qubo(n, -100, 100, seed=42)
+    kw = dict(searches=32, pools=4, pool_cap=8, tabu=8, s=(1, 10), b=(1, 1), max_generations=4)
+    ctx = D.Context(W1, **kw)
+    ctx.solve(10**9, seed=1)
+    ctx.load_weights(W2)
+    got = ctx.solve(10**9, seed=2)
+    ref = D.Context(W2, **kw)
+    ref.set_graphs(False)
+    want = ref.solve(10**9, seed=2)
+    assert got[1:] == want[1:] and np.array_equal(got[0], want[0])
+
+
 def test_checkpoint_restore_continues_exactly(D, orc):
     n, S = 90, 48
     W = wl.dense_qubo(n, -100, 100, seed=6)
