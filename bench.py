@@ -192,6 +192,14 @@ def pct(xs, q):
     return xs[k]
 
 
+def row_roofline(row_bytes_per_s):
+    """The flip kernel's algorithmic row traffic (2 n bytes per flip) as a
+    fraction of the measured HBM copy peak (whole-run rates, host timing)."""
+    hbm, kind = peaks()
+    return {"row_gbs": row_bytes_per_s / 1e9, "frac_of_hbm": row_bytes_per_s / 1e9 / hbm,
+            "peak": f"{kind} HBM copy {hbm:.0f} GB/s"}
+
+
 def tsp_ttt(dabs, seeds=8, generations=30):
     """TSP-shaped QUBO (32 cities, one-hot 1024 bits, 2048 searches, b = 1,
     s = 1/10): per seed the target is the best energy that seed's solve reaches
@@ -215,7 +223,7 @@ def tsp_ttt(dabs, seeds=8, generations=30):
     return {"workload": "TSP 32 cities one-hot n=1024, 2048 searches, b=1, s=1/10",
             "seeds": seeds, "target": f"best energy of the same seed after {generations} generations",
             "ttt_p50_s": pct(ttt, 50), "ttt_p99_s": pct(ttt, 99), "flips_per_s": flips / sum(ttt),
-            "feasible_targets": feasible}
+            "feasible_targets": feasible, "roofline": row_roofline(flips / sum(ttt) * 2 * 1024)}
 
 
 def batched_vs_plain(dabs, count=64, generations=3):
@@ -242,6 +250,7 @@ def batched_vs_plain(dabs, count=64, generations=3):
     same = all(b[1] == q[1] and b[2] == q[2] and np.array_equal(b[0], q[0])
                for b, q in zip(bout, pout))
     fl = sum(b[2] for b in bout)
+    row_bytes = sum(b[2] * 2 * int(n) for b, n in zip(bout, ns))
     # time to target: every instance's target is the energy it reaches alone in
     # `generations` generations; all 64 arrive at t = 0.  Plain: one solve after
     # another (an instance waits for those before it); served: submitted at once
@@ -271,6 +280,7 @@ def batched_vs_plain(dabs, count=64, generations=3):
                         f"{generations} generations, tensor-core recompute seeding",
             "batched_flips_per_s": fl / tb, "plain_flips_per_s": fl / tp,
             "speedup": tp / tb, "identical_results": bool(same), "flips": fl,
+            "roofline_batched": row_roofline(row_bytes / tb),
             "ttt": {"target": f"the energy each instance reaches alone in {generations} generations; "
                               f"all {count} arrive at t = 0",
                     "plain_p50_s": pct(plain_ttt, 50), "plain_p99_s": pct(plain_ttt, 99),
@@ -303,6 +313,7 @@ def small_graphs(dabs, generations=200, reps=3):
                                                            "ms_per_generation": best * 1e3 / generations}
         ctx.close()
     out["identical_results"] = res[True] == res[False]
+    out["roofline"] = row_roofline(out["graphs"]["flips_per_s"] * 2 * 64)
     out["speedup"] = out["kernel_by_kernel"]["ms_per_generation"] / out["graphs"]["ms_per_generation"]
     out["workload"] = "dense n=64, 32 searches, 200 generations x >= 64 flips per search"
     return out
@@ -352,16 +363,18 @@ def serving(dabs, seconds=4.0, rate=50.0, generations=20, sizes=(512, 1024, 2048
             continue
         pending = srv.step(1)
     wall = time.perf_counter() - t0
-    lat, fl = [], 0
+    lat, fl, rb = [], 0, 0
     for t, (_, n, _) in zip(tickets, reqs):
         st, X, E, F, L = srv.poll(t)
         lat.append(L)
         fl += F
+        rb += F * 2 * n
         if n == big:
             out["served_big_latency_s"] = L
     srv.close()
     out.update({"served_p50_s": pct(lat, 50), "served_p99_s": pct(lat, 99),
-                "served_flips_per_s": fl / wall, "served_wall_s": wall})
+                "served_flips_per_s": fl / wall, "served_wall_s": wall,
+                "roofline_served": row_roofline(rb / wall)})
     if plain:
         t0 = time.perf_counter()
         lat2, free_at = [], 0.0
