@@ -651,9 +651,7 @@ struct Searcher {
             const uint64_t R = (q * span) >> 32;
             // threshold in [mn, mx]: fits int32
             const int thr = (int)((int64_t)mn + (int64_t)(((uint64_t)u0 * (R + 1)) >> 32));
-#pragma unroll
-            for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)(d[p] <= thr) << p;
-            Cm &= F;
+            Cm = mask_of([&](int p) { return d[p] <= thr; }) & F;
             ukth = __shfl_sync(FULL, rnd1, it & 31);
           } else {
             int cmp[CH];
@@ -670,9 +668,7 @@ struct Searcher {
             m = v[0];
             const int pm = v[1];
             if (pm != INT_MAX) {
-#pragma unroll
-              for (int p = 0; p < EPT; ++p) Cm |= (uint32_t)(d[p] <= pm) << p;
-              Cm &= F;
+              Cm = mask_of([&](int p) { return d[p] <= pm; }) & F;
             } else {
               Cm = F;
             }
@@ -726,15 +722,10 @@ struct Searcher {
           thr = thr < c8 ? c8 : (thr > 256u ? 256u : thr);
           if (!rr_ready) randmin_draw(flips, rr);
           rr_ready = false;
-          uint32_t Cm = 0;
-#pragma unroll
-          for (int c = 0; c < CH; ++c)
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const uint32_t u8 = ((e < 4 ? rr[c].x : rr[c].y) >> (8 * (e & 3))) & 0xFFu;
-              Cm |= (uint32_t)(u8 < thr) << (8 * c + e);
-            }
-          Cm &= F;
+          const uint32_t Cm = mask_of([&](int p) {
+            const int c = p >> 3, e = p & 7;
+            return (((e < 4 ? rr[c].x : rr[c].y) >> (8 * (e & 3))) & 0xFFu) < thr;
+          }) & F;
           int cmc[CH];
           chunk_min(Cm, cmc);
           int v[2] = {min_of(cma), min_of(cmc)};
