@@ -67,3 +67,38 @@ def test_create_without_gpu_reports_no_device(L):
     h = C.c_void_p()
     p = dabs.default_params(searches=4, pools=1)
     assert L.dabs_create(W.ctypes.data_as(C.c_void_p), 4, C.byref(p), C.byref(h)) == dabs.E_NO_DEVICE
+
+
+def test_header_is_plain_c_and_links(L, tmp_path):
+    """include/dabs.h is a C ABI: a C99 program using its types and calls
+    compiles with gcc and links against libdabs.so (it is not run: no GPU)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src = tmp_path / "use_dabs.c"
+    src.write_text(r"""
+#include <stdint.h>
+#include <stdio.h>
+#include "dabs.h"
+int main(void) {
+    dabs_params p;
+    int16_t W[4] = {1, -2, -2, 3};
+    dabs_ctx* ctx = NULL;
+    uint8_t x[2];
+    int64_t e = 0;
+    uint64_t flips = 0;
+    if (dabs_params_default(&p) != DABS_OK) return 1;
+    int rc = dabs_create(W, 2, &p, &ctx);
+    if (rc != DABS_OK) { printf("%s\n", dabs_strerror(rc)); return 0; }
+    rc = dabs_solve(ctx, 1000, 1, INT64_MIN, x, &e, &flips);
+    dabs_destroy(ctx);
+    return rc == DABS_OK ? 0 : 2;
+}
+""")
+    lib = os.path.join(ROOT, "paper_2207_03069_gb300")
+    out = tmp_path / "use_dabs"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-L", lib, "-ldabs", "-Wl,-rpath," + lib, "-o", str(out)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
