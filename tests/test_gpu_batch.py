@@ -105,3 +105,24 @@ def test_server_warp_cap_serves_in_arrival_order(D):
         st, X, E, F, _ = srv.poll(t)
         aX, aE, aF = D.Context(W, **kw).solve(10**9, 40 + k)
         assert (E, F) == (aE, aF) and np.array_equal(X, aX)
+
+
+def test_batch_with_row_formats_equals_alone(D):
+    """Contexts set to sparse rows (shared or global) or to W in shared memory
+    join a batched solve (whose launches read dense rows) with the results each
+    gets alone in its own format."""
+    kw = dict(searches=64, pools=4, pool_cap=16, tabu=8, s=(1, 10), b=(1, 1), max_generations=3)
+    Ws = [wl.maxcut_qubo(300, 0.05, seed=1), wl.maxcut_qubo(700, 0.03, seed=2),
+          wl.dense_qubo(200, -100, 100, seed=3)]
+    modes = [D.ROWS_SPARSE_SMEM, D.ROWS_SPARSE_GLOBAL, D.ROWS_DENSE_SMEM]
+    ctxs = []
+    for W, m in zip(Ws, modes):
+        c = D.Context(W, **kw)
+        c.set_rows(m)
+        ctxs.append(c)
+    out = D.batch_solve(ctxs, [10**9] * 3, [5, 6, 7])
+    for k, (W, m) in enumerate(zip(Ws, modes)):
+        alone = D.Context(W, **kw)
+        alone.set_rows(m)
+        a = alone.solve(10**9, 5 + k)
+        assert out[k][1] == a[1] and out[k][2] == a[2] and np.array_equal(out[k][0], a[0])
