@@ -200,7 +200,7 @@ def row_roofline(row_bytes_per_s):
             "peak": f"{kind} HBM copy {hbm:.0f} GB/s"}
 
 
-def tsp_ttt(dabs, seeds=8, generations=30):
+def tsp_ttt(dabs, seeds=32, generations=30):
     """TSP-shaped QUBO (32 cities, one-hot 1024 bits, 2048 searches, b = 1,
     s = 1/10): per seed the target is the best energy that seed's solve reaches
     in `generations` generations; time-to-target = wall time of the solve with
