@@ -65,43 +65,59 @@ bool default_variant(int n, SearchVariant* v) {
 int tc_limbs(dabs_ctx* ctx);
 bool rows_ok(const dabs_ctx* ctx, const SearchVariant& v, int mode);
 
+// Loads W (host, n x n, row-major): one DMA into the -W buffer as staging,
+// then the checks and row measurements on the device (weights.cu).  Only
+// their verdict comes back to the host; when it rejects W, -W is rebuilt
+// from the unchanged W and the context is as before the call.
 int upload_weights(dabs_ctx* ctx, const int16_t* W) {
   const int n = ctx->n, ld = ctx->ld;
+  cudaStream_t st = ctx->stream;
   // launch arguments that depend on W's values (a captured generation stays
   // valid while they do not change: W itself is read through fixed pointers)
   const int old_kb = ctx->key_bits, old_nnz = ctx->sp_nnz, old_rows = ctx->rows_mode;
   const uint32_t* old_ent = ctx->sp_ent;
-  // symmetry and the -32768 check over the upper triangle, in 64 x 64 tiles
-  // (the transposed reads of a tile stay in cache)
-  constexpr int TB = 64;
-  for (int bi = 0; bi < n; bi += TB)
-    for (int bj = bi; bj < n; bj += TB)
-      for (int i = bi; i < std::min(bi + TB, n); ++i)
-        for (int j = std::max(bj, i); j < std::min(bj + TB, n); ++j) {
-          const int16_t w = W[(size_t)i * n + j];
-          if (w != W[(size_t)j * n + i])
-            return fail(ctx, DABS_E_NOT_SYMMETRIC, "W[%d][%d] != W[%d][%d]", i, j, j, i);
-          if (w == INT16_MIN)
-            return fail(ctx, DABS_E_INVALID_ARG, "W[%d][%d] = -32768 (weights must lie in [-32767, 32767])", i, j);
-        }
-  // one row-major pass: the diagonal, the largest row sum of |W| and the
-  // off-diagonal non-zero count
-  std::vector<int32_t> dg(n);
-  int64_t R = 0;
-  size_t nnz_all = 0;
-  for (int i = 0; i < n; ++i) {
-    const int16_t* wr = W + (size_t)i * n;
-    int64_t r = 0;
-    size_t z = 0;
-    for (int j = 0; j < n; ++j) {
-      const int16_t w = wr[j];
-      r += w < 0 ? -(int)w : (int)w;
-      z += w != 0;
+  WeightsArgs a{};
+  a.Ws = ctx->Wneg;
+  a.W = ctx->W;
+  a.Wneg = ctx->Wneg;
+  a.diag = ctx->diag;
+  a.n = n;
+  a.ld = ld;
+  a.rowsum = ctx->wrow;
+  a.rowcnt = ctx->wrow + n;
+  a.rowptr = ctx->wptr;
+  a.rowptr_len = 4 * sparse_row16(n);
+  a.chk = ctx->wchk;
+  // stream order keeps the DMA behind any generation still reading -W
+  CK(cudaMemcpy2DAsync(ctx->Wneg, (size_t)ld * sizeof(int16_t), W, (size_t)n * sizeof(int16_t),
+                       (size_t)n * sizeof(int16_t), (size_t)n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(ctx->wrow, 0, 2 * (size_t)n * sizeof(uint32_t), st));
+  CK(cudaMemsetAsync(ctx->wchk, 0xff, sizeof(WCheck), st));
+  const unsigned tiles = (unsigned)((n + 31) / 32);
+  k_weights_tiles<<<dim3(tiles, tiles), dim3(32, 8), 0, st>>>(a);
+  CKLAUNCH();
+  k_weights_rows<<<1, 1024, 0, st>>>(a);
+  CKLAUNCH();
+  CK(cudaMemcpyAsync(ctx->h_wchk, ctx->wchk, sizeof(WCheck), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const WCheck c = *ctx->h_wchk;
+  const unsigned vec_blocks = (unsigned)std::min<size_t>(((size_t)n * ld / 8 + 255) / 256, 4096);
+  if (c.bad != ~0ull || c.low != ~0ull) {
+    k_negate<<<vec_blocks, 256, 0, st>>>(ctx->W, ctx->Wneg, (size_t)n * ld);
+    CKLAUNCH();
+    CK(cudaStreamSynchronize(st));
+    if (c.bad != ~0ull) {
+      const int i = (int)(c.bad / n), j = (int)(c.bad % n);
+      return fail(ctx, DABS_E_NOT_SYMMETRIC, "W[%d][%d] != W[%d][%d]", i, j, j, i);
     }
-    dg[i] = wr[i];
-    R = std::max(R, r);
-    nnz_all += z - (wr[i] != 0);
+    return fail(ctx, DABS_E_INVALID_ARG, "W[%d][%d] = -32768 (weights must lie in [-32767, 32767])",
+                (int)(c.low / n), (int)(c.low % n));
   }
+  k_weights_commit<<<vec_blocks, 256, 0, st>>>(a);
+  CKLAUNCH();
+  ctx->w_hash_ok = false;
+  const int64_t R = (int64_t)c.R;
+  const size_t nnz_all = (size_t)c.nnz;
   // keyed Delta: |Delta_k| <= R_k = sum_j |W_kj| in every state, and a key
   // (Delta << kb | k << 1 | x_k) plus the diagonal term added to it before
   // Eq. (5) overwrites it must stay inside int32
@@ -113,11 +129,49 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
     ctx->smem_ok = R < (1 << 29) - 1 &&
                    smem_search_bytes(n) + 1024 <= (size_t)std::max(ctx->smem_optin, 0);
   }
-  // hash of W (ties checkpoints to their instance): four independent
-  // xor-multiply chains over 64-bit words, then the tail bytes
-  {
-    const unsigned char* by = reinterpret_cast<const unsigned char*>(W);
-    const size_t nb = (size_t)n * n * sizeof(int16_t);
+  // sparse rows: the off-diagonal non-zeros of each row, column ascending,
+  // kept while they take at most half the bytes of the dense rows (or 64
+  // entries, for tiny instances)
+  const size_t limit = std::max<size_t>((size_t)n * n / 4, 64);
+  ctx->sp_nnz = -1;
+  if (nnz_all <= limit) {
+    const int nnz = (int)nnz_all;
+    const size_t cap = 4 * (size_t)sparse_ent16(nnz);
+    if (cap > ctx->sp_cap) {
+      CK(cudaStreamSynchronize(st));
+      if (ctx->sp_ent) cudaFree(ctx->sp_ent);
+      ctx->sp_ent = nullptr;
+      ctx->sp_cap = 0;
+      CK(cudaMalloc(&ctx->sp_ent, cap * 4));
+      ctx->sp_cap = cap;
+    }
+    a.ent = ctx->sp_ent;
+    CK(cudaMemcpyAsync(ctx->sp_row, ctx->wptr, 4 * (size_t)sparse_row16(n) * 4, cudaMemcpyDeviceToDevice, st));
+    if (cap > (size_t)nnz) CK(cudaMemsetAsync(ctx->sp_ent + nnz, 0, (cap - nnz) * 4, st));
+    k_sparse_fill<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(a);
+    CKLAUNCH();
+    ctx->sp_nnz = nnz;
+  }
+  if (!rows_ok(ctx, ctx->var, ctx->rows_mode)) ctx->rows_mode = ROWS_DENSE;
+  if (ctx->key_bits != old_kb || ctx->sp_nnz != old_nnz || ctx->rows_mode != old_rows ||
+      ctx->sp_ent != old_ent)
+    graph_stale(ctx);
+  if (ctx->tc_ready) return tc_limbs(ctx);
+  return DABS_OK;
+}
+
+// hash of W (ties checkpoints to their instance), from the device copy on
+// first use after a load: four independent xor-multiply chains over the
+// row-major n x n bytes in 64-bit words, then the tail bytes
+static int weights_hash(dabs_ctx* ctx, uint64_t* out) {
+  if (!ctx->w_hash_ok) {
+    const int n = ctx->n;
+    std::vector<int16_t> h((size_t)n * n);
+    CK(cudaMemcpy2DAsync(h.data(), (size_t)n * sizeof(int16_t), ctx->W, (size_t)ctx->ld * sizeof(int16_t),
+                         (size_t)n * sizeof(int16_t), (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const unsigned char* by = reinterpret_cast<const unsigned char*>(h.data());
+    const size_t nb = h.size() * sizeof(int16_t);
     const uint64_t P = 1099511628211ull;
     uint64_t ln[4] = {1469598103934665603ull, 0x9E3779B97F4A7C15ull, 0xC2B2AE3D27D4EB4Full,
                       0x165667B19E3779F9ull};
@@ -129,56 +183,12 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
         ln[l] = (ln[l] ^ w) * P;
       }
     for (; q < nb; ++q) ln[0] = (ln[0] ^ by[q]) * P;
-    uint64_t h = ln[0];
-    for (int l = 1; l < 4; ++l) h = (h ^ ((ln[l] << (16 * l)) | (ln[l] >> (64 - 16 * l)))) * P;
-    ctx->w_hash = h ^ (uint64_t)nb;
+    uint64_t hv = ln[0];
+    for (int l = 1; l < 4; ++l) hv = (hv ^ ((ln[l] << (16 * l)) | (ln[l] >> (64 - 16 * l)))) * P;
+    ctx->w_hash = hv ^ (uint64_t)nb;
+    ctx->w_hash_ok = true;
   }
-  CK(cudaStreamSynchronize(ctx->stream));
-  // rows of n entries into rows of ld (the padding columns stay zero from creation),
-  // straight from the caller's buffer (a DMA when it is pinned)
-  CK(cudaMemcpy2D(ctx->W, (size_t)ld * sizeof(int16_t), W, (size_t)n * sizeof(int16_t),
-                  (size_t)n * sizeof(int16_t), (size_t)n, cudaMemcpyHostToDevice));
-  {  // -W on the device (the flip kernels read row i of sigma(x_i) W directly)
-    const size_t cnt = (size_t)n * ld;
-    k_negate<<<(unsigned)std::min<size_t>((cnt / 8 + 255) / 256 + 1, 4096), 256, 0, ctx->stream>>>(ctx->W, ctx->Wneg, cnt);
-    CKLAUNCH();
-    CK(cudaStreamSynchronize(ctx->stream));
-  }
-  CK(cudaMemcpy(ctx->diag, dg.data(), dg.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  // sparse rows: the off-diagonal non-zeros of each row, column ascending,
-  // kept while they take at most half the bytes of the dense rows (or 64
-  // entries, for tiny instances)
-  const size_t limit = std::max<size_t>((size_t)n * n / 4, 64);
-  ctx->sp_nnz = -1;
-  if (nnz_all <= limit) {
-    std::vector<uint32_t> rp(4 * (size_t)sparse_row16(n), 0), ent;
-    ent.reserve(nnz_all);
-    for (int i = 0; i < n; ++i) {
-      rp[i] = (uint32_t)ent.size();
-      for (int k = 0; k < n; ++k) {
-        const int16_t w = W[(size_t)i * n + k];
-        if (k != i && w != 0) ent.push_back(((uint32_t)k << 16) | (uint16_t)w);
-      }
-    }
-    rp[n] = (uint32_t)ent.size();
-    const int nnz = (int)ent.size();
-    ent.resize(4 * (size_t)sparse_ent16(nnz), 0u);
-    if (ent.size() > ctx->sp_cap) {
-      if (ctx->sp_ent) cudaFree(ctx->sp_ent);
-      ctx->sp_ent = nullptr;
-      ctx->sp_cap = 0;
-      CK(cudaMalloc(&ctx->sp_ent, ent.size() * 4));
-      ctx->sp_cap = ent.size();
-    }
-    CK(cudaMemcpy(ctx->sp_row, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice));
-    if (!ent.empty()) CK(cudaMemcpy(ctx->sp_ent, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice));
-    ctx->sp_nnz = nnz;
-  }
-  if (!rows_ok(ctx, ctx->var, ctx->rows_mode)) ctx->rows_mode = ROWS_DENSE;
-  if (ctx->key_bits != old_kb || ctx->sp_nnz != old_nnz || ctx->rows_mode != old_rows ||
-      ctx->sp_ent != old_ent)
-    graph_stale(ctx);
-  if (ctx->tc_ready) return tc_limbs(ctx);
+  *out = ctx->w_hash;
   return DABS_OK;
 }
 
@@ -417,6 +427,7 @@ void dabs_destroy(dabs_ctx* ctx) {
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->sp_ent) cudaFree(ctx->sp_ent);
   if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
+  if (ctx->h_wchk) cudaFreeHost(ctx->h_wchk);
   if (ctx->own) cudaStreamDestroy(ctx->own);
   delete ctx;
 }
@@ -466,9 +477,12 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
   }
   TRY(dalloc(ctx, &ctx->sp_row, 4 * (size_t)sparse_row16(n)));
   TRY(dalloc(ctx, &ctx->W, (size_t)n * ld));
-  TRY(cudaMemset(ctx->W, 0, (size_t)n * ld * sizeof(int16_t)) == cudaSuccess ? DABS_OK : DABS_E_CUDA);
+  TRY(cudaMemsetAsync(ctx->W, 0, (size_t)n * ld * sizeof(int16_t), ctx->stream) == cudaSuccess ? DABS_OK : DABS_E_CUDA);
   TRY(dalloc(ctx, &ctx->Wneg, (size_t)n * ld));
   TRY(dalloc(ctx, &ctx->diag, (size_t)n));
+  TRY(dalloc(ctx, &ctx->wrow, 2 * (size_t)n));
+  TRY(dalloc(ctx, &ctx->wptr, 4 * (size_t)sparse_row16(n)));
+  TRY(dalloc(ctx, &ctx->wchk, 1));
   TRY(dalloc(ctx, &ctx->ctrl, 1));
   TRY(dalloc(ctx, &ctx->bulk_ctrl, 1));
   for (int b = 0; b < 2; ++b) {
@@ -491,11 +505,12 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
   TRY(dalloc(ctx, &ctx->stats, kStats));
   TRY(dalloc(ctx, &ctx->rflag, 1));
   TRY(dalloc(ctx, &ctx->serr, 1));
-  TRY(cudaMemset(ctx->serr, 0, sizeof(int)) == cudaSuccess ? DABS_OK : DABS_E_CUDA);
+  TRY(cudaMemsetAsync(ctx->serr, 0, sizeof(int), ctx->stream) == cudaSuccess ? DABS_OK : DABS_E_CUDA);
   TRY(dalloc(ctx, &ctx->one_X, nw));
   TRY(dalloc(ctx, &ctx->one_d, ld));
   TRY(dalloc(ctx, &ctx->one_E, 1));
   if (cudaMallocHost(&ctx->h_ctrl, sizeof(DevCtrl)) != cudaSuccess) { dabs_destroy(ctx); return DABS_E_OOM; }
+  if (cudaMallocHost(&ctx->h_wchk, sizeof(WCheck)) != cudaSuccess) { dabs_destroy(ctx); return DABS_E_OOM; }
   if (ctx->merge_smem > 48 * 1024) {
     if (cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)ctx->merge_smem) != cudaSuccess) {
@@ -913,7 +928,8 @@ int dabs_kernel_status(dabs_ctx* ctx) {
     int e = 0;
     CK(cudaMemcpy(&e, flag, sizeof e, cudaMemcpyDeviceToHost));
     if (e) {
-      CK(cudaMemset(flag, 0, sizeof(int)));
+      CK(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
       return fail(ctx, DABS_E_TIMEOUT, "a device wait ran out (kernel error %d)", e);
     }
   }
@@ -975,12 +991,14 @@ int dabs_checkpoint(dabs_ctx* ctx, void* buf, size_t cap, size_t* size) {
   if (!buf) return DABS_OK;
   if (cap < total) return fail(ctx, DABS_E_INVALID_ARG, "checkpoint buffer of %zu < %zu bytes", cap, total);
   CK(cudaStreamSynchronize(ctx->stream));
+  uint64_t wh = 0;
+  if (const int rc = weights_hash(ctx, &wh)) return rc;
   CkptHeader h{};
   memcpy(h.magic, "DABSCKP1", 8);
   h.version = 2;
   h.n = ctx->n; h.S = ctx->S; h.P = ctx->P; h.C = ctx->C;
   h.p = ctx->p;
-  h.w_hash = ctx->w_hash;
+  h.w_hash = wh;
   h.bytes = total;
   unsigned char* o = static_cast<unsigned char*>(buf);
   memcpy(o, &h, sizeof h);
@@ -996,8 +1014,10 @@ int dabs_restore(dabs_ctx* ctx, const void* buf, size_t size) {
   if (!ctx || !buf || size < sizeof(CkptHeader)) return DABS_E_INVALID_ARG;
   CkptHeader h;
   memcpy(&h, buf, sizeof h);
+  uint64_t wh = 0;
+  if (const int rc = weights_hash(ctx, &wh)) return rc;
   if (memcmp(h.magic, "DABSCKP1", 8) != 0 || h.version != 2 || h.bytes != size || h.n != ctx->n ||
-      h.S != ctx->S || h.P != ctx->P || h.C != ctx->C || h.w_hash != ctx->w_hash ||
+      h.S != ctx->S || h.P != ctx->P || h.C != ctx->C || h.w_hash != wh ||
       memcmp(&h.p, &ctx->p, sizeof h.p) != 0)
     return fail(ctx, DABS_E_INVALID_ARG, "checkpoint does not match this context");
   const auto pieces = ckpt_pieces(ctx);

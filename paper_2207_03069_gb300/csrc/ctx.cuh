@@ -17,7 +17,8 @@ struct dabs_ctx {
   int dev = 0;
   int n = 0, ld = 0, nw = 0;
   dabs_params p{};
-  uint64_t w_hash = 0;  // FNV-1a of the host W
+  uint64_t w_hash = 0;      // FNV-1a-style hash of W (ties checkpoints to their instance)
+  bool w_hash_ok = false;   // w_hash is that of the current W (computed on demand)
   int T = 1, tau = 0;
   uint32_t B = 1;
   int S = 0, P = 0, C = 0, Mmax = 1;
@@ -26,6 +27,10 @@ struct dabs_ctx {
   int16_t* W = nullptr;
   int16_t* Wneg = nullptr;  // -W: lets the flip kernel read row i of sigma(x_i) W
   int32_t* diag = nullptr;
+  uint32_t* wrow = nullptr;   // [2n] row sums of |W| and row non-zero counts of a staged W
+  uint32_t* wptr = nullptr;   // [4 * sparse_row16(n)] their prefix sums (sparse row starts)
+  WCheck* wchk = nullptr;     // checks of a staged W, and a pinned host copy
+  WCheck* h_wchk = nullptr;
   DevCtrl* ctrl = nullptr;
   DevCtrl* bulk_ctrl = nullptr;
   DevCtrl* h_ctrl = nullptr;  // pinned staging

@@ -95,6 +95,32 @@ struct EDArgs {
   const DevCtrl* ctrl; // optional: skip when a solve has stopped
 };
 
+// residency of W (weights.cu): verdict of the checks on a staged W
+struct WCheck {
+  unsigned long long bad;  // lowest i * n + j with W_ij != W_ji (all ones: none)
+  unsigned long long low;  // lowest i * n + j with W_ij = -32768 (all ones: none)
+  unsigned long long R;    // max_i sum_j |W_ij|
+  unsigned long long nnz;  // off-diagonal non-zeros
+};
+
+struct WeightsArgs {
+  const int16_t* Ws;  // staged rows [n][ld] (columns >= n unspecified)
+  int16_t* W;         // committed W [n][ld]
+  int16_t* Wneg;      // committed -W [n][ld] (may be the staging buffer)
+  int32_t* diag;      // [n]
+  int n, ld;
+  uint32_t* rowsum;   // [n] sums of |W_ij|, zeroed before k_weights_tiles
+  uint32_t* rowcnt;   // [n] off-diagonal non-zeros, zeroed before k_weights_tiles
+  uint32_t* rowptr;   // [rowptr_len] exclusive prefix sums of rowcnt, total, zeros
+  int rowptr_len;
+  WCheck* chk;        // bad and low set to all ones before k_weights_tiles
+  uint32_t* ent;      // sparse entries written by k_sparse_fill
+};
+
+__global__ void k_weights_tiles(const WeightsArgs a);
+__global__ void k_weights_rows(const WeightsArgs a);
+__global__ void k_weights_commit(const WeightsArgs a);
+__global__ void k_sparse_fill(const WeightsArgs a);
 __global__ void k_negate(const int16_t* W, int16_t* Wneg, size_t count);
 __global__ void k_pool_init(const PoolArgs a);
 __global__ void k_state_init(const StateArgs a);
