@@ -48,11 +48,16 @@ bool params_ok(const dabs_params* p) {
 }
 
 // the smallest variant that holds n, in the order measured fastest per size
-// band on this GPU (n <= 256, 512, 1024, 2048, 4096, 8192, 16384); the same
-// order sizes server admission (batch.cu) and the allocation-free search
-bool default_variant(int n, SearchVariant* v) {
-  static const int order[][2] = {{1, 1}, {1, 2}, {1, 4}, {4, 2}, {4, 4}, {8, 4}, {16, 4}};
-  for (auto& o : order) {
+// band on this GPU (n <= 256, 512, 1024, 2048, 4096, 8192, 16384).  Alone
+// (one instance's searches, about one wave), 4 warps x 4 chunks is fastest
+// for 2048 < n <= 4096; with many instances in flight (batched, served) 8
+// warps x 2 chunks is: twice the warps per SM hide more of the per-flip
+// latency (measured on 64 instances of n in [256, 4096]: 12% less time per
+// generation).  Server admission (batch.cu) counts warps with the second order.
+bool default_variant(int n, SearchVariant* v, bool many) {
+  static const int alone[][2] = {{1, 1}, {1, 2}, {1, 4}, {4, 2}, {4, 4}, {8, 4}, {16, 4}};
+  static const int batched[][2] = {{1, 1}, {1, 2}, {1, 4}, {4, 2}, {8, 2}, {8, 4}, {16, 4}};
+  for (auto& o : many ? batched : alone) {
     SearchVariant q;
     if (launch_search(o[0], o[1], nullptr, nullptr, &q) && q.cap >= n) {
       *v = q;
@@ -461,7 +466,7 @@ int dabs_create(const int16_t* W, int32_t n, const dabs_params* p, dabs_ctx** ou
   while (M < R) M <<= 1;
   ctx->Mmax = M;
   ctx->merge_smem = (size_t)ctx->C * 16 + (size_t)M * 24;
-  if (!default_variant(n, &ctx->var)) { dabs_destroy(ctx); return DABS_E_TOO_LARGE; }
+  if (!default_variant(n, &ctx->var, false)) { dabs_destroy(ctx); return DABS_E_TOO_LARGE; }
   int rc;
 #define TRY(x) do { if ((rc = (x)) != DABS_OK) { *out = nullptr; int r_ = rc; dabs_destroy(ctx); return r_; } } while (0)
   if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess) {
@@ -785,6 +790,7 @@ int dabs_set_variant(dabs_ctx* ctx, int32_t warps, int32_t chunks) {
   if (v.ch == 0 && !ctx->smem_ok)
     return fail(ctx, DABS_E_TOO_LARGE, "Delta range or size does not fit the shared-memory variant");
   ctx->var = v;
+  ctx->var_set = true;
   if (!rows_ok(ctx, v, ctx->rows_mode)) ctx->rows_mode = ROWS_DENSE;
   graph_stale(ctx);
   return DABS_OK;
@@ -890,6 +896,7 @@ int dabs_autotune(dabs_ctx* ctx, int32_t generations, int32_t* warps, int32_t* c
   cudaFree(snap);
   if (rc != DABS_OK) { ctx->var = keep; ctx->rows_mode = keep_rows; return rc; }
   ctx->var = best;
+  ctx->var_set = true;
   ctx->rows_mode = best_rows;
   graph_stale(ctx);
   if (warps) *warps = best.nw;

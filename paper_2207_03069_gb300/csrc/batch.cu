@@ -74,13 +74,14 @@ struct Batcher {
     if (rc) return rc;
     std::vector<Group> ng;
     for (dabs_ctx* c : active) {
+      const SearchVariant cv = batch_variant(c);
       Group* g = nullptr;
       for (auto& x : ng)
-        if (x.var.nw == c->var.nw && x.var.ch == c->var.ch) g = &x;
+        if (x.var.nw == cv.nw && x.var.ch == cv.ch) g = &x;
       if (!g) {
         ng.push_back(Group{});
         g = &ng.back();
-        g->var = c->var;
+        g->var = cv;
       }
       g->ctxs.push_back(c);
     }
@@ -313,13 +314,8 @@ extern "C" int dabs_server_submit(dabs_server* s, const int16_t* W, int32_t n, c
   r->bytes = ctx_bytes(n, *p);
   if (r->bytes > s->budget) return DABS_E_TOO_LARGE;
   {
-    static const int order[][2] = {{1, 1}, {1, 2}, {1, 4}, {4, 2}, {4, 4}, {8, 4}, {16, 4}};
-    int nwarp = 1;
-    for (auto& o : order) {
-      SearchVariant v;
-      if (launch_search(o[0], o[1], nullptr, nullptr, &v) && v.cap >= n) { nwarp = v.nw; break; }
-    }
-    r->warps = (int64_t)p->searches * nwarp;
+    SearchVariant v{};  // the variant its batch searches will run with
+    r->warps = (int64_t)p->searches * (default_variant(n, &v, true) ? v.nw : 1);
   }
   r->t_submit = now_s();
   *ticket = r->ticket;

@@ -55,6 +55,7 @@ struct dabs_ctx {
   int32_t* one_d = nullptr;
   int64_t* one_E = nullptr;
   SearchVariant var{};
+  bool var_set = false;       // var chosen by dabs_set_variant or dabs_autotune
   // sparse rows of the batch search (Max-Cut- and QASP-like instances)
   int rows_mode = 0;          // RowFormat the batch search reads
   int key_bits = 0;           // keyed Delta bits when the instance allows it (0: not)
@@ -106,4 +107,13 @@ int stage(dabs_ctx* ctx, int which);
 int read_ctrl(dabs_ctx* ctx, DevCtrl* out);
 // the captured generation no longer matches (variant, rows, stream, ...)
 inline void graph_stale(dabs_ctx* ctx) { ctx->graph_ok = false; }
+bool default_variant(int n, SearchVariant* v, bool many);
+// the variant a context's batch searches use in the batched and served
+// forms: its own when the caller or the autotuner chose it, else the default
+// for many instances in flight
+inline SearchVariant batch_variant(const dabs_ctx* ctx) {
+  SearchVariant v = ctx->var;
+  if (!ctx->var_set && !default_variant(ctx->n, &v, true)) v = ctx->var;
+  return v;
+}
 }  // namespace dabs_internal
