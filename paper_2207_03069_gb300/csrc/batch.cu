@@ -50,16 +50,42 @@ struct Batcher {
   SearchArgs* h_insts = nullptr;  // pinned staging
   int32_t* h_prefix = nullptr;
   int h_cap = 0;
+  // the groups' batch searches run concurrently, one side stream per group
+  // after the first, forked from and joined back into `stream`
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;  // ev[0] fork, ev[1 + g] join of side stream g
 
   ~Batcher() {
     if (stream) cudaStreamSynchronize(stream);
+    for (cudaStream_t s : side) cudaStreamSynchronize(s);
     for (auto& g : groups) {
       cudaFree(g.d_insts);
       cudaFree(g.d_prefix);
     }
     if (h_insts) cudaFreeHost(h_insts);
     if (h_prefix) cudaFreeHost(h_prefix);
+    for (cudaStream_t s : side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
     if (own && stream) cudaStreamDestroy(stream);
+  }
+
+  int ensure_side(size_t k) {
+    if (ev.empty()) {
+      cudaEvent_t e;
+      int rc = check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      if (rc) return rc;
+      ev.push_back(e);
+    }
+    while (side.size() < k) {
+      cudaStream_t s;
+      cudaEvent_t e;
+      int rc = check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      if (rc) return rc;
+      side.push_back(s);
+      if ((rc = check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming)))) return rc;
+      ev.push_back(e);
+    }
+    return DABS_OK;
   }
 
   int init() {
@@ -99,7 +125,16 @@ struct Batcher {
       cudaFree(g.d_insts);
       cudaFree(g.d_prefix);
     }
+    // largest group first: its CTAs are dispatched first, and the smaller
+    // groups' CTAs fill the SMs its tail leaves idle
+    std::stable_sort(ng.begin(), ng.end(), [](const Group& x, const Group& y) {
+      double wx = 0, wy = 0;
+      for (const dabs_ctx* c : x.ctxs) wx += (double)c->S * c->n * c->n;
+      for (const dabs_ctx* c : y.ctxs) wy += (double)c->S * c->n * c->n;
+      return wx > wy;
+    });
     groups.swap(ng);
+    if (groups.size() > 1 && (rc = ensure_side(groups.size() - 1))) return rc;
     int need = 1;
     for (auto& g : groups) need = std::max<int>(need, (int)g.ctxs.size());
     if (need > h_cap) {
@@ -145,14 +180,22 @@ struct Batcher {
     int rc;
     for (dabs_ctx* c : active)
       if ((rc = stage(c, 0)) || (rc = stage(c, 4))) return rc;
-    for (auto& g : groups) {
+    const size_t G = groups.size();
+    if (G > 1 && (rc = check(cudaEventRecord(ev[0], stream)))) return rc;
+    for (size_t gi = 0; gi < G; ++gi) {
+      const Group& g = groups[gi];
+      cudaStream_t st = gi == 0 ? stream : side[gi - 1];
+      if (gi > 0 && (rc = check(cudaStreamWaitEvent(st, ev[0], 0)))) return rc;
       int32_t max_n = 0;
       for (const dabs_ctx* c : g.ctxs) max_n = std::max(max_n, (int32_t)c->n);
       const MultiArgs m{g.d_insts, g.d_prefix, (int32_t)g.ctxs.size(), g.total, max_n};
       const SearchArgs first = solve_search_args(g.ctxs[0]);
-      if (!launch_search(g.var.nw, g.var.ch, &first, stream, nullptr, &m)) return DABS_E_INVALID_ARG;
+      if (!launch_search(g.var.nw, g.var.ch, &first, st, nullptr, &m)) return DABS_E_INVALID_ARG;
       if ((rc = check(cudaGetLastError()))) return rc;
+      if (gi > 0 && (rc = check(cudaEventRecord(ev[gi], st)))) return rc;
     }
+    for (size_t gi = 1; gi < G; ++gi)
+      if ((rc = check(cudaStreamWaitEvent(stream, ev[gi], 0)))) return rc;
     for (dabs_ctx* c : active)
       if ((rc = stage(c, 2)) || (rc = stage(c, 3))) return rc;
     return DABS_OK;
