@@ -572,6 +572,23 @@ def main():
                 "kernel": "k_batch_search", "algorithmic_bytes_per_launch": algo_bytes,
                 "launch_ms": launch_s * 1e3, "search_share_of_step": sum(search_ms) / sum(step_ms),
                 "l2_copy_gbs_measured": l2, "frac_of_l2_copy": achieved / l2}
+    # integer-ALU ceiling beside the memory roofline: the ALU pipe (integer
+    # compare, min, select, logic) issues 16 lanes per scheduler, 4 schedulers
+    # per SM; the ncu capture gives the ALU instructions the kernel spends per flip
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * 4 * 16 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6
+    rate = flips_rank / (sum(step_ms) * 1e-3)  # this GPU's flips/s
+    alu = {"pipe": "ALU (integer compare/min/select/logic), 64 lanes per SM",
+           "peak_lane_ops_per_s": alu_peak, "algorithmic_lane_ops_per_flip": 2 * n,
+           "frac_algorithmic": rate * 2 * n / alu_peak}
+    pv = prof["variants"].get(vkey) if prof else None
+    if pv and "alu_warp_inst_per_flip_est" in pv:
+        per_flip = pv["alu_warp_inst_per_flip_est"]
+        alu.update({"executed_warp_inst_per_flip_ncu": per_flip,
+                    "ceiling_flips_per_s": alu_peak / (32 * per_flip),
+                    "frac_of_ceiling": rate * 32 * per_flip / alu_peak,
+                    "alu_pct_of_peak_ncu": pv.get("alu_pct_of_peak_active")})
+    roofline["alu"] = alu
 
     # ---------------- end to end through the C ABI with host buffers
     Wpin = torch.empty((n, n), dtype=torch.int16, pin_memory=True).numpy()
