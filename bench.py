@@ -629,6 +629,12 @@ def main():
         cpu = {"value": rate, "unit": "flips/s", "cores": threads, "kind": "oracle",
                "sample": f"first {gens} generation(s) of the same workload ({spec['searches']} "
                          f"searches), about {args.cpu_seconds:.0f} s"}
+        # the same oracle on one thread, over a smaller solve of the same W and
+        # parameters (one generation of 64 searches: about 1/16 of the work)
+        one = dict(spec, searches=64)
+        r1, g1 = oracle_rate(Wm, one, seed, 0.0, 1)
+        cpu["single_thread"] = {"value": r1, "unit": "flips/s", "cores": 1,
+                                "sample": f"{g1} generation(s) of 64 searches, same W and parameters"}
 
     if rank == 0:
         line = {"metric": "bit flips/s", "value": value, "unit": "flips/s", "n_gpus": ws,
