@@ -72,7 +72,7 @@ bool rows_ok(const dabs_ctx* ctx, const SearchVariant& v, int mode);
 
 // Loads W (host, n x n, row-major): one DMA into the -W buffer as staging,
 // then the checks and row measurements on the device (weights.cu).  Only
-// their verdict comes back to the host; when it rejects W, -W is rebuilt
+// their outcome comes back to the host; when it rejects W, -W is rebuilt
 // from the unchanged W and the context is as before the call.
 int upload_weights(dabs_ctx* ctx, const int16_t* W) {
   const int n = ctx->n, ld = ctx->ld;

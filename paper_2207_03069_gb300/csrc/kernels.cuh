@@ -95,7 +95,7 @@ struct EDArgs {
   const DevCtrl* ctrl; // optional: skip when a solve has stopped
 };
 
-// residency of W (weights.cu): verdict of the checks on a staged W
+// residency of W (weights.cu): outcome of the checks on a staged W
 struct WCheck {
   unsigned long long bad;  // lowest i * n + j with W_ij != W_ji (all ones: none)
   unsigned long long low;  // lowest i * n + j with W_ij = -32768 (all ones: none)

@@ -2,7 +2,7 @@
 // memory as in Section V-A): the caller's rows arrive by one DMA into a
 // staging buffer, and these kernels check them (symmetry, no -32768), measure
 // them (row sums of |W|, off-diagonal non-zeros per row, their prefix sums)
-// and, once the host has read the verdict, commit W, -W and the diagonal and
+// and, once the host has read the outcome, commit W, -W and the diagonal and
 // build the sparse rows.  Loading an instance thus reads the host buffer once.
 #include "kernels.cuh"
 
