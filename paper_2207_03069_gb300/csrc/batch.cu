@@ -69,6 +69,17 @@ struct Batcher {
     if (own && stream) cudaStreamDestroy(stream);
   }
 
+  // waits for the main stream and every side stream (also after a failed
+  // generation, whose forked launches were never joined)
+  int sync_all() {
+    int rc = check(cudaStreamSynchronize(stream));
+    for (cudaStream_t s : side) {
+      const int r = check(cudaStreamSynchronize(s));
+      if (!rc) rc = r;
+    }
+    return rc;
+  }
+
   int ensure_side(size_t k) {
     if (ev.empty()) {
       cudaEvent_t e;
@@ -96,7 +107,7 @@ struct Batcher {
 
   // rebuild the groups for `active` (contexts must use `stream`)
   int rebuild() {
-    int rc = check(cudaStreamSynchronize(stream));
+    int rc = sync_all();
     if (rc) return rc;
     std::vector<Group> ng;
     for (dabs_ctx* c : active) {
@@ -234,7 +245,7 @@ extern "C" int dabs_batch_solve(dabs_ctx* const* ctxs, int32_t k, const uint64_t
     ctxs[i]->stream = b.stream;
   }
   auto restore = [&]() {
-    cudaStreamSynchronize(b.stream);
+    b.sync_all();
     for (int i = 0; i < k; ++i) ctxs[i]->stream = saved[i];
   };
   for (int i = 0; i < k && !rc; ++i)
@@ -336,7 +347,7 @@ extern "C" int dabs_server_create(size_t hbm_budget_bytes, dabs_server** out) {
 
 extern "C" void dabs_server_destroy(dabs_server* s) {
   if (!s) return;
-  cudaStreamSynchronize(s->batch.stream);
+  s->batch.sync_all();
   for (auto& kv : s->all)
     if (kv.second->ctx) dabs_destroy(kv.second->ctx);
   delete s;
