@@ -102,7 +102,10 @@ const char* dabs_last_error(const dabs_ctx* ctx);
 int dabs_set_stream(dabs_ctx* ctx, void* stream);
 
 /* Replaces the weights with another symmetric n x n matrix of the same n
- * (host buffer), keeping the solver state allocations. */
+ * (host buffer, read once by one copy), keeping the solver state
+ * allocations.  The checks run on the device before anything is replaced:
+ * NOT_SYMMETRIC (the message names the lowest i * n + j with W_ij != W_ji)
+ * or INVALID_ARG (an entry -32768), and on error the context is unchanged. */
 int dabs_load_weights(dabs_ctx* ctx, const int16_t* W);
 
 /* Eq. (2): energy of one host vector X (n bytes, each 0 or 1). */
@@ -152,7 +155,11 @@ int dabs_solve(dabs_ctx* ctx, uint64_t budget, uint64_t seed, int64_t target, ui
  * Solves the k contexts together (Sections III and IV per instance): every
  * generation runs each instance's offspring, recompute, merge and finalise
  * kernels and one batch-search launch per kernel variant covering all the
- * instances of that variant, on one stream.  Each instance stops on its own
+ * instances of that variant; the variants' launches run concurrently, the
+ * one with the most work first.  An instance uses the variant chosen for it
+ * by dabs_set_variant or dabs_autotune; otherwise the default for many
+ * instances in flight (8 warps x 2 chunks for 2048 < n <= 4096, where a
+ * context alone uses 4 x 4).  Each instance stops on its own
  * budget/target/generation limit; instance i's results (best_X[i], n_i host
  * bytes; best_E[i]; flips[i]) equal dabs_solve(ctxs[i], budgets[i], seeds[i],
  * targets[i]) alone.  targets, best_X, best_E, flips may be NULL.
