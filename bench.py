@@ -462,8 +462,10 @@ def run_reference(args, ws, rank, pg):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": spec["desc"], "searches": spec["searches"],
+            "config": {"workload": spec["desc"], "n": spec["n"], "searches": spec["searches"],
                        "pools": spec["pools"], "pool_cap": spec["pool_cap"],
+                       "tabu": spec["tabu"], "s": "%d/%d" % spec["s"], "b": "%d/%d" % spec["b"],
+                       "seeding": "straight" if spec["seed_mode"] == 0 else "recompute",
                        "parallelism": "host threads"},
             "cpu_baseline": {"value": v, "unit": "flips/s", "cores": threads, "kind": "oracle",
                              "sample": f"{args.steps} whole generations after {args.warmup} "
