@@ -102,3 +102,30 @@ int main(void) {
                         str(src), "-L", lib, "-ldabs", "-Wl,-rpath," + lib, "-o", str(out)],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def header_constants():
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "dabs.h")).read(), flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"#define (DABS_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src)}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", src):
+        for k, v in re.findall(r"(DABS_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            consts[k] = int(v)
+    fields = re.search(r"typedef struct dabs_params \{(.*?)\} dabs_params;", src, re.S).group(1)
+    names = [n for decl in re.findall(r"int32_t\s+([^;]+);", fields)
+             for n in (x.strip() for x in decl.split(","))]
+    return consts, names
+
+
+def test_binding_constants_and_params_match_the_header():
+    """The ctypes binding mirrors the header: error codes, row formats, the
+    autotuner's table size, and dabs_params field by field (all int32_t)."""
+    from paper_2207_03069_gb300 import dabs
+    consts, names = header_constants()
+    for k in ("OK", "E_INVALID_ARG", "E_NOT_SYMMETRIC", "E_TOO_LARGE", "E_OOM", "E_TIMEOUT",
+              "E_CUDA", "E_BUSY", "E_NO_DEVICE", "ROWS_DENSE", "ROWS_SPARSE_SMEM",
+              "ROWS_SPARSE_GLOBAL", "ROWS_DENSE_SMEM"):
+        assert getattr(dabs, k) == consts["DABS_" + k], k
+    assert len(dabs.Context.VARIANTS) * len(dabs.ROW_SUFFIX) == consts["DABS_N_VARIANTS"]
+    assert [f for f, _ in dabs.Params._fields_] == names
+    assert all(t is C.c_int32 for _, t in dabs.Params._fields_)
+    assert C.sizeof(dabs.Params) == 4 * len(names)
