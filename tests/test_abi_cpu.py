@@ -129,3 +129,18 @@ def test_binding_constants_and_params_match_the_header():
     assert [f for f, _ in dabs.Params._fields_] == names
     assert all(t is C.c_int32 for _, t in dabs.Params._fields_)
     assert C.sizeof(dabs.Params) == 4 * len(names)
+
+
+def test_binding_argument_counts_match_the_header():
+    """Every call the binding declares takes as many arguments as its
+    prototype in include/dabs.h (ctypes would not notice a mismatch)."""
+    from paper_2207_03069_gb300 import dabs
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "dabs.h")).read(), flags=re.S)
+    protos = {}
+    for name, args in re.findall(r"\b(dabs_[a-z_]+)\s*\(([^()]*)\)\s*;", src):
+        a = " ".join(args.split())
+        protos[name] = 0 if a in ("", "void") else a.count(",") + 1
+    assert len(protos) >= 20
+    for name, (_, argtypes) in dabs.EXPORTS.items():
+        assert name in protos, name
+        assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
