@@ -30,11 +30,13 @@
  *      CyclicMin run and each next one starts where the last one ended
  *      (cyclically); argmin over non-tabu bits of the window, ties to the
  *      first bit in cyclic order from the window start.
- *  R8  RandomMin: threshold thr = clamp(cube21(t,T) >> 24, ceil(2^13 / n),
- *      256), i.e. p(t) in units of 1/256 with the floor ceil(8192/n)/256 >=
- *      32/n; bit k is a candidate iff its 8-bit uniform < thr; argmin of
- *      Delta over non-tabu candidates (lowest index on ties); if there is no
- *      candidate, argmin over all non-tabu bits.
+ *  R8  RandomMin: p(t) = max((t/T)^3, c) with c = 32/n is held in units of
+ *      2^-16: thr = clamp(cube21(t,T) >> 16, ceil(2^21 / n), 65536), so the
+ *      floor ceil(32 * 2^16 / n) / 2^16 is c rounded up to the next 2^-16 for
+ *      every n (exactly c when n divides 2^21) and p = 1 when n <= 32; bit k
+ *      is a candidate iff its 16-bit uniform < thr; argmin of Delta over
+ *      non-tabu candidates (lowest index on ties); if there is no candidate,
+ *      argmin over all non-tabu bits.
  *  R9  PositiveMin: posmin = min Delta > 0 over non-tabu bits; candidates are
  *      non-tabu bits with Delta <= posmin (all non-tabu bits if no positive
  *      Delta exists); the pick is the ((u0 * count) >> 32)-th candidate.
@@ -82,7 +84,7 @@
  *      (x, y, z, w):
  *        MaxMin      (flip, g, s, 1<<24)         u0 threshold, u1 pick
  *        PositiveMin (flip, g, s, 2<<24)         u0 pick
- *        RandomMin   (flip, g, s, 3<<24 | k/16)  byte (k%16) of the block
+ *        RandomMin   (flip, g, s, 3<<24 | k/8)   16-bit half (k%8) of the block
  *        choice      (0, g, s, 4<<24)            u0..u3 of R15
  *        parents     (0, g, s, 5<<24)            u0 rank A, u1 rank B, u2/u3 R17
  *        bits        (word, g, s, 6<<24)         R16
@@ -181,6 +183,39 @@ uint64_t orc_cube21(uint64_t a, uint64_t T) {
     return (f * f * f) >> 31;
 }
 
+/* R8: RandomMin's candidate probability p(t) = max((t/T)^3, 32/n) in units of
+ * 2^-16 (Section III-A, RandomMin).                                         */
+uint32_t orc_randmin_threshold(uint64_t t, uint64_t T, int32_t n) {
+    uint64_t thr = orc_cube21(t, T) >> 16;
+    uint64_t floor_c = ((1ull << 21) + (uint64_t)n - 1) / (uint64_t)n; /* ceil(32 * 2^16 / n) */
+    if (thr < floor_c) thr = floor_c;
+    if (thr > 65536) thr = 65536;
+    return (uint32_t)thr;
+}
+
+/* R8/R21: the 16-bit uniform of every bit k < n for the RandomMin iteration
+ * made as flip `flip` of search s in generation g.                          */
+void orc_randmin_draws(uint64_t seed, uint32_t flip, uint32_t g, uint32_t s, int32_t n,
+                       uint16_t* u16) {
+    uint32_t u[4];
+    for (int32_t k = 0; k < n; ++k) {
+        if ((k & 7) == 0) draw(seed, flip, g, s, (3u << 24) | (uint32_t)(k >> 3), u);
+        u16[k] = (uint16_t)(u[(k & 7) >> 1] >> (16 * (k & 1)));
+    }
+}
+
+/* R6: MaxMin's threshold d, drawn uniformly from [mn, D(t)] with
+ * D(t) = mn + ((T-t)/T)^3 (mx - mn) (Section III-A, MaxMin); *R_out gets
+ * the width floor(((T-t)/T)^3 (mx - mn)) of the interval.                   */
+int64_t orc_maxmin_threshold(int32_t mn, int32_t mx, uint64_t t, uint64_t T, uint32_t u0,
+                             uint64_t* R_out) {
+    uint64_t q = orc_cube21(T - t, T);
+    uint64_t span = (uint64_t)((int64_t)mx - (int64_t)mn);
+    uint64_t R = (q * span) >> 32;
+    if (R_out) *R_out = R;
+    return (int64_t)mn + (int64_t)(((uint64_t)u0 * (R + 1)) >> 32);
+}
+
 /* Section III-B: another (main search, Greedy) round is run while fewer than
  * B = b*n flips were made; TwoNeighbor runs at most once (R10, R12).        */
 int orc_batch_continue(uint64_t total, uint64_t B, int32_t main_runs, int32_t algo) {
@@ -210,6 +245,7 @@ typedef struct {
     int32_t bad;
     int32_t* last; /* tabu: iteration of the last flip in the current main run */
     int32_t* scratch;
+    orc_sel_trace* sel; /* optional per-flip record of the selectors' quantities */
 } search_run;
 
 /* Step 1: examine every one-bit neighbour, keep the best in BEST (R2).
@@ -278,6 +314,14 @@ static void straight(search_run* b, const uint8_t* D) {
     }
 }
 
+/* selector record of the iteration about to flip (test instrumentation) */
+static void sel_record(search_run* b, int64_t a, int64_t r, uint32_t count) {
+    if (!b->sel || (int64_t)b->flips >= b->sel->cap) return;
+    b->sel->a[b->flips] = a;
+    b->sel->r[b->flips] = r;
+    b->sel->count[b->flips] = (int32_t)count;
+}
+
 static int is_tabu(const search_run* b, int32_t k, int32_t t, int32_t tau) {
     return b->last[k] > 0 && t - b->last[k] <= tau;
 }
@@ -306,10 +350,15 @@ static void main_search(search_run* b, int32_t algo, int32_t T, int32_t tau) {
     }
     for (int32_t k = 0; k < n; ++k) b->last[k] = 0;
     uint8_t* cand = (uint8_t*)malloc((size_t)n);
+    uint16_t* u16 = (uint16_t*)malloc(sizeof(uint16_t) * (size_t)n);
     int32_t win_start = 0;
     const int32_t c_win = n < 32 ? n : 32;
-    const uint32_t c8 = (uint32_t)(((1u << 13) + (uint32_t)n - 1) / (uint32_t)n);
     for (int32_t t = 1; t <= T; ++t) {
+        if (b->sel && (int64_t)b->flips < b->sel->cap) {
+            int32_t nf = 0;
+            for (int32_t k = 0; k < n; ++k) nf += !is_tabu(b, k, t, tau);
+            b->sel->free[b->flips] = nf;
+        }
         step1(b, &j);
         int32_t i = -1;
         uint32_t u[4];
@@ -321,17 +370,16 @@ static void main_search(search_run* b, int32_t algo, int32_t T, int32_t tau) {
                 if (!any || b->delta[k] > mx) mx = b->delta[k];
                 any = 1;
             }
-            uint64_t q = orc_cube21((uint64_t)(T - t), (uint64_t)T);
-            uint64_t span = (uint64_t)((int64_t)mx - (int64_t)mn);
-            uint64_t R = (q * span) >> 32;
             draw(b->seed, (uint32_t)b->flips, b->g, b->s, 1u << 24, u);
-            int64_t d = (int64_t)mn + (int64_t)(((uint64_t)u[0] * (R + 1)) >> 32);
+            uint64_t R;
+            int64_t d = orc_maxmin_threshold(mn, mx, (uint64_t)t, (uint64_t)T, u[0], &R);
             uint32_t count = 0;
             for (int32_t k = 0; k < n; ++k) {
                 cand[k] = !is_tabu(b, k, t, tau) && (int64_t)b->delta[k] <= d;
                 count += cand[k];
             }
             i = kth_candidate(cand, n, uidx(u[1], count));
+            sel_record(b, d, (int64_t)R, count);
         } else if (algo == ORC_CYCLICMIN) {
             uint64_t w = (orc_cube21((uint64_t)t, (uint64_t)T) * (uint64_t)n) >> 32;
             if (w < (uint64_t)c_win) w = (uint64_t)c_win;
@@ -342,19 +390,20 @@ static void main_search(search_run* b, int32_t algo, int32_t T, int32_t tau) {
                 if (i < 0 || b->delta[k] < b->delta[i]) i = k;
             }
             win_start = (int32_t)((win_start + (int64_t)w) % n);
+            sel_record(b, (int64_t)w, 0, 0);
         } else if (algo == ORC_RANDOMMIN) {
-            uint64_t thr = orc_cube21((uint64_t)t, (uint64_t)T) >> 24;
-            if (thr < c8) thr = c8;
-            if (thr > 256) thr = 256;
+            uint32_t thr = orc_randmin_threshold((uint64_t)t, (uint64_t)T, n);
+            orc_randmin_draws(b->seed, (uint32_t)b->flips, b->g, b->s, n, u16);
+            uint32_t count = 0;
             for (int32_t k = 0; k < n; ++k) {
-                if (is_tabu(b, k, t, tau)) continue;
-                draw(b->seed, (uint32_t)b->flips, b->g, b->s, (3u << 24) | (uint32_t)(k >> 4), u);
-                uint32_t u8 = (u[(k & 15) >> 2] >> (8 * (k & 3))) & 0xFFu;
-                if (u8 < thr && (i < 0 || b->delta[k] < b->delta[i])) i = k;
+                if (is_tabu(b, k, t, tau) || u16[k] >= thr) continue;
+                ++count;
+                if (i < 0 || b->delta[k] < b->delta[i]) i = k;
             }
             if (i < 0)
                 for (int32_t k = 0; k < n; ++k)
                     if (!is_tabu(b, k, t, tau) && (i < 0 || b->delta[k] < b->delta[i])) i = k;
+            sel_record(b, thr, 0, count);
         } else { /* ORC_POSITIVEMIN */
             int32_t pm = 0, anypos = 0;
             for (int32_t k = 0; k < n; ++k)
@@ -369,11 +418,13 @@ static void main_search(search_run* b, int32_t algo, int32_t T, int32_t tau) {
             }
             draw(b->seed, (uint32_t)b->flips, b->g, b->s, 2u << 24, u);
             i = kth_candidate(cand, n, uidx(u[0], count));
+            sel_record(b, anypos ? pm : INT64_MAX, 0, count);
         }
         flip(b, i);
         b->last[i] = t;
     }
     free(cand);
+    free(u16);
 }
 
 static uint64_t main_flips(const orc_params* p, int32_t n) {
@@ -388,8 +439,18 @@ int orc_batch_search(const int16_t* W, int32_t n, const orc_params* p, uint64_t 
                      uint32_t s, uint8_t* X, int32_t* delta, int64_t* E, const uint8_t* D,
                      int32_t algo, uint8_t* best_X, int64_t* best_E, uint64_t* flips,
                      int32_t* trace_idx, int32_t* trace_phase, int64_t trace_cap, int32_t check) {
+    return orc_batch_search_sel(W, n, p, seed, g, s, X, delta, E, D, algo, best_X, best_E, flips,
+                                trace_idx, trace_phase, trace_cap, check, NULL);
+}
+
+int orc_batch_search_sel(const int16_t* W, int32_t n, const orc_params* p, uint64_t seed,
+                         uint32_t g, uint32_t s, uint8_t* X, int32_t* delta, int64_t* E,
+                         const uint8_t* D, int32_t algo, uint8_t* best_X, int64_t* best_E,
+                         uint64_t* flips, int32_t* trace_idx, int32_t* trace_phase,
+                         int64_t trace_cap, int32_t check, orc_sel_trace* sel) {
     search_run b;
     memset(&b, 0, sizeof b);
+    b.sel = sel;
     b.W = W; b.n = n; b.seed = seed; b.g = g; b.s = s;
     b.X = X; b.delta = delta; b.E = E; b.best_X = best_X; b.best_E = INT64_MAX;
     b.trace_idx = trace_idx; b.trace_phase = trace_phase; b.trace_cap = trace_cap;

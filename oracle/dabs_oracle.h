@@ -53,6 +53,15 @@ void     orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4
 uint32_t orc_parent_rank(uint32_t u, uint32_t m);          /* Section IV-A */
 uint64_t orc_cube21(uint64_t a, uint64_t T);               /* (a/T)^3 in 2^-32 units */
 int      orc_batch_continue(uint64_t total, uint64_t B, int32_t main_runs, int32_t algo);
+/* Section III-A RandomMin: p(t) in units of 2^-16 (reading R8) and the per-bit
+ * 16-bit uniforms of the iteration made as flip `flip` of search s, gen g */
+uint32_t orc_randmin_threshold(uint64_t t, uint64_t T, int32_t n);
+void     orc_randmin_draws(uint64_t seed, uint32_t flip, uint32_t g, uint32_t s, int32_t n,
+                           uint16_t* u16);
+/* Section III-A MaxMin: threshold d in [mn, D(t)] (reading R6); *R_out (may be
+ * NULL) receives the interval width floor(((T-t)/T)^3 (mx - mn)) */
+int64_t  orc_maxmin_threshold(int32_t mn, int32_t mx, uint64_t t, uint64_t T, uint32_t u0,
+                              uint64_t* R_out);
 
 /* ---- one batch search (Section III-B) on persistent state X, delta, E ----
  * trace_idx/trace_phase (optional, may be NULL) receive one entry per flip,
@@ -63,6 +72,27 @@ int orc_batch_search(const int16_t* W, int32_t n, const orc_params* p, uint64_t 
                      const uint8_t* D, int32_t algo, uint8_t* best_X, int64_t* best_E,
                      uint64_t* flips, int32_t* trace_idx, int32_t* trace_phase,
                      int64_t trace_cap, int32_t check);
+
+/* Per-flip record of the main searches' selectors, indexed by flip number
+ * (entries of other phases are left untouched), up to cap entries:
+ *   a     MaxMin threshold d; RandomMin threshold (units of 2^-16);
+ *         PositiveMin posmin (INT64_MAX if no positive Delta); CyclicMin width
+ *   r     MaxMin interval width R (0 otherwise)
+ *   count candidates: MaxMin and PositiveMin (non-tabu, Delta <= bound),
+ *         RandomMin (non-tabu bits whose uniform is below the threshold)
+ *   free  non-tabu bits at that iteration                                   */
+typedef struct {
+    int64_t* a;
+    int64_t* r;
+    int32_t* count;
+    int32_t* free;
+    int64_t cap;
+} orc_sel_trace;
+int orc_batch_search_sel(const int16_t* W, int32_t n, const orc_params* p, uint64_t seed,
+                         uint32_t g, uint32_t s, uint8_t* X, int32_t* delta, int64_t* E,
+                         const uint8_t* D, int32_t algo, uint8_t* best_X, int64_t* best_E,
+                         uint64_t* flips, int32_t* trace_idx, int32_t* trace_phase,
+                         int64_t trace_cap, int32_t check, orc_sel_trace* sel);
 
 /* ---- solver object: pools + per-search state, one generation at a time ---- */
 typedef struct orc_solver orc_solver;

@@ -34,6 +34,12 @@ class Params(C.Structure):
         "seed_mode", "max_generations", "restart", "restart_dist", "abs_mode")]
 
 
+class SelTrace(C.Structure):
+    _fields_ = [("a", C.POINTER(C.c_int64)), ("r", C.POINTER(C.c_int64)),
+                ("count", C.POINTER(C.c_int32)), ("free", C.POINTER(C.c_int32)),
+                ("cap", C.c_int64)]
+
+
 def make_params(searches=32, pools=4, pool_cap=64, tabu=8, s=(1, 10), b=(1, 1),
                 seed_mode=0, max_generations=0, restart=0, restart_dist=0,
                 abs_mode=0) -> Params:
@@ -72,6 +78,18 @@ def lib():
         L.orc_cube21.argtypes = [C.c_uint64, C.c_uint64]
         L.orc_batch_continue.restype = C.c_int
         L.orc_batch_continue.argtypes = [C.c_uint64, C.c_uint64, C.c_int32, C.c_int32]
+        L.orc_randmin_threshold.restype = C.c_uint32
+        L.orc_randmin_threshold.argtypes = [C.c_uint64, C.c_uint64, C.c_int32]
+        L.orc_randmin_draws.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                        C.c_int32, P(C.c_uint16)]
+        L.orc_maxmin_threshold.restype = C.c_int64
+        L.orc_maxmin_threshold.argtypes = [C.c_int32, C.c_int32, C.c_uint64, C.c_uint64,
+                                           C.c_uint32, u64p]
+        L.orc_batch_search_sel.restype = C.c_int
+        L.orc_batch_search_sel.argtypes = [i16p, C.c_int32, P(Params), C.c_uint64, C.c_uint32,
+                                           C.c_uint32, u8p, i32p, i64p, u8p, C.c_int32, u8p,
+                                           i64p, u64p, i32p, i32p, C.c_int64, C.c_int32,
+                                           P(SelTrace)]
         L.orc_batch_search.restype = C.c_int
         L.orc_batch_search.argtypes = [i16p, C.c_int32, P(Params), C.c_uint64, C.c_uint32,
                                        C.c_uint32, u8p, i32p, i64p, u8p, C.c_int32, u8p, i64p,
@@ -142,9 +160,29 @@ def batch_continue(total, B, main_runs, algo) -> bool:
     return bool(lib().orc_batch_continue(total, B, main_runs, algo))
 
 
+def randmin_threshold(t: int, T: int, n: int) -> int:
+    """RandomMin's p(t) in units of 2^-16."""
+    return int(lib().orc_randmin_threshold(t, T, n))
+
+
+def randmin_draws(seed: int, flip: int, g: int, s: int, n: int) -> np.ndarray:
+    """The 16-bit uniform of every bit for one RandomMin iteration."""
+    out = np.zeros(max(n, 1), np.uint16)
+    lib().orc_randmin_draws(seed, flip, g, s, n, _p(out, C.c_uint16))
+    return out[:n]
+
+
+def maxmin_threshold(mn: int, mx: int, t: int, T: int, u0: int):
+    """MaxMin's threshold d and the interval width R."""
+    R = C.c_uint64(0)
+    d = lib().orc_maxmin_threshold(mn, mx, t, T, u0, C.byref(R))
+    return int(d), int(R.value)
+
+
 def batch_search(W, params: Params, seed: int, g: int, s: int, X, dlt, E: int, D, algo: int,
-                 trace_cap: int = 0, check: bool = False):
-    """One batch search.  Returns dict(X, delta, E, best_X, best_E, flips, trace, phases, ok)."""
+                 trace_cap: int = 0, check: bool = False, sel: bool = False):
+    """One batch search.  Returns dict(X, delta, E, best_X, best_E, flips, trace, phases, ok),
+    plus sel_a, sel_r, sel_count, sel_free (per flip, see orc_sel_trace) when sel is set."""
     W = _W(W)
     n = W.shape[0]
     X = np.array(X, dtype=np.uint8, copy=True)
@@ -156,15 +194,24 @@ def batch_search(W, params: Params, seed: int, g: int, s: int, X, dlt, E: int, D
     fl = C.c_uint64(0)
     tr = np.zeros(max(trace_cap, 1), np.int32)
     ph = np.zeros(max(trace_cap, 1), np.int32)
-    rc = lib().orc_batch_search(_p(W, C.c_int16), n, C.byref(params), seed, g, s,
-                                _p(X, C.c_uint8), _p(dlt, C.c_int32), C.byref(Ec),
-                                _p(D, C.c_uint8), algo, _p(bX, C.c_uint8), C.byref(bE),
-                                C.byref(fl), _p(tr, C.c_int32) if trace_cap else None,
-                                _p(ph, C.c_int32) if trace_cap else None, trace_cap,
-                                1 if check else 0)
+    cap = max(trace_cap, 1)
+    sa, sr = np.zeros(cap, np.int64), np.zeros(cap, np.int64)
+    sc, sf = np.full(cap, -1, np.int32), np.full(cap, -1, np.int32)
+    st = SelTrace(_p(sa, C.c_int64), _p(sr, C.c_int64), _p(sc, C.c_int32), _p(sf, C.c_int32),
+                  trace_cap if sel else 0)
+    rc = lib().orc_batch_search_sel(_p(W, C.c_int16), n, C.byref(params), seed, g, s,
+                                    _p(X, C.c_uint8), _p(dlt, C.c_int32), C.byref(Ec),
+                                    _p(D, C.c_uint8), algo, _p(bX, C.c_uint8), C.byref(bE),
+                                    C.byref(fl), _p(tr, C.c_int32) if trace_cap else None,
+                                    _p(ph, C.c_int32) if trace_cap else None, trace_cap,
+                                    1 if check else 0, C.byref(st) if sel else None)
     f = int(fl.value)
-    return dict(X=X, delta=dlt, E=int(Ec.value), best_X=bX, best_E=int(bE.value), flips=f,
-                trace=tr[:min(f, trace_cap)], phases=ph[:min(f, trace_cap)], ok=(rc == 0))
+    m = min(f, trace_cap)
+    out = dict(X=X, delta=dlt, E=int(Ec.value), best_X=bX, best_E=int(bE.value), flips=f,
+               trace=tr[:m], phases=ph[:m], ok=(rc == 0))
+    if sel:
+        out.update(sel_a=sa[:m], sel_r=sr[:m], sel_count=sc[:m], sel_free=sf[:m])
+    return out
 
 
 class Solver:
