@@ -297,26 +297,18 @@ struct Searcher {
     ++flips;
   }
 
-  // RandomMin draws of one iteration: byte (k % 16) of the Philox block
-  // (flip, g, s, RNG_RANDMIN | k/16) for each owned bit k.  A block covers the
-  // 8-bit runs of two neighbouring lanes; lane pairs split two chunks' blocks
-  // and swap halves, so a lane computes one block per two chunks.
-  __device__ __forceinline__ void randmin_draw(uint32_t flip_idx, uint2 (&r)[CH]) const {
-    const bool odd = t & 1;
+  // RandomMin draws of one iteration: 16-bit half (k % 8) of the Philox block
+  // (flip, g, s, RNG_RANDMIN | k/8) for each owned bit k.  A thread's eight
+  // bits of chunk c are k/8 = c NT + t: one whole block per chunk.
+  __device__ __forceinline__ void randmin_draw(uint32_t flip_idx, uint4 (&r)[CH]) const {
 #pragma unroll
-    for (int c = 0; c + 1 < CH; c += 2) {
-      const int cc = odd ? c + 1 : c;
-      const uint4 u = draw(seed, flip_idx, g, s, RNG_RANDMIN | (uint32_t)(cc * (NT / 2) + (t >> 1)));
-      const uint32_t s0 = odd ? u.x : u.z, s1 = odd ? u.y : u.w;
-      const uint32_t g0 = __shfl_xor_sync(FULL, s0, 1), g1 = __shfl_xor_sync(FULL, s1, 1);
-      r[c] = odd ? make_uint2(g0, g1) : make_uint2(u.x, u.y);
-      r[c + 1 < CH ? c + 1 : c] = odd ? make_uint2(u.z, u.w) : make_uint2(g0, g1);
-    }
-    if constexpr (CH & 1) {
-      const int c = CH - 1;
-      const uint4 u = draw(seed, flip_idx, g, s, RNG_RANDMIN | (uint32_t)(c * (NT / 2) + (t >> 1)));
-      r[c] = odd ? make_uint2(u.z, u.w) : make_uint2(u.x, u.y);
-    }
+    for (int c = 0; c < CH; ++c)
+      r[c] = draw(seed, flip_idx, g, s, RNG_RANDMIN | (uint32_t)(c * NT + t));
+  }
+  // bit p's 16-bit uniform is below thr
+  __device__ __forceinline__ static bool randmin_hit(const uint4 (&r)[CH], int p, uint32_t thr) {
+    const int c = p >> 3, e = p & 7;
+    return ((u32of(r[c], e >> 1) >> (16 * (e & 1))) & 0xFFFFu) < thr;
   }
 
   // ------------------------------------------------------------ k-th pick
@@ -536,10 +528,11 @@ struct Searcher {
     uint32_t fup = 0, rup = 0, fdn = 1u << 21;
     int rdn = 0;
     uint32_t rnd0 = 0, rnd1 = 0;  // 32 MaxMin/PositiveMin draws, one per lane
-    uint2 rr[CH];                 // RandomMin draws of the current iteration
+    uint4 rr[CH];                 // RandomMin draws of the current iteration
     bool rr_ready = false;
     const int cwin = n < 32 ? n : 32;
-    const uint32_t c8 = ((1u << 13) + (uint32_t)n - 1) / (uint32_t)n;
+    // RandomMin's floor c = 32/n in units of 2^-16, rounded up
+    const uint32_t c16 = ((1u << 21) + (uint32_t)n - 1) / (uint32_t)n;
     for (;;) {
       int i = 0, xi = 0, di = 0;
       uint32_t kj = UINT_MAX;
@@ -718,14 +711,11 @@ struct Searcher {
           ws += wsz;
           if (ws >= n) ws -= n;
         } else {  // RANDOMMIN
-          uint32_t thr = (uint32_t)(cube_of(fup) >> 24);
-          thr = thr < c8 ? c8 : (thr > 256u ? 256u : thr);
+          uint32_t thr = (uint32_t)(cube_of(fup) >> 16);
+          thr = thr < c16 ? c16 : (thr > 65536u ? 65536u : thr);
           if (!rr_ready) randmin_draw(flips, rr);
           rr_ready = false;
-          const uint32_t Cm = mask_of([&](int p) {
-            const int c = p >> 3, e = p & 7;
-            return (((e < 4 ? rr[c].x : rr[c].y) >> (8 * (e & 3))) & 0xFFu) < thr;
-          }) & F;
+          const uint32_t Cm = mask_of([&](int p) { return randmin_hit(rr, p, thr); }) & F;
           int cmc[CH];
           chunk_min(Cm, cmc);
           int v[2] = {min_of(cma), min_of(cmc)};
@@ -803,10 +793,11 @@ struct Searcher {
     uint32_t fup = 0, rup = 0, fdn = 1u << 21;
     int rdn = 0;
     uint32_t rnd0 = 0, rnd1 = 0;  // 32 MaxMin/PositiveMin draws, one per lane
-    uint2 rr[CH];                 // RandomMin draws of the current iteration
+    uint4 rr[CH];                 // RandomMin draws of the current iteration
     bool rr_ready = false;
     const int cwin = n < 32 ? n : 32;
-    const uint32_t c8 = ((1u << 13) + (uint32_t)n - 1) / (uint32_t)n;
+    // RandomMin's floor c = 32/n in units of 2^-16, rounded up
+    const uint32_t c16 = ((1u << 21) + (uint32_t)n - 1) / (uint32_t)n;
     const int low = (1 << kb) - 1;  // (k << 1 | x_k) part of a key
     const int unit = 1 << kb;       // Delta = 1 in key units
     for (;;) {
@@ -945,14 +936,11 @@ struct Searcher {
           ws += wsz;
           if (ws >= n) ws -= n;
         } else {  // RANDOMMIN
-          uint32_t thr = (uint32_t)(cube_of(fup) >> 24);
-          thr = thr < c8 ? c8 : (thr > 256u ? 256u : thr);
+          uint32_t thr = (uint32_t)(cube_of(fup) >> 16);
+          thr = thr < c16 ? c16 : (thr > 65536u ? 65536u : thr);
           if (!rr_ready) randmin_draw(flips, rr);
           rr_ready = false;
-          const uint32_t Cm = mask_of([&](int p) {
-            const int c = p >> 3, e = p & 7;
-            return (((e < 4 ? rr[c].x : rr[c].y) >> (8 * (e & 3))) & 0xFFu) < thr;
-          }) & F;
+          const uint32_t Cm = mask_of([&](int p) { return randmin_hit(rr, p, thr); }) & F;
           int cmc[CH];
           chunk_min(Cm, cmc);
           int v[2] = {min_of(cma), min_of(cmc)};

@@ -174,22 +174,22 @@ struct SmemSearch {
       }
     }
   }
-  // RandomMin: also the minimum over the candidates (one byte of draw per
-  // bit below the threshold)
+  // RandomMin: also the minimum over the candidates (bit k's 16-bit uniform,
+  // half k % 8 of block k / 8, below the threshold)
   __device__ void scan_random(uint32_t thr, int& fv, int& fk, int& cv, int& ck) const {
     int mv = INT_MAX, mq = 0, mc = INT_MAX, kc = INT_MAX;
-    for (int b = 0; b < L / 16; ++b) {
-      const uint4 u = draw(seed, flips, g, s, RNG_RANDMIN | (uint32_t)((base >> 4) + b));
+    for (int b = 0; b < L / 8; ++b) {
+      const uint4 u = draw(seed, flips, g, s, RNG_RANDMIN | (uint32_t)((base >> 3) + b));
 #pragma unroll
-      for (int qq = 0; qq < 4; ++qq) {
-        const int q = 4 * b + qq;
+      for (int qq = 0; qq < 2; ++qq) {
+        const int q = 2 * b + qq;
         const int4 v = ld4(q);
         track(min4(v), q, mv, mq);
-        const uint32_t word = qq == 0 ? u.x : qq == 1 ? u.y : qq == 2 ? u.z : u.w;
-        const int a0 = (word & 0xFFu) < thr ? v.x : INT_MAX;
-        const int a1 = ((word >> 8) & 0xFFu) < thr ? v.y : INT_MAX;
-        const int a2 = ((word >> 16) & 0xFFu) < thr ? v.z : INT_MAX;
-        const int a3 = (word >> 24) < thr ? v.w : INT_MAX;
+        const uint32_t w0 = qq == 0 ? u.x : u.z, w1 = qq == 0 ? u.y : u.w;
+        const int a0 = (w0 & 0xFFFFu) < thr ? v.x : INT_MAX;
+        const int a1 = (w0 >> 16) < thr ? v.y : INT_MAX;
+        const int a2 = (w1 & 0xFFFFu) < thr ? v.z : INT_MAX;
+        const int a3 = (w1 >> 16) < thr ? v.w : INT_MAX;
         const int gm = min(__vimin3_s32(a0, a1, a2), a3);
         if (gm < mc) {
           mc = gm;
@@ -367,7 +367,8 @@ struct SmemSearch {
     int rdn = 0;
     uint32_t rnd0 = 0, rnd1 = 0;
     const int cwin = n < 32 ? n : 32;
-    const uint32_t c8 = ((1u << 13) + (uint32_t)n - 1) / (uint32_t)n;
+    // RandomMin's floor c = 32/n in units of 2^-16, rounded up
+    const uint32_t c16 = ((1u << 21) + (uint32_t)n - 1) / (uint32_t)n;
     for (;;) {
       int i, di, m, j;
       if (phase != P_MAIN) {
@@ -461,8 +462,8 @@ struct SmemSearch {
           ws += wsz;
           if (ws >= n) ws -= n;
         } else {  // RANDOMMIN
-          uint32_t thr = (uint32_t)(cube21f(fup) >> 24);
-          thr = thr < c8 ? c8 : (thr > 256u ? 256u : thr);
+          uint32_t thr = (uint32_t)(cube21f(fup) >> 16);
+          thr = thr < c16 ? c16 : (thr > 65536u ? 65536u : thr);
           int cv, ck;
           scan_random(thr, fv, fk, cv, ck);
           wmin(cv, ck);
