@@ -168,6 +168,33 @@ int dabs_batch_solve(dabs_ctx* const* ctxs, int32_t k, const uint64_t* budgets,
                      const uint64_t* seeds, const int64_t* targets, uint8_t* const* best_X,
                      int64_t* best_E, uint64_t* flips);
 
+/* The same batched form one step at a time (dabs_batch_solve is built on
+ * it).  dabs_batch_create takes k distinct contexts (k >= 1) and a
+ * cudaStream_t (NULL: the batch makes its own); while the batch lives every
+ * context's work is enqueued on that stream (their own streams are restored
+ * by dabs_batch_destroy), and each context's inspection calls
+ * (dabs_solve_status, dabs_solve_best, dabs_read_pools, ...) stay valid.
+ * dabs_batch_begin starts every instance's solve as dabs_solve_begin(ctxs[i],
+ * seeds[i], budgets[i], targets[i]) would (targets may be NULL: none).
+ * dabs_batch_generations runs `count` generations of every instance still
+ * running, then waits for the stream and retires the instances whose solve
+ * has stopped; *running (may be NULL) receives how many remain.  After g
+ * generations instance i is in the state g calls of
+ * dabs_solve_generations(ctxs[i], 1) leave it in alone.  INVALID_ARG for a
+ * NULL or repeated context, or generations before begin. */
+typedef struct dabs_batch dabs_batch;
+int  dabs_batch_create(dabs_ctx* const* ctxs, int32_t k, void* stream, dabs_batch** out);
+int  dabs_batch_begin(dabs_batch* b, const uint64_t* budgets, const uint64_t* seeds,
+                      const int64_t* targets);
+int  dabs_batch_generations(dabs_batch* b, int32_t count, int32_t* running);
+/* Measurement of a batch since its creation (waits for its stream): the
+ * instances still running, the batch-search launch groups in use, the kernels
+ * launched on the device, and the summed device time (ms) of the
+ * generations' batch-search phases.  Any output may be NULL. */
+int  dabs_batch_info(dabs_batch* b, int32_t* running, int32_t* search_groups,
+                     uint64_t* launches, double* search_ms);
+void dabs_batch_destroy(dabs_batch* b);
+
 /* ---- served form: request queue with continuous batching ----------------
  * A server owns a queue of solve requests.  dabs_server_step admits queued
  * requests (first come, first served) while the device bytes of their
@@ -236,18 +263,21 @@ int dabs_bulk_search_dev(dabs_ctx* ctx, uint64_t seed, uint32_t g, int32_t count
  * another allocator (a framework's caching allocator or a fixed arena) that
  * must not see cudaMalloc/cudaFree, which may synchronise the device and
  * fragment the arena.  No context is needed and nothing is allocated: the
- * negated weight copy, the slot launch order and the control block live in
- * one file-scope device array of 2 MiB + 64 KiB + 256 B that every GPU which
- * loads the library keeps until the process exits.
+ * negated weight copy, the diagonal, the slot launch order and the control
+ * block live in one file-scope device array of 2 MiB + 128 KiB + 256 B that
+ * every GPU which loads the library keeps until the process exits.
  *   W      device, n x ld int16 row-major, 16-byte aligned, ld a multiple of
- *          8, columns >= n zero, entries in [-32767, 32767]
+ *          8, columns >= n zero, entries in [-32767, 32767]; an entry of
+ *          -32768 is found on the device and refuses the call there: no
+ *          search runs and every slot gets best_E = INT64_MAX, flips = 0
  *   p      tabu, s_num/s_den, b_num/b_den and seed_mode are used
  *   X, delta (count x ld int32, 16-byte aligned), E, D, algo, best_X, best_E,
  *   flips  as in dabs_bulk_search_dev (device buffers of the caller)
  *   stream the cudaStream_t to enqueue on (NULL = default stream)
  * Limits: n * ld <= 1048576 and count <= 16384, else DABS_E_TOO_LARGE.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
+ * device and CUDA context, with that device current; after a cudaDeviceReset
+ * the next call looks it up again); make that first call before any stream
  * capture.  All calls share the array and it keeps the last call's contents
  * (each call rewrites the parts it reads), so calls whose GPU work overlaps
  * race: order them on one stream.  Asynchronous.                            */
@@ -255,6 +285,15 @@ int dabs_bulk_search_noalloc(const int16_t* W, int32_t n, int32_t ld, const dabs
                              uint64_t seed, uint32_t g, int32_t count, uint32_t* X,
                              int32_t* delta, int64_t* E, const uint32_t* D, const uint8_t* algo,
                              uint32_t* best_X, int64_t* best_E, uint32_t* flips, void* stream);
+
+/* ---- measurement (no counterpart in the paper) --------------------------
+ * Read bandwidth (GB/s) of `bytes` of device memory at `buf` (16-byte
+ * aligned), read `reps` times back to back after three warm-up passes on
+ * `stream` (NULL: the default stream).  A buffer well under the L2's size
+ * stays resident, which measures the L2 read bandwidth the batch search's
+ * row reads are compared with when W fits the L2.  Synchronous; allocates a
+ * 4-byte result slot. */
+int dabs_measure_read_gbs(const void* buf, size_t bytes, int32_t reps, void* stream, double* gbs);
 
 /* ---- inspection (host copies; synchronous) ------------------------------ */
 /* n, padded row length ld, packed words per vector, S, P, C, and the

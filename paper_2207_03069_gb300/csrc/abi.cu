@@ -257,14 +257,14 @@ int tc_recompute(dabs_ctx* ctx, const uint32_t* X, int count, int64_t* E, int32_
   const size_t pairs = (size_t)ctx->rows_pad * (ctx->n_pad / 2);
   k_bits_to_bf16<<<(unsigned)std::min<size_t>((pairs + 255) / 256, 4096), 256, 0, st>>>(
       X, count, ctx->n, ctx->nw, ctx->rows_pad, ctx->n_pad, ctx->Abf, ctrl);
-  CKLAUNCH();
+  CKSTAGE();
   CK(cudaMemsetAsync(ctx->E2, 0, sizeof(int64_t) * ctx->rows_pad, st));
   UmmaArgs u{count, ctx->n, ctx->n_pad, ctx->nw, ld_delta, X, ctx->diag, delta, ctx->E2, ctx->kerr, ctrl};
   const dim3 grid(ctx->n_pad / umma_tile_n(), (count + umma_tile_m() - 1) / umma_tile_m());
   k_recompute_umma<<<grid, 128, umma_smem_bytes(), st>>>(ctx->mapA, ctx->mapHi, ctx->mapLo, u);
-  CKLAUNCH();
+  CKSTAGE();
   k_halve<<<(count + 255) / 256, 256, 0, st>>>(E, ctx->E2, count, ctrl);
-  CKLAUNCH();
+  CKSTAGE();
   return DABS_OK;
 }
 
@@ -272,6 +272,7 @@ SearchArgs solve_search_args(dabs_ctx* ctx) {
   SearchArgs a{};
   a.W = ctx->W;
   a.Wneg = ctx->Wneg;
+  a.diag = ctx->diag;
   a.n = ctx->n; a.ld = ctx->ld; a.nw = ctx->nw; a.S = ctx->S;
   a.T = ctx->T; a.tau = ctx->tau; a.B = ctx->B; a.seed_mode = ctx->p.seed_mode;
   a.ctrl = ctx->ctrl;
@@ -297,58 +298,58 @@ int stage(dabs_ctx* ctx, int which) {
     for (int b = 0; b < 2; ++b) { o.pool_X[b] = ctx->poolX[b]; o.pool_algo[b] = ctx->poolA[b]; o.pool_op[b] = ctx->poolO[b]; }
     o.D = ctx->D; o.algo = ctx->algo; o.op = ctx->op; o.abs_mode = ctx->p.abs_mode;
     k_offspring<<<(ctx->S * 32 + 255) / 256, 256, 0, st>>>(o);
-    CKLAUNCH();
+    CKSTAGE();
     if (ctx->p.seed_mode == 1) {
       const size_t words = (size_t)ctx->S * ctx->nw;
       k_copy_targets<<<148, 256, 0, st>>>(ctx->D, ctx->X, ctx->E, words, ctx->S, ctx->ctrl);
-      CKLAUNCH();
+      CKSTAGE();
       if (ctx->recompute_mode == 1) {
         const int rc = tc_recompute(ctx, ctx->D, ctx->S, ctx->E, ctx->delta, ctx->ld, ctx->ctrl);
         if (rc) return rc;
       } else {
         EDArgs e{ctx->W, ctx->n, ctx->ld, ctx->nw, ctx->X, ctx->delta, ctx->ld, ctx->E, ctx->ctrl};
         k_energy_delta<<<dim3((ctx->n + 255) / 256, ctx->S), 256, 0, st>>>(e);
-        CKLAUNCH();
+        CKSTAGE();
       }
     }
   } else if (which == 1 || which == 4) {
     k_order_by_algo<<<1, 1024, 0, st>>>(ctx->algo, ctx->S, ctx->order, ctx->ctrl);
-    CKLAUNCH();
+    CKSTAGE();
     if (which == 4) return DABS_OK;  // launch order only (batched search follows)
     const SearchArgs a = solve_search_args(ctx);
     if (!launch_search(ctx->var.nw, ctx->var.ch, &a, st, nullptr))
       return fail(ctx, DABS_E_INVALID_ARG, "no batch-search variant %d/%d", ctx->var.nw, ctx->var.ch);
-    CKLAUNCH();
+    CKSTAGE();
   } else if (which == 2) {
     MergeArgs m{};
     m.nw = ctx->nw; m.S = ctx->S; m.P = ctx->P; m.C = ctx->C; m.Mmax = ctx->Mmax; m.ctrl = ctx->ctrl;
     for (int b = 0; b < 2; ++b) { m.pool_X[b] = ctx->poolX[b]; m.pool_E[b] = ctx->poolE[b]; m.pool_algo[b] = ctx->poolA[b]; m.pool_op[b] = ctx->poolO[b]; }
     m.best_X = ctx->bestX; m.best_E = ctx->bestE; m.algo = ctx->algo; m.op = ctx->op;
     k_merge<<<ctx->P, kMergeThreads, ctx->merge_smem, st>>>(m);
-    CKLAUNCH();
+    CKSTAGE();
   } else if (which == 3) {
     const bool restart = ctx->p.restart != 0;
     if (restart) CK(cudaMemsetAsync(ctx->rflag, 1, sizeof(uint32_t), st));  // skip unless armed
     FinArgs f{ctx->nw, ctx->S, ctx->ctrl, ctx->bestX, ctx->bestE, ctx->flips, ctx->gbestX,
               ctx->algo, ctx->op, ctx->stats, restart ? ctx->rflag : nullptr};
     k_finalize<<<1, 1024, 0, st>>>(f);
-    CKLAUNCH();
+    CKSTAGE();
     if (restart) {  // Section IV-B: restart once every pool has merged around the best
       const int entries = ctx->P * ctx->C;
       RestartArgs r{ctx->nw, ctx->P, ctx->C, ctx->p.restart_dist, ctx->ctrl,
                     {ctx->poolX[0], ctx->poolX[1]}, ctx->gbestX, ctx->rflag};
       k_restart_check<<<std::min((entries * 32 + 255) / 256, 1216), 256, 0, st>>>(r);
-      CKLAUNCH();
+      CKSTAGE();
       PoolArgs pa{};
       pa.n = ctx->n; pa.nw = ctx->nw; pa.P = ctx->P; pa.C = ctx->C; pa.ctrl = ctx->ctrl;
       pa.cond = ctx->rflag;
       for (int b = 0; b < 2; ++b) { pa.pool_X[b] = ctx->poolX[b]; pa.pool_E[b] = ctx->poolE[b]; pa.pool_algo[b] = ctx->poolA[b]; pa.pool_op[b] = ctx->poolO[b]; }
       k_pool_init<<<(entries * 32 + 255) / 256, 256, 0, st>>>(pa);
-      CKLAUNCH();
+      CKSTAGE();
       StateArgs sa{ctx->n, ctx->ld, ctx->nw, ctx->S, ctx->diag, ctx->X, ctx->delta, ctx->E,
                    nullptr, ctx->rflag, ctx->ctrl};
       k_state_init<<<304, 256, 0, st>>>(sa);
-      CKLAUNCH();
+      CKSTAGE();
     }
   } else {
     return fail(ctx, DABS_E_INVALID_ARG, "stage %d", which);

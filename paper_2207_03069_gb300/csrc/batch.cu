@@ -54,6 +54,12 @@ struct Batcher {
   // after the first, forked from and joined back into `stream`
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;  // ev[0] fork, ev[1 + g] join of side stream g
+  // measurement: kernels launched by generation() (all instances), and the
+  // device time of the batch-search phase (fork to join) of each generation
+  uint64_t search_launches = 0;
+  std::vector<cudaEvent_t> t_ev;  // a (start, end) pair per generation since the last collect
+  size_t t_used = 0;
+  double search_ms = 0;
 
   ~Batcher() {
     if (stream) cudaStreamSynchronize(stream);
@@ -66,6 +72,7 @@ struct Batcher {
     if (h_prefix) cudaFreeHost(h_prefix);
     for (cudaStream_t s : side) cudaStreamDestroy(s);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : t_ev) cudaEventDestroy(e);
     if (own && stream) cudaStreamDestroy(stream);
   }
 
@@ -109,6 +116,7 @@ struct Batcher {
   int rebuild() {
     int rc = sync_all();
     if (rc) return rc;
+    collect_search_time();
     std::vector<Group> ng;
     for (dabs_ctx* c : active) {
       const SearchVariant cv = batch_variant(c);
@@ -186,12 +194,30 @@ struct Batcher {
     return DABS_OK;
   }
 
+  // adds the search phases timed since the last call (the stream must have
+  // been synchronised)
+  void collect_search_time() {
+    for (size_t i = 0; i + 1 < t_used; i += 2) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, t_ev[i], t_ev[i + 1]) == cudaSuccess) search_ms += ms;
+    }
+    t_used = 0;
+  }
+
   // one generation of every active context
   int generation() {
     int rc;
     for (dabs_ctx* c : active)
       if ((rc = stage(c, 0)) || (rc = stage(c, 4))) return rc;
     const size_t G = groups.size();
+    while (t_ev.size() < t_used + 2) {
+      cudaEvent_t e;
+      if ((rc = check(cudaEventCreate(&e)))) return rc;
+      t_ev.push_back(e);
+    }
+    cudaEvent_t t0 = t_ev[t_used], t1 = t_ev[t_used + 1];
+    t_used += 2;
+    if ((rc = check(cudaEventRecord(t0, stream)))) return rc;
     if (G > 1 && (rc = check(cudaEventRecord(ev[0], stream)))) return rc;
     for (size_t gi = 0; gi < G; ++gi) {
       const Group& g = groups[gi];
@@ -203,10 +229,12 @@ struct Batcher {
       const SearchArgs first = solve_search_args(g.ctxs[0]);
       if (!launch_search(g.var.nw, g.var.ch, &first, st, nullptr, &m)) return DABS_E_INVALID_ARG;
       if ((rc = check(cudaGetLastError()))) return rc;
+      ++search_launches;
       if (gi > 0 && (rc = check(cudaEventRecord(ev[gi], st)))) return rc;
     }
     for (size_t gi = 1; gi < G; ++gi)
       if ((rc = check(cudaStreamWaitEvent(stream, ev[gi], 0)))) return rc;
+    if ((rc = check(cudaEventRecord(t1, stream)))) return rc;
     for (dabs_ctx* c : active)
       if ((rc = stage(c, 2)) || (rc = stage(c, 3))) return rc;
     return DABS_OK;
@@ -228,6 +256,107 @@ int read_done(std::vector<dabs_ctx*>& ctxs, std::vector<DevCtrl>& out, cudaStrea
 
 }  // namespace
 
+// A batch: contexts advanced together generation by generation on one
+// stream (the contexts' own streams are switched to it while the batch lives).
+struct dabs_batch {
+  Batcher b;
+  std::vector<dabs_ctx*> all;
+  std::vector<cudaStream_t> saved;
+  std::vector<uint64_t> launches0;  // the contexts' launch counters at creation
+  bool begun = false;
+};
+
+extern "C" int dabs_batch_create(dabs_ctx* const* ctxs, int32_t k, void* stream, dabs_batch** out) {
+  if (!out || k < 1 || !ctxs) return DABS_E_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < k; ++i) {
+    if (!ctxs[i]) return DABS_E_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return DABS_E_INVALID_ARG;  // one context at most once
+  }
+  dabs_batch* bt = new (std::nothrow) dabs_batch;
+  if (!bt) return DABS_E_OOM;
+  int rc = DABS_OK;
+  if (stream) bt->b.stream = static_cast<cudaStream_t>(stream);
+  else rc = bt->b.init();
+  if (rc) {
+    delete bt;
+    return rc;
+  }
+  bt->all.assign(ctxs, ctxs + k);
+  bt->saved.resize(k);
+  for (int i = 0; i < k; ++i) bt->launches0.push_back(ctxs[i]->launches);
+  for (int i = 0; i < k; ++i) {
+    bt->saved[i] = ctxs[i]->stream;
+    cudaStreamSynchronize(bt->saved[i]);
+    ctxs[i]->stream = bt->b.stream;
+    graph_stale(ctxs[i]);
+  }
+  *out = bt;
+  return DABS_OK;
+}
+
+extern "C" void dabs_batch_destroy(dabs_batch* bt) {
+  if (!bt) return;
+  bt->b.sync_all();
+  for (size_t i = 0; i < bt->all.size(); ++i) {
+    bt->all[i]->stream = bt->saved[i];
+    graph_stale(bt->all[i]);
+  }
+  delete bt;
+}
+
+extern "C" int dabs_batch_begin(dabs_batch* bt, const uint64_t* budgets, const uint64_t* seeds,
+                                const int64_t* targets) {
+  if (!bt || !budgets || !seeds) return DABS_E_INVALID_ARG;
+  int rc = bt->b.sync_all();
+  for (size_t i = 0; i < bt->all.size() && !rc; ++i)
+    rc = dabs_solve_begin(bt->all[i], seeds[i], budgets[i], targets ? targets[i] : INT64_MIN);
+  if (rc) return rc;
+  bt->b.active = bt->all;
+  rc = bt->b.rebuild();
+  bt->begun = rc == DABS_OK;
+  return rc;
+}
+
+extern "C" int dabs_batch_generations(dabs_batch* bt, int32_t count, int32_t* running) {
+  if (!bt || count < 0) return DABS_E_INVALID_ARG;
+  if (!bt->begun) return DABS_E_INVALID_ARG;
+  int rc = DABS_OK;
+  if (!bt->b.active.empty() && count > 0) {
+    for (int q = 0; q < count && !rc; ++q) rc = bt->b.generation();
+    std::vector<DevCtrl> cs;
+    if (!rc) rc = read_done(bt->b.active, cs, bt->b.stream);
+    if (!rc) bt->b.collect_search_time();
+    if (!rc) {
+      std::vector<dabs_ctx*> still;
+      for (size_t i = 0; i < bt->b.active.size(); ++i)
+        if (!cs[i].done) still.push_back(bt->b.active[i]);
+      if (still.size() != bt->b.active.size()) {
+        bt->b.active.swap(still);
+        if (!bt->b.active.empty()) rc = bt->b.rebuild();
+      }
+    }
+  }
+  if (running) *running = (int32_t)bt->b.active.size();
+  return rc;
+}
+
+extern "C" int dabs_batch_info(dabs_batch* bt, int32_t* running, int32_t* search_groups,
+                               uint64_t* launches, double* search_ms) {
+  if (!bt) return DABS_E_INVALID_ARG;
+  const int rc = bt->b.sync_all();
+  if (rc) return rc;
+  bt->b.collect_search_time();
+  uint64_t l = bt->b.search_launches;
+  for (size_t i = 0; i < bt->all.size(); ++i) l += bt->all[i]->launches - bt->launches0[i];
+  if (running) *running = (int32_t)bt->b.active.size();
+  if (search_groups) *search_groups = (int32_t)bt->b.groups.size();
+  if (launches) *launches = l;
+  if (search_ms) *search_ms = bt->b.search_ms;
+  return DABS_OK;
+}
+
 extern "C" int dabs_batch_solve(dabs_ctx* const* ctxs, int32_t k, const uint64_t* budgets,
                                 const uint64_t* seeds, const int64_t* targets,
                                 uint8_t* const* best_X, int64_t* best_E, uint64_t* flips) {
@@ -235,36 +364,13 @@ extern "C" int dabs_batch_solve(dabs_ctx* const* ctxs, int32_t k, const uint64_t
   for (int i = 0; i < k; ++i)
     if (!ctxs[i]) return DABS_E_INVALID_ARG;
   if (k == 0) return DABS_OK;
-  Batcher b;
-  int rc = b.init();
+  dabs_batch* bt = nullptr;
+  int rc = dabs_batch_create(ctxs, k, nullptr, &bt);
   if (rc) return rc;
-  std::vector<cudaStream_t> saved(k);
-  for (int i = 0; i < k; ++i) {
-    saved[i] = ctxs[i]->stream;
-    cudaStreamSynchronize(saved[i]);
-    ctxs[i]->stream = b.stream;
-  }
-  auto restore = [&]() {
-    b.sync_all();
-    for (int i = 0; i < k; ++i) ctxs[i]->stream = saved[i];
-  };
-  for (int i = 0; i < k && !rc; ++i)
-    rc = dabs_solve_begin(ctxs[i], seeds[i], budgets[i], targets ? targets[i] : INT64_MIN);
-  b.active.assign(ctxs, ctxs + k);
-  if (!rc) rc = b.rebuild();
-  int chunk = 1;
-  std::vector<DevCtrl> cs;
-  while (!rc && !b.active.empty()) {
-    for (int q = 0; q < chunk && !rc; ++q) rc = b.generation();
-    if (rc) break;
-    if ((rc = read_done(b.active, cs, b.stream))) break;
-    std::vector<dabs_ctx*> still;
-    for (size_t i = 0; i < b.active.size(); ++i)
-      if (!cs[i].done) still.push_back(b.active[i]);
-    if (still.size() != b.active.size()) {
-      b.active.swap(still);
-      if (!b.active.empty()) rc = b.rebuild();
-    }
+  rc = dabs_batch_begin(bt, budgets, seeds, targets);
+  int chunk = 1, running = k;
+  while (!rc && running > 0) {
+    rc = dabs_batch_generations(bt, chunk, &running);
     if (chunk < 16) chunk <<= 1;
   }
   for (int i = 0; i < k && !rc; ++i) {
@@ -273,7 +379,7 @@ extern "C" int dabs_batch_solve(dabs_ctx* const* ctxs, int32_t k, const uint64_t
       rc = dabs_solve_best(ctxs[i], best_X ? best_X[i] : nullptr, best_E ? &best_E[i] : nullptr);
     if (!rc && flips) rc = dabs_solve_status(ctxs[i], &flips[i], nullptr, nullptr, nullptr);
   }
-  restore();
+  dabs_batch_destroy(bt);
   return rc;
 }
 
@@ -425,6 +531,7 @@ extern "C" int dabs_server_step(dabs_server* s, int32_t generations, int32_t* pe
       if ((rc = s->batch.generation())) return rc;
     std::vector<DevCtrl> cs;
     if ((rc = read_done(s->batch.active, cs, s->batch.stream))) return rc;
+    s->batch.collect_search_time();
     std::vector<Request*> still;
     for (size_t i = 0; i < s->running.size(); ++i) {
       Request* r = s->running[i];

@@ -100,6 +100,7 @@ struct DevCtrl {
 struct SearchArgs {
   const int16_t* W;     // [n][ld] row-major, zero padded
   const int16_t* Wneg;  // -W, same layout
+  const int32_t* diag;  // [n] W_kk
   int32_t n, ld, nw; // nw = 32-bit words of a bit vector
   int32_t S;         // search slots in this launch
   int32_t T;         // flips per main search

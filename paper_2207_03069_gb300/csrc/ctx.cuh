@@ -84,6 +84,7 @@ struct dabs_ctx {
   CUtensorMap mapA{}, mapHi{}, mapLo{};
   std::vector<void*> allocs;
   std::string err;
+  uint64_t launches = 0;      // kernels launched by stage() (counted for the batched form)
 };
 
 
@@ -96,6 +97,12 @@ struct dabs_ctx {
   } while (0)
 
 #define CKLAUNCH() CK(cudaGetLastError())
+// a kernel launch of a generation's stages: checked and counted
+#define CKSTAGE()        \
+  do {                   \
+    CKLAUNCH();          \
+    ++ctx->launches;     \
+  } while (0)
 
 
 namespace dabs_internal {

@@ -74,6 +74,7 @@ struct SmemSearch {
   int4 red[2][C::NW];        // reduction slots (double buffered)
   int tot[C::CH][C::NW];     // per chunk, per warp candidate counts (k-th pick)
   int pick[4];               // broadcast of a pick made by one thread
+  int dflip;                 // Delta_i of the flip being made, from the owner of bit i
 };
 
 #define DABS_CASES(X)                                                                      \
@@ -103,6 +104,7 @@ struct Searcher {
   uint64_t seed;
   const int16_t* W;     // W, and Wneg = -W: row i of sigma(x_i) W is read directly
   const int16_t* Wneg;
+  const int32_t* diag;  // W_kk
   int n, ld;
   int ring_len, ring_head;  // tabu ring (uniform); entry j lives in lane j's ringv
   int ringv;
@@ -118,7 +120,7 @@ struct Searcher {
   __device__ __forceinline__ Searcher(const SearchArgs& a, SmemSearch<C>* smem, int tid,
                                       uint32_t sidx, uint32_t gen, uint64_t sd)
       : sm(smem), t(tid), lane(tid & 31), warp(tid >> 5), buf(0), s(sidx), g(gen), seed(sd),
-        W(a.W), Wneg(a.Wneg), n(a.n), ld(a.ld), ring_len(0), ring_head(0), ringv(0),
+        W(a.W), Wneg(a.Wneg), diag(a.diag), n(a.n), ld(a.ld), ring_len(0), ring_head(0), ringv(0),
         kb(C::KEY ? a.key_bits : 0) {}
 
   // ------------------------------------------------------------ bit helpers
@@ -131,34 +133,27 @@ struct Searcher {
   __device__ __forceinline__ uint32_t key_of(int lp) const {
     return lp < 0 ? UINT_MAX : (((uint32_t)kidx(lp) << 1) | (uint32_t)bit_at(xb, lp));
   }
-  // value of d at a run-time position 0 <= p < EPT: a binary select tree on
-  // the bits of p (no branch, no local memory)
-  __device__ __forceinline__ int get_at(int p) const {
-    int v[EPT];
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) v[q] = d[q];
-#pragma unroll
-    for (int w = 1; w < EPT; w <<= 1) {
-      const bool hi = (p & w) != 0;
-#pragma unroll
-      for (int q = 0; q < EPT; q += 2 * w) v[q] = hi ? v[q + w] : v[q];
-    }
-    return v[0];
-  }
-  // Eq. (5) at a run-time position: Delta_i = -Delta_i (given), sigma flips
-  __device__ __forceinline__ void set_flipped(int p, int v) {
+  // Eq. (5) at a run-time position p (the owner of bit i = kidx(p)): reads
+  // Delta_i, stores the flipped value plus corr, and flips sigma(x_i).  A
+  // switch on p keeps d in registers (no local memory).
+  __device__ __forceinline__ int flip_at(int p, int i, int xi, int corr) {
+    int di = 0;
     switch (p) {
-#define DABS_SET(q)                         \
-  case q:                                   \
-    if constexpr (q < EPT) {                \
-      d[q < EPT ? q : 0] = v;               \
-      sg[q < EPT ? q : 0] = -sg[q < EPT ? q : 0]; \
-    }                                       \
+#define DABS_FLIP(q)                                                          \
+  case q:                                                                     \
+    if constexpr (q < EPT) {                                                  \
+      constexpr int qq = q < EPT ? q : 0;                                     \
+      const int o = d[qq];                                                    \
+      di = C::KEY ? (o >> kb) : o;                                            \
+      d[qq] = (C::KEY ? -di * (1 << kb) + ((i << 1) | (xi ^ 1)) : -di) + corr; \
+      sg[qq] = -sg[qq];                                                       \
+    }                                                                         \
     break;
-      DABS_CASES(DABS_SET)
-#undef DABS_SET
+      DABS_CASES(DABS_FLIP)
+#undef DABS_FLIP
       default: break;
     }
+    return di;
   }
 
   // ------------------------------------------------------------ reductions
@@ -277,8 +272,33 @@ struct Searcher {
       rv[c] = off < ld ? __ldg(reinterpret_cast<const uint4*>(row + off)) : make_uint4(0, 0, 0, 0);
     }
   }
-  __device__ __forceinline__ void row_apply(const uint4 (&rv)[CH], int i, int di, int xi) {
+  // Eq. (5) and x_i ^= 1, made while row i is in flight: the owner of bit i
+  // reads Delta_i from its register and stores -Delta_i raised by W_ii (in
+  // key units), because the row update that follows adds
+  // sigma(x_i) W_ii sigma'(x_i) = -W_ii at k = i once sigma(x_i) is flipped
+  // (sparse rows hold no diagonal entry: nothing to raise).  Returns
+  // Delta_i in every thread of the group.
+  __device__ __forceinline__ int commit(int i, int xi) {
     i = min(max(i, 0), n - 1);
+    int di = 0;
+    if (t == owner_t(i)) {
+      constexpr bool sparse = C::RF == ROWS_SPARSE_SMEM || C::RF == ROWS_SPARSE_GLOBAL;
+      const int corr = sparse ? 0 : __ldg(diag + i) * (C::KEY ? (1 << kb) : 1);
+      const int pi = local_p(i);
+      di = flip_at(pi, i, xi, corr);
+      xb[0] ^= 1u << pi;
+    }
+    if constexpr (NW == 1) {
+      di = __shfl_sync(FULL, di, owner_t(i));
+    } else {
+      if (t == owner_t(i)) sm->dflip = di;
+      __syncthreads();
+      di = sm->dflip;
+    }
+    return di;
+  }
+  // Eq. (4) for every k (k = i included, see commit), E += Delta_i
+  __device__ __forceinline__ void row_apply(const uint4 (&rv)[CH], int di) {
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
 #pragma unroll
@@ -286,12 +306,6 @@ struct Searcher {
         const int p = 8 * c + e;
         d[p] += w16(rv[c], e) * sg[p];
       }
-    }
-    if (t == owner_t(i)) {
-      const int pi = local_p(i);
-      // Eq. (5): Delta_i = -Delta_i (and x_i, in the keyed form's low bits)
-      set_flipped(pi, C::KEY ? -di * (1 << kb) + ((i << 1) | (xi ^ 1)) : -di);
-      xb[0] ^= 1u << pi;
     }
     E += di;
     ++flips;
@@ -313,8 +327,8 @@ struct Searcher {
 
   // ------------------------------------------------------------ k-th pick
   // The ((u * count) >> 32)-th set bit of the group-wide candidate mask Cm, in
-  // ascending bit order.  Returns key = (i << 1) | x_i and Delta_i via *di.
-  __device__ __forceinline__ uint32_t kth(uint32_t Cm, uint32_t u, int* di) {
+  // ascending bit order.  Returns key = (i << 1) | x_i.
+  __device__ __forceinline__ uint32_t kth(uint32_t Cm, uint32_t u) {
     int cnt[CH], wt[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -356,7 +370,6 @@ struct Searcher {
         }
     }
     uint32_t key = 0;
-    int dv = 0;
     if (warp == wsel) {
       int mycnt = 0;
 #pragma unroll
@@ -380,44 +393,34 @@ struct Searcher {
       if (r >= c2) { pos += 2; r -= c2; byte >>= 2; }
       if (r >= (int)(byte & 1u)) pos += 1;
       const int p = 8 * csel + pos;
-      if (mine) {
-        key = key_of(p);
-        dv = get_at(p);
-      }
+      if (mine) key = key_of(p);
       const unsigned bal = __ballot_sync(FULL, mine);
       const int src = bal ? __ffs(bal) - 1 : 0;
       key = __shfl_sync(FULL, key, src);
-      dv = __shfl_sync(FULL, dv, src);
       if constexpr (NW > 1) {
-        if (lane == 0) { sm->pick[0] = (int)key; sm->pick[1] = dv; }
+        if (lane == 0) sm->pick[0] = (int)key;
       }
     }
     if constexpr (NW > 1) {
       __syncthreads();
       key = (uint32_t)sm->pick[0];
-      dv = sm->pick[1];
     }
-    *di = dv;
     return key;
   }
 
-  // Delta_i and x_i of a bit chosen without a reduction (TwoNeighbor)
-  __device__ __forceinline__ uint32_t fetch(int i, int* di) {
+  // x_i of a bit chosen without a reduction (TwoNeighbor)
+  __device__ __forceinline__ int fetch_x(int i) {
     const int pi = local_p(i), ot = owner_t(i);
-    int v = get_at(pi);
-    uint32_t x = bit_at(xb, pi) ? 1u : 0u;
+    int x = bit_at(xb, pi) ? 1 : 0;
     if constexpr (NW == 1) {
-      v = __shfl_sync(FULL, v, ot);
       x = __shfl_sync(FULL, x, ot);
     } else {
-      if (t == ot) { sm->pick[2] = v; sm->pick[3] = (int)x; }
+      if (t == ot) sm->pick[3] = x;
       __syncthreads();
-      v = sm->pick[2];
-      x = (uint32_t)sm->pick[3];
+      x = sm->pick[3];
       __syncthreads();
     }
-    *di = v;
-    return ((uint32_t)i << 1) | x;
+    return x;
   }
 
   // ------------------------------------------------------------ tabu
@@ -610,7 +613,7 @@ struct Searcher {
             kj = k[0];
           }
           i = it == 0 ? 0 : ((it & 1) ? (it + 1) >> 1 : (it >> 1) - 1);
-          xi = (int)(fetch(i, &di) & 1u);
+          xi = fetch_x(i);
         } else if (ALGO == MAXMIN || ALGO == POSITIVEMIN) {
           if ((it & 31) == 0) {
             // the flips of iterations it .. it+31 are flips .. flips+31
@@ -673,7 +676,7 @@ struct Searcher {
             gminu(k);
             kj = k[0];
           }
-          const uint32_t key = kth(Cm, ukth, &di);
+          const uint32_t key = kth(Cm, ukth);
           i = (int)(key >> 1);
           xi = (int)(key & 1u);
         } else if (ALGO == CYCLICMIN) {
@@ -745,6 +748,7 @@ struct Searcher {
       uint4 rv[CH];
       row_load(i, xi, rv);
       // independent of row i: overlaps its load latency
+      di = commit(i, xi);
       if (phase == PH_MAIN) {
         if (ALGO != TWONEIGHBOR) tabu_push(i, tau);
         if (ALGO == RANDOMMIN && it + 1 < Tmain) {
@@ -752,7 +756,7 @@ struct Searcher {
           rr_ready = true;
         }
       }
-      row_apply(rv, i, di, xi);
+      row_apply(rv, di);
       if (phase == PH_MAIN && ++it == Tmain) {
         phase = PH_GREEDY;
         ++runs;
@@ -851,9 +855,7 @@ struct Searcher {
           gmin(v);
           mk = v[0];
           const int i = it == 0 ? 0 : ((it & 1) ? (it + 1) >> 1 : (it >> 1) - 1);
-          int dk;
-          fetch(i, &dk);
-          sk = dk;
+          sk = (i << 1) | fetch_x(i);  // the low part of its key
         } else if (ALGO == MAXMIN || ALGO == POSITIVEMIN) {
           if ((it & 31) == 0) {
             const uint4 u = draw(seed, flips + (uint32_t)lane, g, s,
@@ -909,9 +911,7 @@ struct Searcher {
             }
             ukth = u0;
           }
-          int dk;
-          kth(Cm, ukth, &dk);
-          sk = dk;
+          sk = (int)kth(Cm, ukth);  // the low part of its key
         } else if (ALGO == CYCLICMIN) {
           const uint64_t wl = (cube_of(fup) * (uint64_t)n) >> 32;
           const int wsz = (int)(wl < (uint64_t)cwin ? (uint64_t)cwin : (wl > (uint64_t)n ? (uint64_t)n : wl));
@@ -958,10 +958,11 @@ struct Searcher {
         const int m = mk >> kb;
         if (E + m < Ebest) take_best((uint32_t)(mk & low), m);
       }
-      const int i = (sk & low) >> 1, xi = sk & 1, di = sk >> kb;
+      const int i = (sk & low) >> 1, xi = sk & 1;
       uint4 rv[CH];
       row_load(i, xi, rv);
       // independent of row i: overlaps its load latency
+      const int di = commit(i, xi);
       if (phase == PH_MAIN) {
         if (ALGO != TWONEIGHBOR) tabu_push(i, tau);
         if (ALGO == RANDOMMIN && it + 1 < Tmain) {
@@ -969,7 +970,7 @@ struct Searcher {
           rr_ready = true;
         }
       }
-      row_apply(rv, i, di, xi);
+      row_apply(rv, di);
       if (phase == PH_MAIN && ++it == Tmain) {
         phase = PH_GREEDY;
         ++runs;

@@ -86,6 +86,13 @@ EXPORTS = {
     "dabs_set_recompute": (C.c_int, [C.c_void_p, C.c_int32]),
     "dabs_kernel_status": (C.c_int, [C.c_void_p]),
     "dabs_batch_solve": (C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 6),
+    "dabs_batch_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "dabs_batch_begin": (C.c_int, [C.c_void_p] * 4),
+    "dabs_batch_generations": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "dabs_batch_destroy": (None, [C.c_void_p]),
+    "dabs_batch_info": (C.c_int, [C.c_void_p] * 5),
+    "dabs_measure_read_gbs": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int32, C.c_void_p,
+                                        C.c_void_p]),
     "dabs_server_create": (C.c_int, [C.c_size_t, C.c_void_p]),
     "dabs_server_destroy": (None, [C.c_void_p]),
     "dabs_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_uint64,
@@ -161,6 +168,67 @@ def batch_solve(ctxs, budgets, seeds, targets=None):
     if rc != OK:
         raise DabsError(rc, lib().dabs_last_error(ctxs[0]._h).decode() if k else "")
     return [(Xs[i], int(E[i]), int(F[i])) for i in range(k)]
+
+
+def measure_read_gbs(buf, reps: int = 100, stream=None) -> float:
+    """dabs_measure_read_gbs on a device tensor: its read bandwidth in GB/s."""
+    handle = None if stream is None else getattr(stream, "cuda_stream", stream)
+    g = C.c_double()
+    rc = lib().dabs_measure_read_gbs(_ptr(buf), buf.numel() * buf.element_size(), reps,
+                                     C.c_void_p(handle) if handle else None, C.byref(g))
+    if rc != OK:
+        raise DabsError(rc)
+    return float(g.value)
+
+
+class Batch:
+    """dabs_batch_*: contexts advanced together, one call per group of generations."""
+
+    def __init__(self, ctxs, stream=None):
+        self.ctxs = list(ctxs)
+        k = len(self.ctxs)
+        hs = (C.c_void_p * k)(*[c._h.value for c in self.ctxs])
+        handle = None if stream is None else getattr(stream, "cuda_stream", stream)
+        self._h = C.c_void_p()
+        rc = lib().dabs_batch_create(hs, k, C.c_void_p(handle) if handle else None,
+                                     C.byref(self._h))
+        if rc != OK:
+            raise DabsError(rc)
+
+    def close(self):
+        if self._h:
+            lib().dabs_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def begin(self, budgets, seeds, targets=None):
+        bud = np.asarray([min(int(b), 2**64 - 1) for b in budgets], np.uint64)
+        sd = np.asarray(seeds, np.uint64)
+        tg = None if targets is None else np.asarray(
+            [INT64_MIN if t is None else int(t) for t in targets], np.int64)
+        rc = lib().dabs_batch_begin(self._h, _ptr(bud), _ptr(sd), _ptr(tg))
+        if rc != OK:
+            raise DabsError(rc)
+
+    def generations(self, count: int = 1) -> int:
+        r = C.c_int32(0)
+        rc = lib().dabs_batch_generations(self._h, count, C.byref(r))
+        if rc != OK:
+            raise DabsError(rc)
+        return int(r.value)
+
+    def info(self) -> dict:
+        r, g, l, ms = C.c_int32(), C.c_int32(), C.c_uint64(), C.c_double()
+        rc = lib().dabs_batch_info(self._h, C.byref(r), C.byref(g), C.byref(l), C.byref(ms))
+        if rc != OK:
+            raise DabsError(rc)
+        return dict(running=int(r.value), search_groups=int(g.value), launches=int(l.value),
+                    search_ms=float(ms.value))
 
 
 class Server:

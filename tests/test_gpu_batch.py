@@ -126,3 +126,40 @@ def test_batch_with_row_formats_equals_alone(D):
         alone.set_rows(m)
         a = alone.solve(10**9, 5 + k)
         assert out[k][1] == a[1] and out[k][2] == a[2] and np.array_equal(out[k][0], a[0])
+
+
+def test_stepwise_batch_generations_equal_alone(D, orc):
+    """dabs_batch_* one generation at a time: after every generation each
+    instance's pools, results and per-search state equal its generations
+    alone (and, for the small instances, the oracle's)."""
+    from test_gpu_parity import compare_generation
+    kw = dict(searches=40, pools=4, pool_cap=12, tabu=8, s=(1, 10), b=(1, 1), seed_mode=1)
+    sizes = [96, 700, 1500, 300]
+    Ws = [instance(n, 30 + k) for k, n in enumerate(sizes)]
+    ctxs = [D.Context(W, **kw) for W in Ws]
+    alone = [D.Context(W, **kw) for W in Ws]
+    small = [orc.Solver(W, orc.make_params(**kw), 70 + k) if W.shape[0] <= 300 else None
+             for k, W in enumerate(Ws)]
+    b = D.Batch(ctxs)
+    budgets = [10**12, 10**12, 10**12, 3 * 40 * 300]  # the last stops on its budget
+    b.begin(budgets, [70 + k for k in range(len(Ws))])
+    for k, a in enumerate(alone):
+        a.solve_begin(70 + k, budget=budgets[k])
+    running = len(Ws)
+    for g in range(5):
+        running = b.generations(1)
+        for k, (c, a) in enumerate(zip(ctxs, alone)):
+            a.solve_generations(1)
+            assert c.solve_status() == a.solve_status(), (g, k)
+            for x, y in zip(c.read_pools(), a.read_pools()):
+                assert np.array_equal(x, y), (g, k)
+            for x, y in zip(c.read_generation(), a.read_generation()):
+                assert np.array_equal(x, y), (g, k)
+            if small[k] is not None and g < 3:
+                small[k].generation(8)
+                compare_generation(c, small[k], Ws[k].shape[0], f"gen {g} instance {k}")
+    assert running == len(Ws) - 1  # the budget-limited instance retired
+    b.close()
+    # the contexts work on their own again afterwards (two generations' budget)
+    X, E, F = ctxs[0].solve(2 * 40 * 96, seed=3)
+    assert (E, F) == alone[0].solve(2 * 40 * 96, seed=3)[1:]
