@@ -1,17 +1,23 @@
 """Benchmark of the DABS bulk local search on GB300.
 
-Default workload: the sparse Max-Cut-shaped QUBO (G(n=800, p=0.06), edge
-weights +-1, seed 1) with 1024 concurrent searches, 4 pools x 100 packets,
-tabu 8, s = 1/10, b = 10, Straight seeding, one instance per launch.  One step
-is one generation: offspring -> batch search (every search flips >= b*n bits)
--> pool merge -> finalise, all in the CUDA library.
+Default workload (the metric's "batched vs plain"): 64 dense QUBOs with n
+log-uniform in [256, 4096] (seed 3), W ~ U[-1000, 1000] (seed 1000 + i), 256
+searches each, 4 pools x 100 packets, tabu 8, s = 1/10, b = 1, recompute
+seeding on the tensor cores.  One step is one generation of every instance:
+offspring -> recompute -> batch search (every search flips >= b*n bits) ->
+pool merge -> finalise, all in the CUDA library, in the batched form (one
+batch-search launch per kernel variant for all instances).  The same instances
+and seeds are also timed in the plain form (one instance per launch) and must
+give identical results.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dabs|reference]
+                    [--workload batched64|maxcut800|tsp32|dense64|qasp5627]
 
 Prints one JSON line.  --impl reference times the plain C oracle (the CPU
-restatement of the method) on the host cores, one generation per step.
-Under torchrun (N > 1) every rank runs an independent replica (weak scaling,
-no collective on the data path); rank 0 prints the aggregate.
+restatement of the method) on the host cores, one generation of a bounded
+sample of the workload per step.  Under torchrun (N > 1) every rank runs an
+independent replica (weak scaling, no collective on the data path); rank 0
+prints the aggregate.
 """
 from __future__ import annotations
 
@@ -33,6 +39,10 @@ sys.path.insert(0, ROOT)
 from paper_2207_03069_gb300 import workloads as wl  # noqa: E402
 
 WORKLOADS = {
+    "batched64": dict(desc="64 dense QUBOs, n log-uniform in [256,4096] (seed 3), W~U[-1000,1000] "
+                           "(seed 1000+i), 256 searches each", kind="batched", count=64, n_lo=256,
+                      n_hi=4096, searches=256, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1),
+                      seed_mode=1, sample_searches=16),
     "maxcut800": dict(desc="sparse Max-Cut QUBO G(n=800,p=0.06) w=+-1 seed 1", n=800,
                       searches=1024, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(10, 1),
                       seed_mode=0),
@@ -44,6 +54,11 @@ WORKLOADS = {
                      n=5627, searches=1024, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1),
                      seed_mode=0),
 }
+
+
+def batched_instances(spec):
+    ns = wl.batched_sizes(spec["count"], spec["n_lo"], spec["n_hi"], seed=3)
+    return [wl.dense_qubo(int(n), -1000, 1000, seed=1000 + i) for i, n in enumerate(ns)]
 
 
 def make_W(name):
@@ -67,10 +82,10 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def search_profile():
-    """DRAM traffic of the batch-search kernel from the committed ncu summary,
+def search_profile(fname="search_maxcut800.json"):
+    """DRAM traffic of the batch-search kernel from a committed ncu summary,
     valid only while the kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", "search_maxcut800.json")
+    path = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(path):
         return None
     with open(path) as f:
@@ -153,6 +168,15 @@ def l2_copy_gbs(torch, dev):
     e1.record()
     torch.cuda.synchronize()
     return 2 * a.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
+def l2_read_gbs(torch, dev, mib=32, reps=400):
+    """Read bandwidth of a buffer that stays in L2 (32 MiB of the 129 MB L2),
+    measured by the library's read kernel (dabs_measure_read_gbs): the L2 peak
+    the flip kernel's row reads are compared with when W fits the L2."""
+    from paper_2207_03069_gb300 import dabs
+    a = torch.randint(-1000, 1000, ((mib << 20) // 4,), dtype=torch.int32, device=dev)
+    return dabs.measure_read_gbs(a, reps)
 
 
 def recompute_rate(torch, dabs, dev, n=4096, count=256, reps=20):
@@ -319,78 +343,13 @@ def small_graphs(dabs, generations=200, reps=3):
     return out
 
 
-def serving(dabs, seconds=4.0, rate=50.0, generations=20, sizes=(512, 1024, 2048, 4096, 8192),
-            budget_gb=60, plain=True, big=16384):
-    """Poisson arrivals (seed 4) of dense QUBOs, n uniform in `sizes`, plus one
-    n = `big` instance mid-trace, 256 searches, 20 generations each, recompute
-    seeding; served with continuous batching under an HBM budget, and (plain)
-    one request at a time on the same trace.  Latency = completion - arrival."""
-    rng = np.random.default_rng(4)
-    arr = wl.poisson_arrivals(rate, seconds, seed=4)
-    reqs = [(float(t), int(rng.choice(sizes)), 5000 + i) for i, t in enumerate(arr)]
-    if big:  # the one n = 16384 instance (512 MB of int16 W), arriving mid-trace
-        reqs.append((seconds / 2, big, 9999))
-        reqs.sort()
-    kw = dict(searches=256, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=1,
-              max_generations=generations)
-    params = dabs.default_params(**kw)
-    Wcache = {}
+_T0 = time.perf_counter()
 
-    def W_of(n, sd):
-        key = (n, sd)
-        if key not in Wcache:
-            Wcache[key] = wl.dense_qubo(n, -1000, 1000, seed=sd)
-        return Wcache[key]
 
-    for _, n, sd in reqs:  # instances are prepared before the clock starts
-        W_of(n, sd)
-    out = {"workload": f"Poisson {rate}/s for {seconds}s, n in {list(sizes)}"
-                       + (f" plus one n={big} instance" if big else "")
-                       + f", 256 searches, {generations} generations, recompute seeding",
-           "requests": len(reqs)}
-    srv = dabs.Server(budget_gb << 30)
-    t0 = time.perf_counter()
-    tickets, i, pending = [], 0, 0
-    while i < len(reqs) or pending:
-        now = time.perf_counter() - t0
-        while i < len(reqs) and reqs[i][0] <= now:
-            _, n, sd = reqs[i]
-            tickets.append(srv.submit(W_of(n, sd), params, 10**12, sd))
-            i += 1
-        if srv.info()[1] + srv.info()[2] == 0:
-            time.sleep(0.001)
-            pending = 0
-            continue
-        pending = srv.step(1)
-    wall = time.perf_counter() - t0
-    lat, fl, rb = [], 0, 0
-    for t, (_, n, _) in zip(tickets, reqs):
-        st, X, E, F, L = srv.poll(t)
-        lat.append(L)
-        fl += F
-        rb += F * 2 * n
-        if n == big:
-            out["served_big_latency_s"] = L
-    srv.close()
-    out.update({"served_p50_s": pct(lat, 50), "served_p99_s": pct(lat, 99),
-                "served_flips_per_s": fl / wall, "served_wall_s": wall,
-                "roofline_served": row_roofline(rb / wall)})
-    if plain:
-        t0 = time.perf_counter()
-        lat2, free_at = [], 0.0
-        for (ta, n, sd) in reqs:
-            start = max(ta, free_at)
-            now = time.perf_counter() - t0
-            if now < start:
-                time.sleep(start - now)
-            c = dabs.Context(W_of(n, sd), **kw)
-            c.solve(10**12, seed=sd)
-            c.close()
-            free_at = time.perf_counter() - t0
-            lat2.append(free_at - ta)
-        out.update({"plain_p50_s": pct(lat2, 50), "plain_p99_s": pct(lat2, 99),
-                    "plain_flips_per_s": fl / (time.perf_counter() - t0)})
-    return out
+def progress(msg):
+    """A progress line on stderr (the JSON line alone goes to stdout)."""
+    sys.stderr.write(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}\n")
+    sys.stderr.flush()
 
 
 def torch_sync():
@@ -440,8 +399,52 @@ def dist_setup():
     return ws, rank, lrank, pg
 
 
+def run_reference_batched(args, ws, rank, pg):
+    """The oracle on the batched workload's sample (every instance, with
+    sample_searches searches each): one generation of all instances per step."""
+    spec = WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    Ws = batched_instances(spec)
+    ns = [W.shape[0] for W in Ws]
+    from oracle import oracle as orc
+    threads = os.cpu_count() or 1
+    p = orc.make_params(searches=spec["sample_searches"], pools=spec["pools"],
+                        pool_cap=spec["pool_cap"], tabu=spec["tabu"], s=spec["s"], b=spec["b"],
+                        seed_mode=spec["seed_mode"])
+    sos = [orc.Solver(W, p, args.seed + i) for i, W in enumerate(Ws)]
+    for _ in range(args.warmup):
+        for so in sos:
+            so.generation(threads)
+    t0 = time.perf_counter()
+    flips = 0
+    for _ in range(args.steps):
+        for so in sos:
+            flips += so.generation(threads)
+    dt = time.perf_counter() - t0
+    v = flips / dt
+    line = {"impl": "reference", "metric": "bit flips/s (batched vs plain, bit-exact)", "value": v,
+            "unit": "flips/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": spec["desc"], "instances": len(Ws), "n_min": min(ns),
+                       "n_max": max(ns), "searches": spec["searches"], "pools": spec["pools"],
+                       "pool_cap": spec["pool_cap"], "tabu": spec["tabu"],
+                       "s": "%d/%d" % spec["s"], "b": "%d/%d" % spec["b"],
+                       "seeding": "recompute", "parallelism": "host threads"},
+            "cpu_baseline": {"value": v, "unit": "flips/s", "cores": threads, "kind": "oracle",
+                             "sample": f"per step one generation of all {len(Ws)} instances with "
+                                       f"{spec['sample_searches']} of their {spec['searches']} "
+                                       f"searches (same W and parameters)"},
+            "e2e": {"value": v, "unit": "flips/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, ws, rank, pg):
     spec = WORKLOADS[args.workload]
+    if spec.get("kind") == "batched":
+        return run_reference_batched(args, ws, rank, pg)
     if rank != 0:
         return
     Wm = make_W(args.workload)
@@ -475,13 +478,433 @@ def run_reference(args, ws, rank, pg):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched workload
+def oracle_batched_rate(Ws, spec, seed, seconds, threads, gens=None):
+    """The oracle (plain C, as it stands) on a bounded sample of the batched
+    workload: every instance with `sample_searches` searches (same W and
+    parameters), whole generations of all instances until `seconds` have
+    passed (or `gens` generations).  Returns (flips/s, generations)."""
+    from oracle import oracle as orc
+    p = orc.make_params(searches=spec["sample_searches"], pools=spec["pools"],
+                        pool_cap=spec["pool_cap"], tabu=spec["tabu"], s=spec["s"], b=spec["b"],
+                        seed_mode=spec["seed_mode"])
+    sos = [orc.Solver(W, p, seed + i) for i, W in enumerate(Ws)]
+    t0 = time.perf_counter()
+    flips, g = 0, 0
+    while True:
+        for so in sos:
+            flips += so.generation(threads)
+        g += 1
+        if (gens is not None and g >= gens) or (gens is None and time.perf_counter() - t0 >= seconds):
+            break
+    return flips / (time.perf_counter() - t0), g
+
+
+def served_trace(dabs, rate, seconds, seed, generations=20, sizes=(512, 1024, 2048, 4096, 8192),
+                 big=0, budget_gb=60, targets=None, Wcache=None):
+    """Poisson arrivals (rate per s for `seconds`, seed) of dense QUBOs with n
+    uniform in `sizes` (W ~ U[-1000, 1000], seed 5000 + i), 256 searches, a
+    flip budget of 256 x generations x n and at most `generations`
+    generations, recompute seeding; plus one n = `big` instance mid-trace.
+    With `targets` (request index -> energy), each request stops at its
+    target; latency = completion - arrival.  Returns (requests, results,
+    latencies, flips, wall seconds)."""
+    rng = np.random.default_rng(seed)
+    arr = wl.poisson_arrivals(rate, seconds, seed=seed)
+    reqs = [(float(t), int(rng.choice(sizes)), 5000 + i) for i, t in enumerate(arr)]
+    if big:
+        reqs.append((seconds / 2, big, 9999))
+        reqs.sort()
+    Wcache = {} if Wcache is None else Wcache
+    for _, n, sd in reqs:  # instances are prepared before the clock starts
+        if (n, sd) not in Wcache:
+            Wcache[(n, sd)] = wl.dense_qubo(n, -1000, 1000, seed=sd)
+    kw = dict(searches=256, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=1,
+              max_generations=generations)
+    params = dabs.default_params(**kw)
+    srv = dabs.Server(budget_gb << 30)
+    t0 = time.perf_counter()
+    tickets, i, pending = [], 0, 0
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i][0] <= now:
+            _, n, sd = reqs[i]
+            tg = None if targets is None else targets[(n, sd)]
+            tickets.append(srv.submit(Wcache[(n, sd)], params, 256 * generations * n, sd, target=tg))
+            i += 1
+        if srv.info()[1] + srv.info()[2] == 0:
+            time.sleep(0.0005)
+            pending = 0
+            continue
+        pending = srv.step(1)
+    wall = time.perf_counter() - t0
+    res, lat, fl = {}, [], 0
+    for t, (_, n, sd) in zip(tickets, reqs):
+        st, X, E, F, L = srv.poll(t)
+        res[(n, sd)] = (X.tobytes(), E, F)
+        lat.append(L)
+        fl += F
+    srv.close()
+    return reqs, res, lat, fl, wall
+
+
+def serving(dabs, seconds=2.0, rate=50.0, sweep=(5.0, 10.0, 25.0), generations=20, big=0):
+    """The served workload with per-request targets: every request's target
+    is the energy it reaches alone (computed before the clock, in batched form,
+    whose results equal the alone ones); the trace at `rate` is served with
+    continuous batching and, on the same arrivals, one request at a time (the
+    plain form); every request's (X, E, flips) must be identical in both.  The
+    same requests are also served at the `sweep` rates (p99 per rate)."""
+    Wcache = {}
+    kw = dict(searches=256, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=1,
+              max_generations=generations)
+    # the union of the requests of every trace (same seed: same instances)
+    keys = []
+    for r in (rate,) + tuple(sweep):
+        rng = np.random.default_rng(4)
+        for i, _ in enumerate(wl.poisson_arrivals(r, seconds, seed=4)):
+            keys.append((int(rng.choice((512, 1024, 2048, 4096, 8192))), 5000 + i))
+    if big:
+        keys.append((big, 9999))
+    keys = sorted(set(keys))
+    for n, sd in keys:
+        Wcache[(n, sd)] = wl.dense_qubo(n, -1000, 1000, seed=sd)
+    targets = {}
+    t0 = time.perf_counter()
+    for c0 in range(0, len(keys), 48):  # untimed: the energies each reaches alone
+        chunk = keys[c0:c0 + 48]
+        ctxs = [dabs.Context(Wcache[k], **kw) for k in chunk]
+        out = dabs.batch_solve(ctxs, [256 * generations * k[0] for k in chunk], [k[1] for k in chunk])
+        for k, o in zip(chunk, out):
+            targets[k] = o[1]
+        for c in ctxs:
+            c.close()
+    t_targets = time.perf_counter() - t0
+    progress(f"serving: {len(keys)} targets in {t_targets:.1f}s")
+    reqs, res, lat, fl, wall = served_trace(dabs, rate, seconds, 4, generations, big=big,
+                                            targets=targets, Wcache=Wcache)
+    out = {"workload": f"Poisson {rate}/s for {seconds}s (seed 4), n uniform in "
+                       f"{{512,...,8192}}" + (f" plus one n={big}" if big else "")
+                       + f", 256 searches, budget 256 x {generations} x n flips, at most "
+                         f"{generations} generations, recompute seeding",
+           "target": "the energy each request reaches alone under the same limits",
+           "requests": len(reqs), "served_p50_s": pct(lat, 50), "served_p99_s": pct(lat, 99),
+           "served_flips_per_s": fl / wall, "served_wall_s": wall,
+           "targets_precompute_s": t_targets}
+    progress(f"serving: served {len(reqs)} requests in {wall:.1f}s")
+    # plain: one request at a time on the same arrivals
+    t0 = time.perf_counter()
+    lat2, free_at, same = [], 0.0, True
+    fl2 = 0
+    for (ta, n, sd) in reqs:
+        start = max(ta, free_at)
+        now = time.perf_counter() - t0
+        if now < start:
+            time.sleep(start - now)
+        c = dabs.Context(Wcache[(n, sd)], **kw)
+        X, E, F = c.solve(256 * generations * n, seed=sd, target=targets[(n, sd)])
+        c.close()
+        free_at = time.perf_counter() - t0
+        lat2.append(free_at - ta)
+        fl2 += F
+        same = same and res[(n, sd)] == (X.tobytes(), E, F)
+    out.update({"plain_p50_s": pct(lat2, 50), "plain_p99_s": pct(lat2, 99),
+                "plain_flips_per_s": fl2 / (time.perf_counter() - t0),
+                "identical_results": bool(same)})
+    progress("serving: plain done")
+    rates = {}
+    for r in sweep:
+        rq, rs, lt, f3, w3 = served_trace(dabs, r, seconds, 4, generations, big=0,
+                                          targets=targets, Wcache=Wcache)
+        ok = all(rs[k] == res[k] for k in rs if k in res)
+        rates[str(r)] = {"requests": len(rq), "p50_s": pct(lt, 50), "p99_s": pct(lt, 99),
+                         "flips_per_s": f3 / w3, "identical_results": bool(ok)}
+    out["rate_sweep"] = rates
+    return out
+
+
+def run_batched(args, ws, rank, lrank, pg):
+    import torch
+    from paper_2207_03069_gb300 import build, dabs
+
+    build.build()
+    torch.cuda.set_device(lrank)
+    dev = torch.device("cuda", lrank)
+    spec = WORKLOADS[args.workload]
+    Ws = batched_instances(spec)
+    ns = [W.shape[0] for W in Ws]
+    kw = {k: spec[k] for k in ("searches", "pools", "pool_cap", "tabu", "s", "b", "seed_mode")}
+    seed0 = args.seed + 1000 * rank
+    seeds = [seed0 + i for i in range(len(Ws))]
+    big = [10**15] * len(Ws)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    def flips_of(ctxs):
+        return [c.solve_status()["flips"] for c in ctxs]
+
+    progress(f"batched: {len(Ws)} instances ready")
+    # ---------------- batched form: one generation of every instance per step
+    ctxs = [dabs.Context(W, **kw) for W in Ws]
+    bt = dabs.Batch(ctxs, stream)
+    bt.begin(big, seeds)
+    for _ in range(args.warmup):
+        bt.generations(1)
+    info0 = bt.info()
+    f0 = flips_of(ctxs)
+    sampler = ClockSampler(lrank)
+    sampler.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)  # untimed: evict L2 between timed steps
+        ev[k][0].record(stream)
+        bt.generations(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = sampler.stop()
+    info1 = bt.info()
+    f1 = flips_of(ctxs)
+    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    per_inst = [b - a for a, b in zip(f0, f1)]
+    flips = sum(per_inst)
+    total_s, flips_all = aggregate(pg, sum(step_ms) * 1e-3, flips)
+    value = flips_all / total_s
+    launches = info1["launches"] - info0["launches"]
+    search_ms = (info1["search_ms"] - info0["search_ms"]) / args.steps
+    best_b = [c.solve_best() for c in ctxs]
+    bt.close()
+
+    progress(f"batched: {value / 1e6:.1f} M flips/s")
+    # ---------------- plain form: the same instances, one instance per launch
+    plain = [dabs.Context(W, **kw) for W in Ws]
+    for c in plain:
+        c.set_stream(stream)
+    for c, sd in zip(plain, seeds):
+        c.solve_begin(sd, budget=10**15)
+    for _ in range(args.warmup):
+        for c in plain:
+            c.solve_generations(1)
+    torch.cuda.synchronize()
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+        pev[k][0].record(stream)
+        for c in plain:
+            c.solve_generations(1)
+        pev[k][1].record(stream)
+    torch.cuda.synchronize()
+    plain_s = sum(e[0].elapsed_time(e[1]) for e in pev) * 1e-3
+    fp = flips_of(plain)
+    best_p = [c.solve_best() for c in plain]
+    identical = all(a[1] == b[1] and np.array_equal(a[0], b[0]) for a, b in zip(best_b, best_p)) \
+        and fp == f1
+    assert identical, "batched and plain forms disagree"
+    plain_value = flips / plain_s
+    for c in plain:
+        c.close()
+    for c in ctxs:
+        c.close()
+
+    progress(f"plain: {plain_value / 1e6:.1f} M flips/s, identical={identical}")
+    # ---------------- roofline of the batch-search phase (the dominant kernel)
+    hbm, peak_kind = peaks()
+    row_bytes = sum(f * 2 * n for f, n in zip(per_inst, ns)) / args.steps  # per generation
+    achieved = row_bytes / (search_ms * 1e-3) / 1e9
+    wset = sum(4 * n * n for n in ns)  # W and -W: the rows one flip may read
+    l2_size = torch.cuda.get_device_properties(dev).L2_cache_size
+    l2 = l2_read_gbs(torch, dev)
+    bound = "hbm" if wset > l2_size else "l2"
+    peak = hbm if bound == "hbm" else l2
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * 4 * 16 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6
+    prof = search_profile("search_batched64.json")
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak,
+                "peak_kind": f"{peak_kind} HBM copy" if bound == "hbm" else "measured L2-resident read",
+                "traffic": prof.get("dram_bytes_per_generation") if prof else None,
+                "traffic_source": "profiles/search_batched64.json" if prof else None,
+                "kernel": "k_batch_search (multi-instance launches, one per variant group)",
+                "algorithmic_bytes_per_launch": row_bytes,
+                "algorithmic_bytes": "flips x 2n per flip (the int16 row of sigma(x_i) W), summed over instances",
+                "launch_ms": search_ms, "search_share_of_step": search_ms / (sum(step_ms) / args.steps),
+                "working_set_bytes": wset, "l2_bytes": l2_size,
+                "frac_of_hbm": achieved / hbm, "l2_read_gbs_measured": l2, "frac_of_l2": achieved / l2,
+                "alu": {"pipe": "ALU (integer compare/min/select/logic), 64 lanes per SM",
+                        "peak_lane_ops_per_s": alu_peak,
+                        "algorithmic_lane_ops_per_flip": "2n (Step 1 compare, Eq. (4) multiply-add)",
+                        "frac_algorithmic": sum(f * 2 * n for f, n in zip(per_inst, ns))
+                        / (sum(step_ms) * 1e-3) / alu_peak}}
+
+    # ---------------- end to end through the C ABI with host buffers
+    pinned = []
+    for W in Ws:
+        t = torch.empty(W.shape, dtype=torch.int16, pin_memory=True).numpy()
+        t[:] = W
+        pinned.append(t)
+    kw1 = dict(kw, max_generations=1)
+    e2e_ctx = [dabs.Context(W, **kw1) for W in Ws]
+    dabs.batch_solve(e2e_ctx, big, seeds)  # warm
+    e2e_steps = max(3, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_flips = 0
+    for k in range(e2e_steps):
+        for c, Wp in zip(e2e_ctx, pinned):
+            c.load_weights(Wp)  # H2D of the step's inputs
+        out = dabs.batch_solve(e2e_ctx, big, [sd + k for sd in seeds])  # best X, E back on the host
+        e2e_flips += sum(o[2] for o in out)
+    e2e_s = time.perf_counter() - t0
+    for c in e2e_ctx:
+        c.close()
+    e2e = {"value": e2e_flips / e2e_s, "unit": "flips/s",
+           "h2d_bytes_per_step": int(sum(2 * n * n for n in ns)),
+           "d2h_bytes_per_step": int(sum(n + 8 + 8 for n in ns)),
+           "call": "dabs_load_weights for all 64 instances + dabs_batch_solve (one generation) "
+                   "per step, best X/E/flips of every instance read back"}
+
+    progress("e2e done")
+    extra = {}
+    if not args.no_extra and ws == 1:
+        extra["time_to_target"] = batched_ttt(dabs, Ws, kw, seeds)
+        progress("time to target done")
+        if args.trace_seconds > 0:
+            extra["serving"] = serving(dabs, seconds=args.trace_seconds, big=args.serve_big)
+            progress("serving done")
+        rec = recompute_rate(torch, dabs, dev) if not args.no_recompute else None
+        if rec:
+            mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+            pk = json.load(open(mp))["bf16_tflops"] if os.path.exists(mp) else 1900.0
+            rec["peak_tflops"] = pk
+            rec["frac"] = rec["tensor_tflops"] / pk
+            extra["recompute_tensor"] = rec
+        extra["maxcut800"] = single_summary(dabs, torch, dev, "maxcut800", clocks)
+        progress("maxcut800 done")
+        extra["small_graphs"] = small_graphs(dabs)
+        extra["tsp_time_to_target"] = tsp_ttt(dabs, seeds=8)
+        progress("small and tsp done")
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        r, g = oracle_batched_rate(Ws, spec, seed0, args.cpu_seconds, threads)
+        cpu = {"value": r, "unit": "flips/s", "cores": threads, "kind": "oracle",
+               "sample": f"{g} generation(s) of all {len(Ws)} instances with "
+                         f"{spec['sample_searches']} searches each (same W and parameters), "
+                         f"about {args.cpu_seconds:.0f} s"}
+
+    if rank == 0:
+        line = {"metric": "bit flips/s (batched vs plain, bit-exact)", "value": value,
+                "unit": "flips/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": sum(step_ms) / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": spec["desc"], "instances": len(Ws), "n_min": min(ns),
+                           "n_max": max(ns), "searches": spec["searches"], "pools": spec["pools"],
+                           "pool_cap": spec["pool_cap"], "tabu": spec["tabu"],
+                           "s": "%d/%d" % spec["s"], "b": "%d/%d" % spec["b"],
+                           "seeding": "recompute (tensor cores)",
+                           "form": "batched: one search launch per variant group",
+                           "l2": "flushed (256 MiB write) between timed steps; W+(-W) "
+                                 f"{wset / 2**20:.0f} MiB > L2",
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "plain": {"value": plain_value, "unit": "flips/s", "speedup": value / plain_value,
+                          "identical_results": bool(identical),
+                          "form": "one instance per launch (its generation as a CUDA graph)"},
+                "delta_updates_per_s": sum(f * n for f, n in zip(per_inst, ns)) / (sum(step_ms) * 1e-3),
+                "gpu_launches": launches, "launches_per_step": launches / args.steps,
+                "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, **extra}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+
+
+def batched_ttt(dabs, Ws, kw, seeds, generations=3):
+    """Time to target, batched vs plain: every instance's target is the energy
+    it reaches alone in `generations` generations; all arrive at t = 0.  Plain:
+    one solve after another (an instance waits for those before it); batched:
+    submitted at once to the continuous-batching server.  Context set-up is
+    counted on both sides."""
+    kwg = dict(kw, max_generations=generations)
+    ctxs = [dabs.Context(W, **kwg) for W in Ws]
+    targets = [o[1] for o in dabs.batch_solve(ctxs, [10**15] * len(Ws), seeds)]
+    for c in ctxs:
+        c.close()
+    torch_sync()
+    t0 = time.perf_counter()
+    plain_ttt = []
+    for W, sd, tg in zip(Ws, seeds, targets):
+        c = dabs.Context(W, **kwg)
+        c.solve(10**15, seed=sd, target=tg)
+        c.close()
+        plain_ttt.append(time.perf_counter() - t0)
+    params = dabs.default_params(**kwg)
+    srv = dabs.Server(60 << 30)
+    tickets = [srv.submit(W, params, 10**15, sd, target=tg) for W, sd, tg in zip(Ws, seeds, targets)]
+    while srv.step(1):
+        pass
+    served, reached = [], True
+    for t, tg in zip(tickets, targets):
+        st, X, E, F, L = srv.poll(t)
+        served.append(L)
+        reached = reached and E <= tg
+    srv.close()
+    return {"target": f"the energy each instance reaches alone in {generations} generations; "
+                      f"all {len(Ws)} arrive at t = 0",
+            "plain_p50_s": pct(plain_ttt, 50), "plain_p99_s": pct(plain_ttt, 99),
+            "served_p50_s": pct(served, 50), "served_p99_s": pct(served, 99),
+            "targets_reached": bool(reached)}
+
+
+def single_summary(dabs, torch, dev, name, clocks, steps=10):
+    """One single-instance workload (autotuned, one generation per step): flips/s,
+    ns per flip and the flip kernel against the L2-resident read bandwidth."""
+    spec = WORKLOADS[name]
+    Wm = make_W(name)
+    n = Wm.shape[0]
+    kw = {k: spec[k] for k in ("searches", "pools", "pool_cap", "tabu", "s", "b", "seed_mode")}
+    ctx = dabs.Context(Wm, **kw)
+    st = torch.cuda.Stream(device=dev)
+    ctx.set_stream(st)
+    ctx.autotune(3)
+    ctx.solve_begin(1)
+    for _ in range(3):
+        ctx.solve_generations(1)
+    s0 = ctx.solve_status()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+    for k in range(steps):
+        ctx.run_stage(dabs.STAGE_OFFSPRING)
+        ev[k][0].record(st)
+        ctx.run_stage(dabs.STAGE_SEARCH)
+        ev[k][1].record(st)
+        ctx.run_stage(dabs.STAGE_MERGE)
+        ctx.run_stage(dabs.STAGE_FINALIZE)
+    torch.cuda.synchronize()
+    s1 = ctx.solve_status()
+    ms = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
+    fl = (s1["flips"] - s0["flips"]) / steps
+    l2 = l2_read_gbs(torch, dev)
+    ach = fl * 2 * n / (ms * 1e-3) / 1e9
+    out = {"workload": spec["desc"], "variant": ctx.variant_name(), "keyed": ctx.keyed()[0],
+           "search_flips_per_s": fl / (ms * 1e-3), "ns_per_flip": ms * 1e6 / fl,
+           "roofline": {"bound": "l2" if 4 * n * n < torch.cuda.get_device_properties(dev).L2_cache_size else "hbm",
+                        "achieved_gbs": ach, "l2_read_gbs_measured": l2, "frac_of_l2": ach / l2}}
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dabs", choices=["dabs", "reference"])
-    ap.add_argument("--workload", default="maxcut800", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="batched64", choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -489,7 +912,9 @@ def main():
     ap.add_argument("--no-recompute", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the TSP time-to-target, batched and serving measurements")
-    ap.add_argument("--trace-seconds", type=float, default=4.0)
+    ap.add_argument("--trace-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-big", type=int, default=0,
+                    help="add one instance of this n (e.g. 16384) mid-trace to the served workload")
     ap.add_argument("--variant", default="", help="force warps x chunks, e.g. 4x1")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -500,6 +925,9 @@ def main():
             pg.barrier()
         return
 
+    if WORKLOADS[args.workload].get("kind") == "batched":
+        run_batched(args, ws, rank, lrank, pg)
+        return
     import torch
     from paper_2207_03069_gb300 import build, dabs
 
@@ -616,7 +1044,6 @@ def main():
         extra["small_graphs"] = small_graphs(dabs)
         extra["time_to_target"] = tsp_ttt(dabs)
         extra["batched"] = batched_vs_plain(dabs)
-        extra["serving"] = serving(dabs, seconds=args.trace_seconds)
     if rec:
         mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
         pk = json.load(open(mp))["bf16_tflops"] if os.path.exists(mp) else 1900.0
