@@ -130,6 +130,13 @@ struct Batcher {
       }
       g->ctxs.push_back(c);
     }
+    // the most work first inside each launch too (longest-processing-time
+    // order): its searches' CTAs are dispatched first, so the tail of the
+    // launch is made of the shortest searches
+    for (auto& g : ng)
+      std::stable_sort(g.ctxs.begin(), g.ctxs.end(), [](const dabs_ctx* x, const dabs_ctx* y) {
+        return (double)x->S * x->n * x->n > (double)y->S * y->n * y->n;
+      });
     // reuse device tables
     for (size_t i = 0; i < ng.size(); ++i) {
       if (i < groups.size()) {

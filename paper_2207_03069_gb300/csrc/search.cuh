@@ -31,11 +31,17 @@
 
 namespace dabs {
 
-template <int NW_, int CH_, int RF_ = ROWS_DENSE, bool KEY_ = false>
+template <int NW_, int CH_, int RF_ = ROWS_DENSE, bool KEY_ = false, bool EARLY_ = false>
 struct Cfg {
   static constexpr int NW = NW_, CH = CH_;
   static constexpr int RF = RF_;               // row format (RowFormat)
   static constexpr bool KEY = KEY_;            // keyed Delta (see Searcher::run_key)
+  // Eq. (5) written by the owner while row i is in flight (Searcher::commit):
+  // single-warp searches of one instance per launch.  Launches of several
+  // instances (the batched form, whose launches share the SMs with other
+  // variants' launches) and groups of warps write it after the update
+  // (flip_after), which measured faster there.
+  static constexpr bool EARLY = EARLY_ && NW_ == 1;
   static constexpr int NT = 32 * NW;           // threads per search
   static constexpr int EPT = 8 * CH;           // bits per thread
   static constexpr int SPAN = 8 * NT;          // bits per chunk
@@ -74,7 +80,6 @@ struct SmemSearch {
   int4 red[2][C::NW];        // reduction slots (double buffered)
   int tot[C::CH][C::NW];     // per chunk, per warp candidate counts (k-th pick)
   int pick[4];               // broadcast of a pick made by one thread
-  int dflip;                 // Delta_i of the flip being made, from the owner of bit i
 };
 
 #define DABS_CASES(X)                                                                      \
@@ -132,6 +137,36 @@ struct Searcher {
   __device__ __forceinline__ static int local_p(int i) { return ((i >> 3) / NT) * 8 + (i & 7); }
   __device__ __forceinline__ uint32_t key_of(int lp) const {
     return lp < 0 ? UINT_MAX : (((uint32_t)kidx(lp) << 1) | (uint32_t)bit_at(xb, lp));
+  }
+  // value of d at a run-time position 0 <= p < EPT: a binary select tree on
+  // the bits of p (no branch, no local memory)
+  __device__ __forceinline__ int get_at(int p) const {
+    int v[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) v[q] = d[q];
+#pragma unroll
+    for (int w = 1; w < EPT; w <<= 1) {
+      const bool hi = (p & w) != 0;
+#pragma unroll
+      for (int q = 0; q < EPT; q += 2 * w) v[q] = hi ? v[q + w] : v[q];
+    }
+    return v[0];
+  }
+  // Eq. (5) at a run-time position after the row update (groups of warps,
+  // where Delta_i is known to every thread): d = v, sigma flips
+  __device__ __forceinline__ void set_flipped(int p, int v) {
+    switch (p) {
+#define DABS_SET(q)                         \
+  case q:                                   \
+    if constexpr (q < EPT) {                \
+      d[q < EPT ? q : 0] = v;               \
+      sg[q < EPT ? q : 0] = -sg[q < EPT ? q : 0]; \
+    }                                       \
+    break;
+      DABS_CASES(DABS_SET)
+#undef DABS_SET
+      default: break;
+    }
   }
   // Eq. (5) at a run-time position p (the owner of bit i = kidx(p)): reads
   // Delta_i, stores the flipped value plus corr, and flips sigma(x_i).  A
@@ -272,13 +307,16 @@ struct Searcher {
       rv[c] = off < ld ? __ldg(reinterpret_cast<const uint4*>(row + off)) : make_uint4(0, 0, 0, 0);
     }
   }
-  // Eq. (5) and x_i ^= 1, made while row i is in flight: the owner of bit i
-  // reads Delta_i from its register and stores -Delta_i raised by W_ii (in
-  // key units), because the row update that follows adds
+  // Eq. (5) and x_i ^= 1 for a single warp, made while row i is in flight:
+  // the owner of bit i reads Delta_i from its register and stores -Delta_i
+  // raised by W_ii (in key units), because the row update that follows adds
   // sigma(x_i) W_ii sigma'(x_i) = -W_ii at k = i once sigma(x_i) is flipped
-  // (sparse rows hold no diagonal entry: nothing to raise).  Returns
-  // Delta_i in every thread of the group.
+  // (sparse rows hold no diagonal entry: nothing to raise).  Returns Delta_i
+  // in every lane.  A group of warps instead knows Delta_i from its
+  // selection and writes it after the update (flip_after): a barrier behind
+  // the owner's write would keep every warp waiting for it.
   __device__ __forceinline__ int commit(int i, int xi) {
+    static_assert(C::EARLY, "single-warp searches of one instance");
     i = min(max(i, 0), n - 1);
     int di = 0;
     if (t == owner_t(i)) {
@@ -288,16 +326,18 @@ struct Searcher {
       di = flip_at(pi, i, xi, corr);
       xb[0] ^= 1u << pi;
     }
-    if constexpr (NW == 1) {
-      di = __shfl_sync(FULL, di, owner_t(i));
-    } else {
-      if (t == owner_t(i)) sm->dflip = di;
-      __syncthreads();
-      di = sm->dflip;
-    }
-    return di;
+    return __shfl_sync(FULL, di, owner_t(i));
   }
-  // Eq. (4) for every k (k = i included, see commit), E += Delta_i
+  __device__ __forceinline__ void flip_after(int i, int di, int xi) {
+    i = min(max(i, 0), n - 1);
+    if (t == owner_t(i)) {
+      const int pi = local_p(i);
+      // Eq. (5): Delta_i = -Delta_i (and x_i, in the keyed form's low bits)
+      set_flipped(pi, C::KEY ? -di * (1 << kb) + ((i << 1) | (xi ^ 1)) : -di);
+      xb[0] ^= 1u << pi;
+    }
+  }
+  // Eq. (4) for every k (k = i included: see commit and flip_after), E += Delta_i
   __device__ __forceinline__ void row_apply(const uint4 (&rv)[CH], int di) {
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -328,7 +368,7 @@ struct Searcher {
   // ------------------------------------------------------------ k-th pick
   // The ((u * count) >> 32)-th set bit of the group-wide candidate mask Cm, in
   // ascending bit order.  Returns key = (i << 1) | x_i.
-  __device__ __forceinline__ uint32_t kth(uint32_t Cm, uint32_t u) {
+  __device__ __forceinline__ uint32_t kth(uint32_t Cm, uint32_t u, int* di) {
     int cnt[CH], wt[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -370,6 +410,7 @@ struct Searcher {
         }
     }
     uint32_t key = 0;
+    int dv = 0;  // groups of warps: the pick's stored d value (see flip_after)
     if (warp == wsel) {
       int mycnt = 0;
 #pragma unroll
@@ -393,30 +434,39 @@ struct Searcher {
       if (r >= c2) { pos += 2; r -= c2; byte >>= 2; }
       if (r >= (int)(byte & 1u)) pos += 1;
       const int p = 8 * csel + pos;
-      if (mine) key = key_of(p);
+      if (mine) {
+        key = key_of(p);
+        if constexpr (!C::EARLY) dv = get_at(p);
+      }
       const unsigned bal = __ballot_sync(FULL, mine);
       const int src = bal ? __ffs(bal) - 1 : 0;
       key = __shfl_sync(FULL, key, src);
+      if constexpr (!C::EARLY) dv = __shfl_sync(FULL, dv, src);
       if constexpr (NW > 1) {
-        if (lane == 0) sm->pick[0] = (int)key;
+        if (lane == 0) { sm->pick[0] = (int)key; sm->pick[1] = dv; }
       }
     }
     if constexpr (NW > 1) {
       __syncthreads();
       key = (uint32_t)sm->pick[0];
+      dv = sm->pick[1];
     }
+    *di = dv;
     return key;
   }
 
-  // x_i of a bit chosen without a reduction (TwoNeighbor)
-  __device__ __forceinline__ int fetch_x(int i) {
+  // x_i (and, for groups of warps, the stored d value) of a bit chosen
+  // without a reduction (TwoNeighbor)
+  __device__ __forceinline__ int fetch_x(int i, int* dv) {
     const int pi = local_p(i), ot = owner_t(i);
     int x = bit_at(xb, pi) ? 1 : 0;
     if constexpr (NW == 1) {
       x = __shfl_sync(FULL, x, ot);
+      *dv = C::EARLY ? 0 : __shfl_sync(FULL, get_at(pi), ot);
     } else {
-      if (t == ot) sm->pick[3] = x;
+      if (t == ot) { sm->pick[2] = get_at(pi); sm->pick[3] = x; }
       __syncthreads();
+      *dv = sm->pick[2];
       x = sm->pick[3];
       __syncthreads();
     }
@@ -613,7 +663,7 @@ struct Searcher {
             kj = k[0];
           }
           i = it == 0 ? 0 : ((it & 1) ? (it + 1) >> 1 : (it >> 1) - 1);
-          xi = fetch_x(i);
+          xi = fetch_x(i, &di);
         } else if (ALGO == MAXMIN || ALGO == POSITIVEMIN) {
           if ((it & 31) == 0) {
             // the flips of iterations it .. it+31 are flips .. flips+31
@@ -676,7 +726,7 @@ struct Searcher {
             gminu(k);
             kj = k[0];
           }
-          const uint32_t key = kth(Cm, ukth);
+          const uint32_t key = kth(Cm, ukth, &di);
           i = (int)(key >> 1);
           xi = (int)(key & 1u);
         } else if (ALGO == CYCLICMIN) {
@@ -748,7 +798,7 @@ struct Searcher {
       uint4 rv[CH];
       row_load(i, xi, rv);
       // independent of row i: overlaps its load latency
-      di = commit(i, xi);
+      if constexpr (C::EARLY) di = commit(i, xi);
       if (phase == PH_MAIN) {
         if (ALGO != TWONEIGHBOR) tabu_push(i, tau);
         if (ALGO == RANDOMMIN && it + 1 < Tmain) {
@@ -757,6 +807,7 @@ struct Searcher {
         }
       }
       row_apply(rv, di);
+      if constexpr (!C::EARLY) flip_after(i, di, xi);
       if (phase == PH_MAIN && ++it == Tmain) {
         phase = PH_GREEDY;
         ++runs;
@@ -855,7 +906,9 @@ struct Searcher {
           gmin(v);
           mk = v[0];
           const int i = it == 0 ? 0 : ((it & 1) ? (it + 1) >> 1 : (it >> 1) - 1);
-          sk = (i << 1) | fetch_x(i);  // the low part of its key
+          int dv;
+          const int x = fetch_x(i, &dv);
+          sk = C::EARLY ? (i << 1) | x : dv;  // its key (early commit: the low part)
         } else if (ALGO == MAXMIN || ALGO == POSITIVEMIN) {
           if ((it & 31) == 0) {
             const uint4 u = draw(seed, flips + (uint32_t)lane, g, s,
@@ -911,7 +964,9 @@ struct Searcher {
             }
             ukth = u0;
           }
-          sk = (int)kth(Cm, ukth);  // the low part of its key
+          int dv;
+          const uint32_t kk = kth(Cm, ukth, &dv);
+          sk = C::EARLY ? (int)kk : dv;  // its key (early commit: the low part)
         } else if (ALGO == CYCLICMIN) {
           const uint64_t wl = (cube_of(fup) * (uint64_t)n) >> 32;
           const int wsz = (int)(wl < (uint64_t)cwin ? (uint64_t)cwin : (wl > (uint64_t)n ? (uint64_t)n : wl));
@@ -962,7 +1017,8 @@ struct Searcher {
       uint4 rv[CH];
       row_load(i, xi, rv);
       // independent of row i: overlaps its load latency
-      const int di = commit(i, xi);
+      int di = sk >> kb;  // groups of warps: from the selection
+      if constexpr (C::EARLY) di = commit(i, xi);
       if (phase == PH_MAIN) {
         if (ALGO != TWONEIGHBOR) tabu_push(i, tau);
         if (ALGO == RANDOMMIN && it + 1 < Tmain) {
@@ -971,6 +1027,7 @@ struct Searcher {
         }
       }
       row_apply(rv, di);
+      if constexpr (!C::EARLY) flip_after(i, di, xi);
       if (phase == PH_MAIN && ++it == Tmain) {
         phase = PH_GREEDY;
         ++runs;
@@ -1053,10 +1110,10 @@ struct Searcher {
 // Eight-warp variants are held to 128 registers so that two searches share an
 // SM (8x4 spills a little; measured 21% faster per flip at n = 8192 than one
 // search per SM); the others keep one CTA's worth of registers per thread.
-template <int NW, int CH, int RF, bool KEY>
+template <int NW, int CH, int RF, bool KEY, bool EARLY>
 __global__ void __launch_bounds__(Cfg<NW, CH, RF, KEY>::CTA, (NW == 8 ? 2 : 1))
     k_batch_search(const SearchArgs single, const MultiArgs multi) {
-  using C = Cfg<NW, CH, RF, KEY>;
+  using C = Cfg<NW, CH, RF, KEY, EARLY>;
   __shared__ SmemSearch<C> smem[C::SPC];
   extern __shared__ __align__(16) unsigned char dsm[];
   const int sl = threadIdx.x / C::NT;
@@ -1125,17 +1182,17 @@ __global__ void __launch_bounds__(Cfg<NW, CH, RF, KEY>::CTA, (NW == 8 ? 2 : 1))
   sr.store(a);
 }
 
-template <int NW, int CH, int RF, bool KEY = false>
+template <int NW, int CH, int RF, bool KEY = false, bool EARLY = true>
 void launch_rows(const SearchArgs& a, const MultiArgs& m, unsigned grid, cudaStream_t st) {
   size_t dyn = 0;
   if constexpr (RF != ROWS_DENSE) {
     dyn = sparse_smem_bytes(RF, a.n, a.sp_nnz, a.ld, a.spc);  // also W for ROWS_DENSE_SMEM
     // a size above the device's limit makes the launch fail (the caller reads
     // the error); the host only selects a sparse format that fits
-    cudaFuncSetAttribute(k_batch_search<NW, CH, RF, KEY>,
+    cudaFuncSetAttribute(k_batch_search<NW, CH, RF, KEY, EARLY>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   }
-  k_batch_search<NW, CH, RF, KEY><<<grid, Cfg<NW, CH, RF, KEY>::CTA, dyn, st>>>(a, m);
+  k_batch_search<NW, CH, RF, KEY, EARLY><<<grid, Cfg<NW, CH, RF, KEY>::CTA, dyn, st>>>(a, m);
 }
 
 // Launches one variant over `slots` searches of one instance (m == nullptr)
@@ -1170,8 +1227,10 @@ bool launch_variant(const SearchArgs* a, cudaStream_t st, SearchVariant* v, cons
     launch_rows<NW, CH, ROWS_SPARSE_GLOBAL>(a2, mm, grid, st);
   else if (!m && a2.key_bits > 0)
     launch_rows<NW, CH, ROWS_DENSE, true>(a2, mm, grid, st);
-  else
+  else if (!m)
     launch_rows<NW, CH, ROWS_DENSE>(a2, mm, grid, st);
+  else  // several instances per launch
+    launch_rows<NW, CH, ROWS_DENSE, false, false>(a2, mm, grid, st);
   return true;
 }
 
