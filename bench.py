@@ -180,9 +180,11 @@ def l2_read_gbs(torch, dev, mib=32, reps=400):
 
 
 def recompute_rate(torch, dabs, dev, n=4096, count=256, reps=20):
-    """Tensor-core recompute of Delta/E (tcgen05, bf16 limbs) for `count`
-    vectors of a dense n x n instance: the batched-seeding step of the batched
-    workload.  Returns timing and the tensor FLOP rate (2 limbs x 2 S n^2)."""
+    """Tensor-core recompute of Delta/E (tcgen05) for `count` vectors of a
+    dense n x n instance with W ~ U[-1000, 1000] (the batched workload's
+    weights): the batched-seeding step.  Returns timing and the rate of the
+    contraction D W in FLOP/s (2 S n^2 per call; with |W| <= 2048 the kernel
+    multiplies by W itself as one fp16 operand)."""
     W = wl.dense_qubo(n, -1000, 1000, seed=3)
     ctx = dabs.Context(W, searches=count, pools=1, pool_cap=1)
     rng = np.random.default_rng(3)
@@ -202,10 +204,12 @@ def recompute_rate(torch, dabs, dev, n=4096, count=256, reps=20):
     ev[1].record(st)
     ctx.kernel_status()
     ms = ev[0].elapsed_time(ev[1]) / reps
-    flops = 4.0 * count * n * n
+    flops = 2.0 * count * n * n
     ctx.close()
     return {"n": n, "vectors": count, "ms": ms, "tensor_tflops": flops / (ms * 1e-3) / 1e12,
-            "note": "bf16 limbs on tcgen05.mma kind::f16, exact; includes bit->bf16 expansion"}
+            "flops_per_call": flops,
+            "note": "tcgen05.mma kind::f16 (W as one fp16 operand, exact for |W| <= 2048), "
+                    "M = 256 vectors per CTA; includes the bit -> fp16 expansion kernel"}
 
 
 def pct(xs, q):

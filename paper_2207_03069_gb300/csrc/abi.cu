@@ -121,6 +121,7 @@ int upload_weights(dabs_ctx* ctx, const int16_t* W) {
   k_weights_commit<<<vec_blocks, 256, 0, st>>>(a);
   CKLAUNCH();
   ctx->w_hash_ok = false;
+  ctx->max_abs = (int)~c.nmax;
   const int64_t R = (int64_t)c.R;
   const size_t nnz_all = (size_t)c.nnz;
   // keyed Delta: |Delta_k| <= R_k = sum_j |W_kj| in every state, and a key
@@ -217,11 +218,24 @@ bool rows_ok(const dabs_ctx* ctx, const SearchVariant& v, int mode) {
 // autotuner select them where they win
 int default_rows(const dabs_ctx*) { return ROWS_DENSE; }
 
+// the tensor-core operands of the loaded W: one fp16 operand when it is
+// exact (|W_ij| <= 2048) and every partial sum stays below 2^24 in fp32
+// (n max|W_ij| < 2^24), else two bf16 limbs (allocated on first need)
 int tc_limbs(dabs_ctx* ctx) {
   const size_t total = (size_t)ctx->n_pad * ctx->n_pad;
+  const int limbs = (ctx->max_abs <= 2048 && (int64_t)ctx->n * ctx->max_abs < (1 << 24)) ? 1 : 2;
+  if (limbs == 2 && !ctx->Wlo) {
+    int rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if ((rc = dalloc(ctx, &ctx->Wlo, total)) != DABS_OK) return rc;
+    if (!make_tmap_bf16(&ctx->mapLo, ctx->Wlo, ctx->n_pad, ctx->n_pad, umma_tile_n()))
+      return fail(ctx, DABS_E_CUDA, "cuTensorMapEncodeTiled failed");
+  }
   k_limbs<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0, ctx->stream>>>(
-      ctx->W, ctx->n, ctx->ld, ctx->n_pad, ctx->Whi, ctx->Wlo);
+      ctx->W, ctx->n, ctx->ld, ctx->n_pad, limbs, ctx->Whi, ctx->Wlo);
   CKLAUNCH();
+  if (limbs != ctx->tc_limbs_n) graph_stale(ctx);
+  ctx->tc_limbs_n = limbs;
   return DABS_OK;
 }
 
@@ -234,17 +248,16 @@ int tc_setup(dabs_ctx* ctx) {
   ctx->rows_pad = (std::max(ctx->S, 1) + bm - 1) / bm * bm;
   int rc;
   if ((rc = dalloc(ctx, &ctx->Whi, (size_t)ctx->n_pad * ctx->n_pad)) != DABS_OK) return rc;
-  if ((rc = dalloc(ctx, &ctx->Wlo, (size_t)ctx->n_pad * ctx->n_pad)) != DABS_OK) return rc;
   if ((rc = dalloc(ctx, &ctx->Abf, (size_t)ctx->rows_pad * ctx->n_pad)) != DABS_OK) return rc;
   if ((rc = dalloc(ctx, &ctx->E2, (size_t)ctx->rows_pad)) != DABS_OK) return rc;
   if ((rc = dalloc(ctx, &ctx->kerr, 1)) != DABS_OK) return rc;
   CK(cudaMemsetAsync(ctx->kerr, 0, sizeof(int), ctx->stream));
   if (!make_tmap_bf16(&ctx->mapA, ctx->Abf, ctx->rows_pad, ctx->n_pad, bm) ||
-      !make_tmap_bf16(&ctx->mapHi, ctx->Whi, ctx->n_pad, ctx->n_pad, bn) ||
-      !make_tmap_bf16(&ctx->mapLo, ctx->Wlo, ctx->n_pad, ctx->n_pad, bn))
+      !make_tmap_bf16(&ctx->mapHi, ctx->Whi, ctx->n_pad, ctx->n_pad, bn))
     return fail(ctx, DABS_E_CUDA, "cuTensorMapEncodeTiled failed");
-  CK(cudaFuncSetAttribute(k_recompute_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)umma_smem_bytes()));
+  // the one-limb form's maps stand in for the unused second limb
+  ctx->mapLo = ctx->mapHi;
+  if (!umma_prepare()) return fail(ctx, DABS_E_CUDA, "tensor-core kernel set-up failed");
   if ((rc = tc_limbs(ctx)) != DABS_OK) return rc;
   ctx->tc_ready = true;
   return DABS_OK;
@@ -255,13 +268,14 @@ int tc_recompute(dabs_ctx* ctx, const uint32_t* X, int count, int64_t* E, int32_
                  int ld_delta, const DevCtrl* ctrl) {
   cudaStream_t st = ctx->stream;
   const size_t pairs = (size_t)ctx->rows_pad * (ctx->n_pad / 2);
+  const uint32_t one = ctx->tc_limbs_n == 1 ? 0x3C00u : 0x3F80u;  // 1.0 in fp16 / bf16
   k_bits_to_bf16<<<(unsigned)std::min<size_t>((pairs + 255) / 256, 4096), 256, 0, st>>>(
-      X, count, ctx->n, ctx->nw, ctx->rows_pad, ctx->n_pad, ctx->Abf, ctrl);
+      X, count, ctx->n, ctx->nw, ctx->rows_pad, ctx->n_pad, ctx->Abf, one, ctrl);
   CKSTAGE();
   CK(cudaMemsetAsync(ctx->E2, 0, sizeof(int64_t) * ctx->rows_pad, st));
   UmmaArgs u{count, ctx->n, ctx->n_pad, ctx->nw, ld_delta, X, ctx->diag, delta, ctx->E2, ctx->kerr, ctrl};
   const dim3 grid(ctx->n_pad / umma_tile_n(), (count + umma_tile_m() - 1) / umma_tile_m());
-  k_recompute_umma<<<grid, 128, umma_smem_bytes(), st>>>(ctx->mapA, ctx->mapHi, ctx->mapLo, u);
+  launch_recompute_umma(ctx->tc_limbs_n, grid, st, ctx->mapA, ctx->mapHi, ctx->mapLo, u);
   CKSTAGE();
   k_halve<<<(count + 255) / 256, 256, 0, st>>>(E, ctx->E2, count, ctrl);
   CKSTAGE();

@@ -75,6 +75,8 @@ struct dabs_ctx {
   // tensor-core recompute (tcgen05): W limbs, bf16 copy of the vectors, maps
   int recompute_mode = 0;     // 0 = CUDA cores, 1 = tensor cores
   bool tc_ready = false;
+  int tc_limbs_n = 2;         // tensor-core operand form: 1 fp16 W, 2 bf16 limbs
+  int max_abs = 32767;        // max_ij |W_ij| of the loaded W
   int n_pad = 0, rows_pad = 0;
   uint16_t* Whi = nullptr;
   uint16_t* Wlo = nullptr;

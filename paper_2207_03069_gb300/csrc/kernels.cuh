@@ -101,6 +101,7 @@ struct WCheck {
   unsigned long long low;  // lowest i * n + j with W_ij = -32768 (all ones: none)
   unsigned long long R;    // max_i sum_j |W_ij|
   unsigned long long nnz;  // off-diagonal non-zeros
+  unsigned long long nmax; // ~max_ij |W_ij| (all ones: W = 0)
 };
 
 struct WeightsArgs {

@@ -22,11 +22,15 @@ struct UmmaArgs {
 };
 
 __global__ void k_bits_to_bf16(const uint32_t* D, int count, int n, int nw, int rows_pad,
-                               int n_pad, uint16_t* A, const DevCtrl* ctrl);
-__global__ void k_limbs(const int16_t* W, int n, int ld, int n_pad, uint16_t* Whi, uint16_t* Wlo);
-__global__ void k_recompute_umma(const __grid_constant__ CUtensorMap mapA,
-                                 const __grid_constant__ CUtensorMap mapHi,
-                                 const __grid_constant__ CUtensorMap mapLo, const UmmaArgs a);
+                               int n_pad, uint16_t* A, uint32_t one, const DevCtrl* ctrl);
+__global__ void k_limbs(const int16_t* W, int n, int ld, int n_pad, int limbs, uint16_t* Whi,
+                        uint16_t* Wlo);
+// the tensor-core recompute: limbs = 1, W as one fp16 operand; 2, two bf16
+// limbs (see umma.cu).  umma_prepare sets the kernels' shared-memory limit
+// (once); false on a CUDA error.
+bool umma_prepare();
+void launch_recompute_umma(int limbs, dim3 grid, cudaStream_t st, const CUtensorMap& mapA,
+                           const CUtensorMap& mapHi, const CUtensorMap& mapLo, const UmmaArgs& a);
 __global__ void k_halve(int64_t* E, const int64_t* E2, int count, const DevCtrl* ctrl);
 
 size_t umma_smem_bytes();

@@ -28,10 +28,12 @@ __global__ void k_weights_tiles(const WeightsArgs a) {
     B[r][tx] = (i2 < n && j2 < n) ? a.Ws[(size_t)i2 * a.ld + j2] : (int16_t)0;
   }
   __syncthreads();
-  unsigned long long bad = ~0ull, low = ~0ull;
+  unsigned long long bad = ~0ull, low = ~0ull, nmax = ~0ull;
   for (int r = ty; r < 32; r += 8) {
     const int i = ti * 32 + r, j = tj * 32 + tx;
     const int16_t w = A[r][tx];
+    nmax = min(nmax, ~(unsigned long long)abs((int)w));
+    if (ti != tj) nmax = min(nmax, ~(unsigned long long)abs((int)B[r][tx]));
     if (i < n && j < n) {
       const unsigned long long at = (unsigned long long)i * n + j;
       if (w != B[tx][r]) bad = min(bad, at);
@@ -67,10 +69,12 @@ __global__ void k_weights_tiles(const WeightsArgs a) {
   for (int o = 16; o > 0; o >>= 1) {
     bad = min(bad, __shfl_xor_sync(0xffffffffu, bad, o));
     low = min(low, __shfl_xor_sync(0xffffffffu, low, o));
+    nmax = min(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
   }
   if (tx == 0) {
     if (bad != ~0ull) atomicMin(&a.chk->bad, bad);
     if (low != ~0ull) atomicMin(&a.chk->low, low);
+    if (nmax != ~0ull) atomicMin(&a.chk->nmax, nmax);
   }
 }
 

@@ -21,10 +21,17 @@ def D():
     return dabs
 
 
-@pytest.mark.parametrize("n,count", [(64, 1), (100, 5), (128, 128), (129, 130), (800, 256),
-                                     (1000, 77), (2048, 256), (4100, 200), (8192, 64)])
-def test_recompute_matches_cuda_cores_and_oracle(D, orc, n, count):
-    W = wl.dense_qubo(n, -32767, 32767, seed=n + 7)
+# wmax 32767: two bf16 limbs; 2048 and 1000: W itself as one fp16 operand
+# (exact for |W| <= 2048 with n |W| < 2^24); 2049 just past that bound
+@pytest.mark.parametrize("n,count,wmax", [(64, 1, 32767), (100, 5, 32767), (128, 128, 32767),
+                                          (129, 130, 32767), (800, 256, 32767),
+                                          (1000, 77, 32767), (2048, 256, 32767),
+                                          (4100, 200, 32767), (8192, 64, 32767),
+                                          (300, 300, 1000), (4096, 256, 1000), (8191, 260, 2048),
+                                          (700, 129, 2049), (16384, 40, 1000)])
+def test_recompute_matches_cuda_cores_and_oracle(D, orc, n, count, wmax):
+    W = wl.dense_qubo(n, -wmax, wmax, seed=n + 7)
+    W[0, 0] = wmax  # the bound itself occurs
     ctx = D.Context(W, searches=max(count, 1), pools=1, pool_cap=1)
     rng = np.random.default_rng(n)
     dens = rng.random((count, 1))
