@@ -54,6 +54,25 @@ struct Batcher {
   // after the first, forked from and joined back into `stream`
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;  // ev[0] fork, ev[1 + g] join of side stream g
+  // the fused generation (every instance's offspring in one launch, the
+  // recompute of all instances in one launch, the variant groups' searches,
+  // every instance's merge and finalise in one launch), replayed from a CUDA
+  // graph; used when no instance restarts its pools and every recompute runs
+  // on the tensor cores
+  bool fused = false;
+  BatchInst* d_binst = nullptr;
+  int32_t* d_post_prefix = nullptr;
+  RecInst* d_rec = nullptr;
+  int32_t* d_rec_prefix = nullptr;
+  uint32_t* d_merged = nullptr;
+  int fcap = 0;
+  int nrec = 0, rec_ctas = 0, post_ctas = 0;
+  size_t post_smem = 0;
+  // the fused generation as three captured graphs (before the searches, the
+  // searches, after them), so that the search phase can be timed by events
+  // recorded on the stream between them
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+  bool use_graph = true;
   // measurement: kernels launched by generation() (all instances), and the
   // device time of the batch-search phase (fork to join) of each generation
   uint64_t search_launches = 0;
@@ -68,6 +87,13 @@ struct Batcher {
       cudaFree(g.d_insts);
       cudaFree(g.d_prefix);
     }
+    for (cudaGraphExec_t& g : gexec)
+      if (g) cudaGraphExecDestroy(g);
+    cudaFree(d_binst);
+    cudaFree(d_post_prefix);
+    cudaFree(d_rec);
+    cudaFree(d_rec_prefix);
+    cudaFree(d_merged);
     if (h_insts) cudaFreeHost(h_insts);
     if (h_prefix) cudaFreeHost(h_prefix);
     for (cudaStream_t s : side) cudaStreamDestroy(s);
@@ -161,6 +187,16 @@ struct Batcher {
     });
     groups.swap(ng);
     if (groups.size() > 1 && (rc = ensure_side(groups.size() - 1))) return rc;
+    for (cudaGraphExec_t& g : gexec)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+    fused = !active.empty();
+    for (const dabs_ctx* c : active)
+      fused = fused && c->p.restart == 0 &&
+              (c->p.seed_mode == 0 || (c->recompute_mode == 1 && c->tc_ready));
+    if (fused && (rc = fused_tables())) return rc;
     int need = 1;
     for (auto& g : groups) need = std::max<int>(need, (int)g.ctxs.size());
     if (need > h_cap) {
@@ -186,6 +222,7 @@ struct Batcher {
       int acc = 0;
       for (int i = 0; i < k; ++i) {
         h_insts[i] = solve_search_args(g.ctxs[i]);
+        if (fused && g.ctxs[i]->p.seed_mode == 1) h_insts[i].E2 = g.ctxs[i]->E2;
         h_prefix[i] = acc;
         acc += g.ctxs[i]->S;
       }
@@ -201,18 +238,192 @@ struct Batcher {
     return DABS_OK;
   }
 
+  // device tables of the fused generation for `active`
+  int fused_tables() {
+    int rc;
+    const int k = (int)active.size();
+    if (k > fcap) {
+      cudaFree(d_binst);
+      cudaFree(d_post_prefix);
+      cudaFree(d_rec);
+      cudaFree(d_rec_prefix);
+      cudaFree(d_merged);
+      d_binst = nullptr;
+      d_post_prefix = d_rec_prefix = nullptr;
+      d_rec = nullptr;
+      d_merged = nullptr;
+      fcap = 0;
+      if ((rc = check(cudaMalloc(&d_binst, sizeof(BatchInst) * k)))) return rc;
+      if ((rc = check(cudaMalloc(&d_post_prefix, sizeof(int32_t) * (k + 1))))) return rc;
+      if ((rc = check(cudaMalloc(&d_rec, sizeof(RecInst) * k)))) return rc;
+      if ((rc = check(cudaMalloc(&d_rec_prefix, sizeof(int32_t) * (k + 1))))) return rc;
+      if ((rc = check(cudaMalloc(&d_merged, sizeof(uint32_t) * k)))) return rc;
+      fcap = k;
+    }
+    std::vector<BatchInst> hb(k);
+    std::vector<int32_t> hpp(k + 1), hrp(k + 1);
+    std::vector<RecInst> hr;
+    int acc = 0, racc = 0;
+    post_smem = 0;
+    for (int i = 0; i < k; ++i) {
+      dabs_ctx* c = active[i];
+      BatchInst& b = hb[i];
+      b = BatchInst{};
+      OffArgs& o = b.off;
+      o.n = c->n; o.nw = c->nw; o.S = c->S; o.P = c->P; o.C = c->C; o.ctrl = c->ctrl;
+      for (int q = 0; q < 2; ++q) { o.pool_X[q] = c->poolX[q]; o.pool_algo[q] = c->poolA[q]; o.pool_op[q] = c->poolO[q]; }
+      o.D = c->D; o.algo = c->algo; o.op = c->op; o.abs_mode = c->p.abs_mode;
+      MergeArgs& m = b.merge;
+      m.nw = c->nw; m.S = c->S; m.P = c->P; m.C = c->C; m.Mmax = c->Mmax; m.ctrl = c->ctrl;
+      for (int q = 0; q < 2; ++q) { m.pool_X[q] = c->poolX[q]; m.pool_E[q] = c->poolE[q]; m.pool_algo[q] = c->poolA[q]; m.pool_op[q] = c->poolO[q]; }
+      m.best_X = c->bestX; m.best_E = c->bestE; m.algo = c->algo; m.op = c->op;
+      b.fin = FinArgs{c->nw, c->S, c->ctrl, c->bestX, c->bestE, c->flips, c->gbestX,
+                      c->algo, c->op, c->stats, nullptr};
+      b.order = c->order;
+      b.seed_mode = c->p.seed_mode;
+      b.X = c->X;
+      b.merged = d_merged + i;
+      hpp[i] = acc;
+      acc += c->P;
+      post_smem = std::max(post_smem, c->merge_smem);
+      if (c->p.seed_mode == 1) {
+        b.A = c->Abf;
+        b.rows_pad = c->rows_pad;
+        b.n_pad = c->n_pad;
+        b.one = c->tc_limbs_n == 1 ? 0x3C00u : 0x3F80u;
+        b.E2 = c->E2;
+        RecInst r{};
+        r.mapA = c->mapA;
+        r.mapHi = c->mapHi;
+        r.mapLo = c->mapLo;
+        r.a = UmmaArgs{c->S, c->n, c->n_pad, c->nw, c->ld, c->D, c->diag, c->delta, c->E2,
+                       c->kerr, c->ctrl};
+        r.limbs = c->tc_limbs_n;
+        r.tiles_n = c->n_pad / umma_tile_n();
+        hrp[hr.size()] = racc;
+        racc += r.tiles_n * ((c->rows_pad + umma_tile_m() - 1) / umma_tile_m());
+        hr.push_back(r);
+      }
+    }
+    hpp[k] = acc;
+    post_ctas = acc;
+    nrec = (int)hr.size();
+    hrp[nrec] = racc;
+    rec_ctas = racc;
+    if ((rc = check(cudaMemcpyAsync(d_binst, hb.data(), sizeof(BatchInst) * k, cudaMemcpyHostToDevice, stream))))
+      return rc;
+    if ((rc = check(cudaMemcpyAsync(d_post_prefix, hpp.data(), sizeof(int32_t) * (k + 1), cudaMemcpyHostToDevice, stream))))
+      return rc;
+    if (nrec > 0) {
+      if ((rc = check(cudaMemcpyAsync(d_rec, hr.data(), sizeof(RecInst) * nrec, cudaMemcpyHostToDevice, stream))))
+        return rc;
+      if ((rc = check(cudaMemcpyAsync(d_rec_prefix, hrp.data(), sizeof(int32_t) * (nrec + 1), cudaMemcpyHostToDevice, stream))))
+        return rc;
+    }
+    if ((rc = check(cudaMemsetAsync(d_merged, 0, sizeof(uint32_t) * k, stream)))) return rc;
+    if (post_smem > 48 * 1024 &&
+        (rc = check(cudaFuncSetAttribute(k_gen_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)post_smem))))
+      return rc;
+    // the host vectors are freed on return: wait for the copies
+    return check(cudaStreamSynchronize(stream));
+  }
+
+  // the variant groups' batch-search launches, concurrently on side streams
+  int searches() {
+    int rc;
+    const size_t G = groups.size();
+    if (G > 1 && (rc = check(cudaEventRecord(ev[0], stream)))) return rc;
+    for (size_t gi = 0; gi < G; ++gi) {
+      const Group& g = groups[gi];
+      cudaStream_t st = gi == 0 ? stream : side[gi - 1];
+      if (gi > 0 && (rc = check(cudaStreamWaitEvent(st, ev[0], 0)))) return rc;
+      int32_t max_n = 0;
+      for (const dabs_ctx* c : g.ctxs) max_n = std::max(max_n, (int32_t)c->n);
+      const MultiArgs m{g.d_insts, g.d_prefix, (int32_t)g.ctxs.size(), g.total, max_n};
+      const SearchArgs first = solve_search_args(g.ctxs[0]);
+      if (!launch_search(g.var.nw, g.var.ch, &first, st, nullptr, &m)) return DABS_E_INVALID_ARG;
+      if ((rc = check(cudaGetLastError()))) return rc;
+      if (gi > 0 && (rc = check(cudaEventRecord(ev[gi], st)))) return rc;
+    }
+    for (size_t gi = 1; gi < G; ++gi)
+      if ((rc = check(cudaStreamWaitEvent(stream, ev[gi], 0)))) return rc;
+    return DABS_OK;
+  }
+
+  // the kernels of one part of the fused generation on `stream` (also used
+  // for capture): 0 offspring and recompute, 1 the searches, 2 merge and
+  // finalise
+  int fused_part(int part) {
+    int rc;
+    if (part == 0) {
+      k_gen_pre<<<(unsigned)active.size(), 1024, 0, stream>>>(d_binst);
+      if ((rc = check(cudaGetLastError()))) return rc;
+      if (nrec > 0) {
+        launch_recompute_multi(d_rec, d_rec_prefix, nrec, rec_ctas, stream);
+        if ((rc = check(cudaGetLastError()))) return rc;
+      }
+      return DABS_OK;
+    }
+    if (part == 1) return searches();
+    k_gen_post<<<(unsigned)post_ctas, kMergeThreads, post_smem, stream>>>(d_binst, d_post_prefix,
+                                                                         (int)active.size());
+    return check(cudaGetLastError());
+  }
+
+  int capture(int part) {
+    int rc = check(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    if (rc) return rc;
+    rc = fused_part(part);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(stream, &gr);
+    if (!rc && e == cudaSuccess) rc = check(cudaGraphInstantiate(&gexec[part], gr, 0));
+    else if (!rc) rc = check(e);
+    if (gr) cudaGraphDestroy(gr);
+    if (rc) {
+      cudaGetLastError();
+      gexec[part] = nullptr;
+    }
+    return rc;
+  }
+
+  int generation_fused() {
+    int rc;
+    for (int part = 0; part < 3 && use_graph; ++part)
+      if (!gexec[part] && (rc = capture(part))) return rc;
+    while (t_ev.size() < t_used + 2) {
+      cudaEvent_t e;
+      if ((rc = check(cudaEventCreate(&e)))) return rc;
+      t_ev.push_back(e);
+    }
+    cudaEvent_t t0 = t_ev[t_used], t1 = t_ev[t_used + 1];
+    t_used += 2;
+    for (int part = 0; part < 3; ++part) {
+      if (part == 1 && (rc = check(cudaEventRecord(t0, stream)))) return rc;
+      rc = use_graph ? check(cudaGraphLaunch(gexec[part], stream)) : fused_part(part);
+      if (rc) return rc;
+      if (part == 1 && (rc = check(cudaEventRecord(t1, stream)))) return rc;
+    }
+    search_launches += groups.size();
+    launches_fused += 2 + (nrec > 0 ? 1 : 0);
+    return DABS_OK;
+  }
+
   // adds the search phases timed since the last call (the stream must have
   // been synchronised)
   void collect_search_time() {
     for (size_t i = 0; i + 1 < t_used; i += 2) {
       float ms = 0;
       if (cudaEventElapsedTime(&ms, t_ev[i], t_ev[i + 1]) == cudaSuccess) search_ms += ms;
+      else cudaGetLastError();  // a pair never recorded (a failed generation): no error left behind
     }
     t_used = 0;
   }
 
+  uint64_t launches_fused = 0;  // the fused generation's non-search kernels
+
   // one generation of every active context
   int generation() {
+    if (fused) return generation_fused();
     int rc;
     for (dabs_ctx* c : active)
       if ((rc = stage(c, 0)) || (rc = stage(c, 4))) return rc;
@@ -355,7 +566,7 @@ extern "C" int dabs_batch_info(dabs_batch* bt, int32_t* running, int32_t* search
   const int rc = bt->b.sync_all();
   if (rc) return rc;
   bt->b.collect_search_time();
-  uint64_t l = bt->b.search_launches;
+  uint64_t l = bt->b.search_launches + bt->b.launches_fused;
   for (size_t i = 0; i < bt->all.size(); ++i) l += bt->all[i]->launches - bt->launches0[i];
   if (running) *running = (int32_t)bt->b.active.size();
   if (search_groups) *search_groups = (int32_t)bt->b.groups.size();

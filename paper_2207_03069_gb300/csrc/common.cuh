@@ -111,6 +111,7 @@ struct SearchArgs {
   uint32_t* X;       // [S][nw]  persistent state
   int32_t* delta;    // [S][ld]
   int64_t* E;        // [S]
+  const int64_t* E2;  // [S] or null: 2 E from the batched recompute (E = E2 / 2 at the start)
   const uint32_t* D; // [S][nw]  targets
   const uint8_t* algo; // [S]
   uint32_t* best_X;  // [S][nw]

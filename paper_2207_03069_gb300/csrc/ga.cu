@@ -104,12 +104,9 @@ __device__ __forceinline__ uint32_t interval_mask(int w, int lo, int hi) {
   return m << (a0 - 32 * w);
 }
 
-__global__ void k_offspring(const OffArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (s >= a.S) return;
+// the target, algorithm and operation of search s (one warp)
+__device__ void offspring_one(const OffArgs& a, int s, int lane) {
   const DevCtrl* ctrl = a.ctrl;
-  if (ctrl->done) return;
   const uint32_t g = ctrl->g;
   const uint64_t seed = ctrl->seed;
   const int cur = g & 1;
@@ -175,6 +172,14 @@ __global__ void k_offspring(const OffArgs a) {
   }
 }
 
+__global__ void k_offspring(const OffArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (s >= a.S) return;
+  if (a.ctrl->done) return;
+  offspring_one(a, s, lane);
+}
+
 // ---------------------------------------------------------------- merge
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -204,11 +209,8 @@ constexpr int64_t kEnergyBias = (int64_t)1 << 46;  // |E| < 2^46 for n <= 65536,
 // equal energies; worst dropped) equals: the first C of the union of the old
 // entries (first) and the new results (in search order), stably sorted by
 // energy, after dropping later copies of an equal (E, X).
-__global__ void __launch_bounds__(kMergeThreads) k_merge(const MergeArgs a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+__device__ void merge_pool(const MergeArgs& a, int p, unsigned char* smraw) {
   const DevCtrl* ctrl = a.ctrl;
-  if (ctrl->done) return;
-  const int p = blockIdx.x;
   const uint32_t g = ctrl->g;
   const int cur = g & 1, nxt = cur ^ 1;
   const int C = a.C, P = a.P, nw = a.nw;
@@ -334,10 +336,15 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const MergeArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(kMergeThreads) k_merge(const MergeArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (a.ctrl->done) return;
+  merge_pool(a, blockIdx.x, smraw);
+}
+
 // ---------------------------------------------------------------- finalize
-__global__ void __launch_bounds__(1024) k_finalize(const FinArgs a) {
+__device__ void finalize_one(const FinArgs& a) {
   DevCtrl* ctrl = a.ctrl;
-  if (ctrl->done) return;
   __shared__ uint64_t sflips[32];
   __shared__ int64_t sbestE[32];
   __shared__ int sbestS[32];
@@ -401,6 +408,11 @@ __global__ void __launch_bounds__(1024) k_finalize(const FinArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(1024) k_finalize(const FinArgs a) {
+  if (a.ctrl->done) return;
+  finalize_one(a);
+}
+
 // ---------------------------------------------------------------- energy / Delta
 // Eq. (2) and Eq. (3) for `count` packed vectors: thread k accumulates the
 // column sums of W over the set bits j < k and j > k; E adds, per set bit k,
@@ -448,12 +460,16 @@ __global__ void __launch_bounds__(256) k_energy_delta(const EDArgs a) {
 // Launch order of the search slots grouped by main algorithm (any order inside
 // a group: it only decides which CTA runs which search, never a result).
 __global__ void __launch_bounds__(1024) k_order_by_algo(const uint8_t* algo, int S, int32_t* order,
-                                                        const DevCtrl* ctrl) {
+                                                        const DevCtrl* ctrl, int mod, int lo, int hi) {
   if (ctrl && ctrl->done) return;
   __shared__ int cnt[N_ALGOS], off[N_ALGOS];
   if (threadIdx.x < N_ALGOS) cnt[threadIdx.x] = 0;
   __syncthreads();
-  for (int s = threadIdx.x; s < S; s += blockDim.x) atomicAdd(&cnt[min((int)algo[s], N_ALGOS - 1)], 1);
+  // with mod > 0 only the slots s with lo <= s mod mod < hi are listed (the
+  // searches of this context's islands when a solve is split over devices)
+  auto listed = [&](int s) { return mod <= 0 || (s % mod >= lo && s % mod < hi); };
+  for (int s = threadIdx.x; s < S; s += blockDim.x)
+    if (listed(s)) atomicAdd(&cnt[min((int)algo[s], N_ALGOS - 1)], 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     int acc = 0;
@@ -461,7 +477,7 @@ __global__ void __launch_bounds__(1024) k_order_by_algo(const uint8_t* algo, int
   }
   __syncthreads();
   for (int s = threadIdx.x; s < S; s += blockDim.x)
-    order[atomicAdd(&off[min((int)algo[s], N_ALGOS - 1)], 1)] = s;
+    if (listed(s)) order[atomicAdd(&off[min((int)algo[s], N_ALGOS - 1)], 1)] = s;
 }
 
 // X <- D and Delta, E from scratch for every search slot (recompute seeding);
@@ -475,6 +491,81 @@ __global__ void k_copy_targets(const uint32_t* D, uint32_t* X, int64_t* E, size_
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)S;
        q += (size_t)gridDim.x * blockDim.x)
     E[q] = 0;
+}
+
+
+// ---------------------------------------------------------------- batched generation
+// The batched form's generation with one launch per stage for every instance
+// (Sections III-B and IV per instance): k_gen_pre breeds the targets and
+// orders the slots of all instances (one CTA each) and prepares their
+// recompute; k_gen_post merges the results into the pools (one CTA per pool)
+// and finalises each instance in the last of its merge CTAs.  Each instance
+// reads and writes only its own buffers and control block, so its results are
+// those of its generations alone.
+
+__global__ void __launch_bounds__(1024) k_gen_pre(const BatchInst* insts) {
+  const BatchInst& b = insts[blockIdx.x];
+  const OffArgs& o = b.off;
+  if (o.ctrl->done) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int s = wid; s < o.S; s += nwarps) offspring_one(o, s, lane);
+  __syncthreads();
+  // launch order of the slots grouped by main algorithm (which CTA runs which
+  // search; never a result)
+  __shared__ int cnt[N_ALGOS], off[N_ALGOS];
+  if (threadIdx.x < N_ALGOS) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < o.S; s += blockDim.x) atomicAdd(&cnt[min((int)o.algo[s], N_ALGOS - 1)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int q = 0; q < N_ALGOS; ++q) { off[q] = acc; acc += cnt[q]; }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < o.S; s += blockDim.x)
+    b.order[atomicAdd(&off[min((int)o.algo[s], N_ALGOS - 1)], 1)] = s;
+  if (b.seed_mode != 1) return;
+  // recompute seeding: X = D, the 0/1 operand of the tensor-core recompute
+  // (zero rows past S, zero columns past n) and its energy accumulators
+  const size_t words = (size_t)o.S * o.nw;
+  for (size_t q = threadIdx.x; q < words; q += blockDim.x) b.X[q] = o.D[q];
+  for (int r = threadIdx.x; r < b.rows_pad; r += blockDim.x) b.E2[r] = 0;
+  const int half = b.n_pad / 2;
+  const size_t pairs = (size_t)b.rows_pad * half;
+  for (size_t q = threadIdx.x; q < pairs; q += blockDim.x) {
+    const int r = (int)(q / half), k = 2 * (int)(q % half);
+    uint32_t v = 0;
+    if (r < o.S && k < o.n) {
+      const uint32_t w = o.D[(size_t)r * o.nw + (k >> 5)];
+      const uint32_t b0 = (w >> (k & 31)) & 1u, b1 = (k + 1 < o.n) ? ((w >> ((k + 1) & 31)) & 1u) : 0u;
+      v = (b0 ? b.one : 0u) | ((b1 ? b.one : 0u) << 16);
+    }
+    reinterpret_cast<uint32_t*>(b.A)[q] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kMergeThreads) k_gen_post(const BatchInst* insts,
+                                                            const int32_t* prefix, int ninst) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int cta = blockIdx.x;
+  int lo = 0, hi = ninst;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= cta) lo = mid; else hi = mid;
+  }
+  const BatchInst& b = insts[lo];
+  if (b.merge.ctrl->done) return;
+  merge_pool(b.merge, cta - prefix[lo], smraw);
+  // the last merge CTA of the instance finalises it (after all its pools)
+  __shared__ unsigned last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(b.merged, 1u) == (unsigned)b.merge.P - 1u;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  finalize_one(b.fin);
+  if (threadIdx.x == 0) *b.merged = 0;
 }
 
 }  // namespace dabs

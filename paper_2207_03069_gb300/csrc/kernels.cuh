@@ -118,6 +118,27 @@ struct WeightsArgs {
   uint32_t* ent;      // sparse entries written by k_sparse_fill
 };
 
+// ---- the batched form's fused generation (ga.cu): one entry per instance
+struct BatchInst {
+  OffArgs off;          // offspring (its ctrl is the instance's control block)
+  MergeArgs merge;      // pool merge
+  FinArgs fin;          // finalise
+  int32_t* order;       // [S] launch order grouped by algorithm
+  int seed_mode;        // 1: X = D, Delta and E recomputed on the tensor cores
+  uint32_t* X;          // [S][nw]
+  uint16_t* A;          // [rows_pad][n_pad] 16-bit 0/1 operand of the recompute
+  int rows_pad, n_pad;
+  uint32_t one;         // 1.0 in the operand's encoding
+  int64_t* E2;          // [rows_pad] 2 E accumulated by the recompute
+  uint32_t* merged;     // merge CTAs of this instance done in this generation
+};
+// offspring + launch order (+ X = D, the recompute operand, E2 = 0): one CTA
+// of 1024 threads per instance
+__global__ void k_gen_pre(const BatchInst* insts);
+// pool merge, one CTA per pool (kMergeThreads threads); the last CTA of an
+// instance to finish runs its finalisation.  prefix[i]: first CTA of instance i
+__global__ void k_gen_post(const BatchInst* insts, const int32_t* prefix, int ninst);
+
 __global__ void k_weights_tiles(const WeightsArgs a);
 __global__ void k_weights_rows(const WeightsArgs a);
 __global__ void k_weights_commit(const WeightsArgs a);
@@ -128,9 +149,13 @@ __global__ void k_state_init(const StateArgs a);
 __global__ void k_offspring(const OffArgs a);
 __global__ void k_merge(const MergeArgs a);
 __global__ void k_finalize(const FinArgs a);
+__device__ void offspring_one(const OffArgs& a, int s, int lane);
+__device__ void merge_pool(const MergeArgs& a, int p, unsigned char* smraw);
+__device__ void finalize_one(const FinArgs& a);
 __global__ void k_restart_check(const RestartArgs a);
 __global__ void k_energy_delta(const EDArgs a);
-__global__ void k_order_by_algo(const uint8_t* algo, int S, int32_t* order, const DevCtrl* ctrl);
+__global__ void k_order_by_algo(const uint8_t* algo, int S, int32_t* order, const DevCtrl* ctrl,
+                                int mod, int lo, int hi);
 __global__ void k_copy_targets(const uint32_t* D, uint32_t* X, int64_t* E, size_t words, int S,
                                const DevCtrl* ctrl);
 

@@ -1072,7 +1072,7 @@ struct Searcher {
         }
       }
     }
-    E = a.E[s];
+    E = a.E2 ? a.E2[s] / 2 : a.E[s];
     Ebest = INT64_MAX;
     flips = 0;
   }

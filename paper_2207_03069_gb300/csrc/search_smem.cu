@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(32) k_batch_search_smem(const SearchArgs singl
     sr.dS[lane * sr.LP + e] = valid ? dl[k] : kSent;
     sr.sS[lane * sr.LP + e] = valid ? (xb ? 1 : -1) : 0;
   }
-  sr.E = a.E[s];
+  sr.E = a.E2 ? a.E2[s] / 2 : a.E[s];
   sr.Ebest = INT64_MAX;
   sr.flips = 0;
   __syncwarp();

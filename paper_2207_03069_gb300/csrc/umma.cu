@@ -177,13 +177,14 @@ __global__ void k_limbs(const int16_t* W, int n, int ld, int n_pad, int limbs, u
 // F of one accumulator element (fp32 holding an exact integer)
 __device__ __forceinline__ int fint(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
 
+// one 256 x 64 output tile (n_tile, m_tile) of one instance; the tensor maps
+// may live in kernel parameters or in global memory
 template <int LIMBS>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_recompute_umma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapHi,
-                     const __grid_constant__ CUtensorMap mapLo, const UmmaArgs a) {
+__device__ __forceinline__ void recompute_tile(const CUtensorMap* pA, const CUtensorMap* pHi,
+                                               const CUtensorMap* pLo, const UmmaArgs& a,
+                                               int n_tile, int m_tile, unsigned char* smraw) {
   constexpr uint32_t STAGE_BYTES = A_BYTES + LIMBS * B_BYTES;
   constexpr uint32_t TMEM_COLS = LIMBS * 2 * BN;  // accumulator (limb l, half h) at (2l + h) BN
-  extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // 1024-byte aligned operand ring
   const uint32_t base = (smem_u32(smraw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int n0 = n_tile * BN, m0 = m_tile * BM;
   const int KB = a.n_pad / BK;
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -227,9 +228,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const uint32_t s0 = base + st * STAGE_BYTES;
         mbar_expect_tx(&full[st], STAGE_BYTES);
-        tma_load_2d(s0, &mapA, kb * BK, m0, &full[st]);
-        tma_load_2d(s0 + A_BYTES, &mapHi, kb * BK, n0, &full[st]);
-        if constexpr (LIMBS == 2) tma_load_2d(s0 + A_BYTES + B_BYTES, &mapLo, kb * BK, n0, &full[st]);
+        tma_load_2d(s0, pA, kb * BK, m0, &full[st]);
+        tma_load_2d(s0 + A_BYTES, pHi, kb * BK, n0, &full[st]);
+        if constexpr (LIMBS == 2) tma_load_2d(s0 + A_BYTES + B_BYTES, pLo, kb * BK, n0, &full[st]);
         ++issued;
       }
       if (abort_flag) {  // let the copies in flight land before the CTA leaves (bounded)
@@ -344,11 +345,45 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(TMEM_COLS) : "memory");
 }
 
+template <int LIMBS>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_recompute_umma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapHi,
+                     const __grid_constant__ CUtensorMap mapLo, const UmmaArgs a) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  recompute_tile<LIMBS>(&mapA, &mapHi, &mapLo, a, blockIdx.x, blockIdx.y, smraw);
+}
+
+// every instance's tiles in one launch: CTA q belongs to the instance i with
+// prefix[i] <= q < prefix[i+1]
+__global__ void __launch_bounds__(kThreads, 1)
+    k_recompute_multi(const RecInst* insts, const int32_t* prefix, int ninst) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  const int cta = blockIdx.x;
+  int lo = 0, hi = ninst;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= cta) lo = mid; else hi = mid;
+  }
+  const RecInst& r = insts[lo];
+  const int local = cta - prefix[lo];
+  if (r.limbs == 1)
+    recompute_tile<1>(&r.mapA, &r.mapHi, &r.mapLo, r.a, local % r.tiles_n, local / r.tiles_n, smraw);
+  else
+    recompute_tile<2>(&r.mapA, &r.mapHi, &r.mapLo, r.a, local % r.tiles_n, local / r.tiles_n, smraw);
+}
+
+void launch_recompute_multi(const RecInst* insts, const int32_t* prefix, int ninst, int ctas,
+                            cudaStream_t st) {
+  k_recompute_multi<<<ctas, kThreads, umma_smem_bytes(), st>>>(insts, prefix, ninst);
+}
+
 bool umma_prepare() {
   const int bytes = (int)umma_smem_bytes();
   return cudaFuncSetAttribute(k_recompute_umma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
              cudaSuccess &&
          cudaFuncSetAttribute(k_recompute_umma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(k_recompute_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
              cudaSuccess;
 }
 
