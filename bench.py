@@ -170,8 +170,8 @@ def l2_copy_gbs(torch, dev):
     return 2 * a.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
 
 
-def l2_read_gbs(torch, dev, mib=32, reps=400):
-    """Read bandwidth of a buffer that stays in L2 (32 MiB of the 129 MB L2),
+def l2_read_gbs(torch, dev, mib=64, reps=20):
+    """Read bandwidth of a buffer that stays in L2 (64 MiB of the 129 MB L2),
     measured by the library's read kernel (dabs_measure_read_gbs): the L2 peak
     the flip kernel's row reads are compared with when W fits the L2."""
     from paper_2207_03069_gb300 import dabs

@@ -393,6 +393,14 @@ int dabs_write_results(dabs_ctx* ctx, const uint32_t* best_X, const int64_t* bes
  * seed_mode = 1), 1 batch search, 2 pool merge, 3 finalise (advances the
  * generation).  Asynchronous. */
 int dabs_run_stage(dabs_ctx* ctx, int32_t stage);
+/* A solve split over devices by island (Section IV-B: the solution pools
+ * are islands; search s breeds from island s mod P): stage 1 then runs only
+ * the searches s with lo <= s mod modulus < hi (modulus = P for whole
+ * islands); the other slots' results are written by dabs_write_results
+ * before the merge (paper_2207_03069_gb300/islands.py exchanges them).
+ * modulus = 0 runs every search (the default).  Applies to dabs_run_stage
+ * only; INVALID_ARG unless 0 <= lo < hi <= modulus. */
+int dabs_set_search_slots(dabs_ctx* ctx, int32_t modulus, int32_t lo, int32_t hi);
 
 #ifdef __cplusplus
 }

@@ -327,10 +327,16 @@ int stage(dabs_ctx* ctx, int which) {
       }
     }
   } else if (which == 1 || which == 4) {
-    k_order_by_algo<<<1, 1024, 0, st>>>(ctx->algo, ctx->S, ctx->order, ctx->ctrl);
+    const bool split = which == 1 && ctx->slot_mod > 0;
+    k_order_by_algo<<<1, 1024, 0, st>>>(ctx->algo, ctx->S, ctx->order, ctx->ctrl,
+                                        split ? ctx->slot_mod : 0, ctx->slot_lo, ctx->slot_hi);
     CKSTAGE();
     if (which == 4) return DABS_OK;  // launch order only (batched search follows)
-    const SearchArgs a = solve_search_args(ctx);
+    SearchArgs a = solve_search_args(ctx);
+    if (split) {
+      if (ctx->slot_count == 0) return DABS_OK;
+      a.S = ctx->slot_count;  // the listed slots only
+    }
     if (!launch_search(ctx->var.nw, ctx->var.ch, &a, st, nullptr))
       return fail(ctx, DABS_E_INVALID_ARG, "no batch-search variant %d/%d", ctx->var.nw, ctx->var.ch);
     CKSTAGE();
@@ -761,7 +767,7 @@ int dabs_bulk_search_dev(dabs_ctx* ctx, uint64_t seed, uint32_t g, int32_t count
   a.ctrl = ctx->bulk_ctrl;
   a.order = nullptr;
   if (count <= ctx->S) {
-    k_order_by_algo<<<1, 1024, 0, ctx->stream>>>(algo, count, ctx->order, ctx->bulk_ctrl);
+    k_order_by_algo<<<1, 1024, 0, ctx->stream>>>(algo, count, ctx->order, ctx->bulk_ctrl, 0, 0, 0);
     CKLAUNCH();
     a.order = ctx->order;
   }
@@ -816,6 +822,19 @@ int dabs_set_rows(dabs_ctx* ctx, int32_t mode) {
   if (!rows_ok(ctx, ctx->var, mode))
     return fail(ctx, DABS_E_TOO_LARGE, "row format %d unavailable (%d stored entries)", mode, ctx->sp_nnz);
   ctx->rows_mode = mode;
+  graph_stale(ctx);
+  return DABS_OK;
+}
+
+int dabs_set_search_slots(dabs_ctx* ctx, int32_t modulus, int32_t lo, int32_t hi) {
+  if (!ctx || modulus < 0 || (modulus > 0 && (lo < 0 || hi <= lo || hi > modulus)))
+    return DABS_E_INVALID_ARG;
+  ctx->slot_mod = modulus;
+  ctx->slot_lo = modulus > 0 ? lo : 0;
+  ctx->slot_hi = modulus > 0 ? hi : 0;
+  int cnt = 0;
+  for (int s = 0; s < ctx->S; ++s) cnt += modulus <= 0 || (s % modulus >= lo && s % modulus < hi);
+  ctx->slot_count = cnt;
   graph_stale(ctx);
   return DABS_OK;
 }

@@ -87,6 +87,9 @@ struct dabs_ctx {
   std::vector<void*> allocs;
   std::string err;
   uint64_t launches = 0;      // kernels launched by stage() (counted for the batched form)
+  // the searches this context runs when a solve is split over devices by
+  // island: slots s with slot_lo <= s mod slot_mod < slot_hi (slot_mod 0: all)
+  int slot_mod = 0, slot_lo = 0, slot_hi = 0, slot_count = 0;
 };
 
 

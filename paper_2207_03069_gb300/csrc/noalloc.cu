@@ -148,7 +148,7 @@ extern "C" int dabs_bulk_search_noalloc(const int16_t* W, int32_t n, int32_t ld,
   k_negate_clear<<<(unsigned)((entries + 255) / 256 < 1024 ? (entries + 255) / 256 : 1024), 256, 0, st>>>(
       W, Wneg, diag, n, ld, ctrl, seed, g);
   if (cudaGetLastError() != cudaSuccess) return DABS_E_CUDA;
-  k_order_by_algo<<<1, 1024, 0, st>>>(algo, count, order, ctrl);
+  k_order_by_algo<<<1, 1024, 0, st>>>(algo, count, order, ctrl, 0, 0, 0);
   if (cudaGetLastError() != cudaSuccess) return DABS_E_CUDA;
 
   SearchArgs a{};

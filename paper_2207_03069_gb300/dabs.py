@@ -91,6 +91,7 @@ EXPORTS = {
     "dabs_batch_generations": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "dabs_batch_destroy": (None, [C.c_void_p]),
     "dabs_batch_info": (C.c_int, [C.c_void_p] * 5),
+    "dabs_set_search_slots": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "dabs_measure_read_gbs": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int32, C.c_void_p,
                                         C.c_void_p]),
     "dabs_server_create": (C.c_int, [C.c_size_t, C.c_void_p]),
@@ -482,6 +483,10 @@ class Context:
 
     def run_stage(self, stage: int):
         self._ck(lib().dabs_run_stage(self._h, stage))
+
+    def set_search_slots(self, modulus: int, lo: int = 0, hi: int = 0):
+        """Stage 1 runs only the searches s with lo <= s mod modulus < hi (0: all)."""
+        self._ck(lib().dabs_set_search_slots(self._h, modulus, lo, hi))
 
     # ---------------------------------------------------------------- bulk search
     def bulk_search_dev(self, seed, g, X, delta, E, D, algo, best_X, best_E, flips):
