@@ -80,6 +80,7 @@ struct SmemSearch {
   int4 red[2][C::NW];        // reduction slots (double buffered)
   int tot[C::CH][C::NW];     // per chunk, per warp candidate counts (k-th pick)
   int pick[4];               // broadcast of a pick made by one thread
+  int2 nx[2];                // TwoNeighbor: (x_k, d_k) of the next bit from its owner (by parity)
 };
 
 #define DABS_CASES(X)                                                                      \
@@ -230,6 +231,49 @@ struct Searcher {
       v[0] = r0;
       if constexpr (K > 1) v[K > 1 ? 1 : 0] = r1;
       buf ^= 1;
+    }
+  }
+
+  // groups of warps: up to two plain minima v (warp-reduced) and one
+  // (value, key) pair -- the group minimum and the lowest key among the
+  // warps holding it -- in one shared-memory round
+  template <int K>
+  __device__ __forceinline__ void gmin_pair(int (&v)[K], int& pv, uint32_t& pk) {
+    static_assert(K >= 1 && K <= 2, "at most two plain values");
+    if constexpr (NW == 1) return;  // a single warp: the warp values are the group's
+    if (lane == 0) sm->red[buf][warp] = make_int4(v[0], K > 1 ? v[K - 1] : 0, pv, (int)pk);
+    __syncthreads();
+    int4 r = sm->red[buf][0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) {
+      const int4 o = sm->red[buf][w];
+      r.x = min(r.x, o.x);
+      r.y = min(r.y, o.y);
+      if (o.z < r.z || (o.z == r.z && (uint32_t)o.w < (uint32_t)r.w)) {
+        r.z = o.z;
+        r.w = o.w;
+      }
+    }
+    v[0] = r.x;
+    if constexpr (K > 1) v[K - 1] = r.y;
+    pv = r.z;
+    pk = (uint32_t)r.w;
+    buf ^= 1;
+  }
+  // Step 1's key for the group minimum m (groups of warps: a round of its own,
+  // taken only when the step improves BEST)
+  __device__ __forceinline__ uint32_t step1_key(const int (&cma)[CH], int m) {
+    uint32_t k[1] = {warp_key(FULL, cma, m)};
+    gminu(k);
+    return k[0];
+  }
+  // TwoNeighbor visits bits in a fixed order: in a group of warps the owner of
+  // the next bit publishes its x_k and d_k once the current flip is applied,
+  // and the group reads them after its next round (slot by iteration parity)
+  __device__ __forceinline__ void publish_next(int k, int it_read) {
+    if (t == owner_t(k)) {
+      const int pk = local_p(k);
+      sm->nx[it_read & 1] = make_int2(bit_at(xb, pk) ? 1 : 0, get_at(pk));
     }
   }
 
@@ -593,7 +637,58 @@ struct Searcher {
       chunk_min_all(cma);  // Step 1: every one-bit neighbour
       int m;
       bool improve;
-      if (phase != PH_MAIN) {
+      if (phase != PH_MAIN && NW > 1) {
+        // ---------------- Straight / Greedy, groups of warps: the selection's
+        // (value, key) pair rides in Step 1's round
+        const bool st = phase == PH_STRAIGHT;
+        const uint32_t Ms = (xb[0] ^ db[0]) & vb[0];
+        int cms[CH];
+        int v[1] = {__reduce_min_sync(FULL, min_of(cma))};
+        int pv;
+        uint32_t pk;
+        if (st) {
+          chunk_min(Ms, cms);
+          pv = __reduce_min_sync(FULL, min_of(cms));
+          pk = pv == INT_MAX ? UINT_MAX : warp_key(Ms, cms, pv);
+        } else {
+          pv = v[0];
+          pk = warp_key(FULL, cma, pv);
+        }
+        gmin_pair(v, pv, pk);
+        m = v[0];
+        if (st && pv == INT_MAX) {  // X == D: Straight ends
+          phase = PH_GREEDY;
+          continue;
+        }
+        improve = E + m < Ebest;
+        if (!st && m >= 0) {  // local minimum: Greedy ends after Step 1
+          if (improve) take_best(pk, m);
+          if (flips < B && !(ALGO == TWONEIGHBOR && runs >= 1)) {
+            phase = PH_MAIN;
+            it = 0;
+            ws = 0;
+            fup = 0;
+            rup = 0;
+            fdn = 1u << 21;
+            rdn = 0;
+            tb[0] = 0;
+            ring_len = 0;
+            ring_head = 0;
+            if (ALGO == TWONEIGHBOR) publish_next(0, 0);  // its first bit
+            continue;
+          }
+          break;
+        }
+        if (st) {
+          kj = improve ? step1_key(cma, m) : UINT_MAX;
+          di = pv;
+        } else {
+          kj = pk;
+          di = m;
+        }
+        i = (int)(pk >> 1);
+        xi = (int)(pk & 1u);
+      } else if (phase != PH_MAIN) {
         // ---------------- Straight / Greedy
         const bool st = phase == PH_STRAIGHT;
         const uint32_t Ms = (xb[0] ^ db[0]) & vb[0];
@@ -663,7 +758,13 @@ struct Searcher {
             kj = k[0];
           }
           i = it == 0 ? 0 : ((it & 1) ? (it + 1) >> 1 : (it >> 1) - 1);
-          xi = fetch_x(i, &di);
+          if constexpr (NW > 1) {
+            const int2 nx = sm->nx[it & 1];  // published before the round above
+            xi = nx.x;
+            di = nx.y;
+          } else {
+            xi = fetch_x(i, &di);
+          }
         } else if (ALGO == MAXMIN || ALGO == POSITIVEMIN) {
           if ((it & 31) == 0) {
             // the flips of iterations it .. it+31 are flips .. flips+31
@@ -746,21 +847,43 @@ struct Searcher {
           int cm1[CH], cm2[CH];
           chunk_min(M1, cm1);
           chunk_min(M2, cm2);
-          int v[2] = {min_of(cma), min(min_of(cm1), min_of(cm2))};
-          gmin(v);
-          m = v[0];
-          improve = E + m < Ebest;
-          // first in cyclic order from ws: [ws, n) before [0, ws + wsz - n)
-          const uint32_t k1 = warp_key(M1, cm1, v[1]), k2 = warp_key(M2, cm2, v[1]);
-          const uint32_t r1 = k1 == UINT_MAX ? UINT_MAX : k1 - ((uint32_t)ws << 1);
-          const uint32_t r2 = k2 == UINT_MAX ? UINT_MAX : k2 + ((uint32_t)(n - ws) << 1);
-          uint32_t k[2] = {improve ? warp_key(FULL, cma, m) : UINT_MAX, min(r1, r2)};
-          gminu(k);
-          kj = k[0];
-          const int sb = ws + (int)(k[1] >> 1);
+          uint32_t wk;  // the window pick's key, relative to ws (cyclic order)
+          if constexpr (NW > 1) {
+            // this warp's window minimum and its first bit in cyclic order from
+            // ws, reduced in Step 1's round
+            int v[1] = {__reduce_min_sync(FULL, min_of(cma))};
+            int pv = __reduce_min_sync(FULL, min(min_of(cm1), min_of(cm2)));
+            uint32_t pk = UINT_MAX;
+            if (pv != INT_MAX) {
+              const uint32_t k1 = warp_key(M1, cm1, pv), k2 = warp_key(M2, cm2, pv);
+              const uint32_t r1 = k1 == UINT_MAX ? UINT_MAX : k1 - ((uint32_t)ws << 1);
+              const uint32_t r2 = k2 == UINT_MAX ? UINT_MAX : k2 + ((uint32_t)(n - ws) << 1);
+              pk = min(r1, r2);
+            }
+            gmin_pair(v, pv, pk);
+            m = v[0];
+            improve = E + m < Ebest;
+            kj = improve ? step1_key(cma, m) : UINT_MAX;
+            wk = pk;
+            di = pv;
+          } else {
+            int v[2] = {min_of(cma), min(min_of(cm1), min_of(cm2))};
+            gmin(v);
+            m = v[0];
+            improve = E + m < Ebest;
+            // first in cyclic order from ws: [ws, n) before [0, ws + wsz - n)
+            const uint32_t k1 = warp_key(M1, cm1, v[1]), k2 = warp_key(M2, cm2, v[1]);
+            const uint32_t r1 = k1 == UINT_MAX ? UINT_MAX : k1 - ((uint32_t)ws << 1);
+            const uint32_t r2 = k2 == UINT_MAX ? UINT_MAX : k2 + ((uint32_t)(n - ws) << 1);
+            uint32_t k[2] = {improve ? warp_key(FULL, cma, m) : UINT_MAX, min(r1, r2)};
+            gminu(k);
+            kj = k[0];
+            wk = k[1];
+            di = v[1];
+          }
+          const int sb = ws + (int)(wk >> 1);
           i = sb >= n ? sb - n : sb;
-          xi = (int)(k[1] & 1u);
-          di = v[1];
+          xi = (int)(wk & 1u);
           ws += wsz;
           if (ws >= n) ws -= n;
         } else {  // RANDOMMIN
@@ -771,27 +894,52 @@ struct Searcher {
           const uint32_t Cm = mask_of([&](int p) { return randmin_hit(rr, p, thr); }) & F;
           int cmc[CH];
           chunk_min(Cm, cmc);
-          int v[2] = {min_of(cma), min_of(cmc)};
-          gmin(v);
-          m = v[0];
-          improve = E + m < Ebest;
-          uint32_t ks;
-          if (v[1] != INT_MAX) {
-            di = v[1];
-            ks = warp_key(Cm, cmc, di);
-          } else {  // no candidate: argmin over the free bits (rare)
-            int cmf[CH];
-            chunk_min(F, cmf);
-            int vf[1] = {min_of(cmf)};
-            gmin(vf);
-            di = vf[0];
-            ks = warp_key(F, cmf, di);
+          uint32_t key;
+          if constexpr (NW > 1) {
+            // the candidates' pair in Step 1's round
+            int v[1] = {__reduce_min_sync(FULL, min_of(cma))};
+            int pv = __reduce_min_sync(FULL, min_of(cmc));
+            uint32_t pk = pv == INT_MAX ? UINT_MAX : warp_key(Cm, cmc, pv);
+            gmin_pair(v, pv, pk);
+            m = v[0];
+            improve = E + m < Ebest;
+            kj = improve ? step1_key(cma, m) : UINT_MAX;
+            if (pv == INT_MAX) {  // no candidate: argmin over the free bits (rare)
+              int cmf[CH];
+              chunk_min(F, cmf);
+              int vf[1] = {min_of(cmf)};
+              gmin(vf);
+              pv = vf[0];
+              uint32_t kf[1] = {warp_key(F, cmf, pv)};
+              gminu(kf);
+              pk = kf[0];
+            }
+            di = pv;
+            key = pk;
+          } else {
+            int v[2] = {min_of(cma), min_of(cmc)};
+            gmin(v);
+            m = v[0];
+            improve = E + m < Ebest;
+            uint32_t ks;
+            if (v[1] != INT_MAX) {
+              di = v[1];
+              ks = warp_key(Cm, cmc, di);
+            } else {  // no candidate: argmin over the free bits (rare)
+              int cmf[CH];
+              chunk_min(F, cmf);
+              int vf[1] = {min_of(cmf)};
+              gmin(vf);
+              di = vf[0];
+              ks = warp_key(F, cmf, di);
+            }
+            uint32_t k[2] = {improve ? warp_key(FULL, cma, m) : UINT_MAX, ks};
+            gminu(k);
+            kj = k[0];
+            key = k[1];
           }
-          uint32_t k[2] = {improve ? warp_key(FULL, cma, m) : UINT_MAX, ks};
-          gminu(k);
-          kj = k[0];
-          i = (int)(k[1] >> 1);
-          xi = (int)(k[1] & 1u);
+          i = (int)(key >> 1);
+          xi = (int)(key & 1u);
         }
       }
       if (improve) take_best(kj, m);
@@ -808,6 +956,12 @@ struct Searcher {
       }
       row_apply(rv, di);
       if constexpr (!C::EARLY) flip_after(i, di, xi);
+      if constexpr (NW > 1 && ALGO == TWONEIGHBOR) {
+        if (phase == PH_MAIN && it + 1 < Tmain) {
+          const int q = it + 1;  // the next bit differs from bit i
+          publish_next((q & 1) ? (q + 1) >> 1 : (q >> 1) - 1, q);
+        }
+      }
       if (phase == PH_MAIN && ++it == Tmain) {
         phase = PH_GREEDY;
         ++runs;
