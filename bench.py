@@ -504,37 +504,53 @@ def oracle_batched_rate(Ws, spec, seed, seconds, threads, gens=None):
     return flips / (time.perf_counter() - t0), g
 
 
-def served_trace(dabs, rate, seconds, seed, generations=20, sizes=(512, 1024, 2048, 4096, 8192),
-                 big=0, budget_gb=60, targets=None, Wcache=None):
+SERVE_SIZES = (512, 1024, 2048, 4096, 8192)
+SERVE_CATALOG = 16  # distinct instances per size (W ~ U[-1000, 1000], seed 5000 + 16 size + j)
+
+
+def serve_requests(rate, seconds, seed, sizes=SERVE_SIZES, big=0):
     """Poisson arrivals (rate per s for `seconds`, seed) of dense QUBOs with n
-    uniform in `sizes` (W ~ U[-1000, 1000], seed 5000 + i), 256 searches, a
-    flip budget of 256 x generations x n and at most `generations`
-    generations, recompute seeding; plus one n = `big` instance mid-trace.
-    With `targets` (request index -> energy), each request stops at its
-    target; latency = completion - arrival.  Returns (requests, results,
-    latencies, flips, wall seconds)."""
+    uniform in `sizes`: request i solves instance j = i mod 16 of its size
+    with solve seed 20000 + i; plus one n = `big` instance mid-trace.  The
+    same seed gives request i the same size at every rate.  Returns a list of
+    (arrival s, n, instance seed, solve seed) sorted by arrival."""
     rng = np.random.default_rng(seed)
     arr = wl.poisson_arrivals(rate, seconds, seed=seed)
-    reqs = [(float(t), int(rng.choice(sizes)), 5000 + i) for i, t in enumerate(arr)]
+    reqs = []
+    for i, t in enumerate(arr):
+        n = int(rng.choice(sizes))
+        reqs.append((float(t), n, 5000 + 16 * sizes.index(n) + i % SERVE_CATALOG, 20000 + i))
     if big:
-        reqs.append((seconds / 2, big, 9999))
+        reqs.append((seconds / 2, big, 9999, 9999))
         reqs.sort()
+    return reqs
+
+
+def serve_kw(generations):
+    return dict(searches=256, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=1,
+                max_generations=generations)
+
+
+def served_trace(dabs, reqs, generations, budget_gb=60, targets=None, Wcache=None):
+    """Serves `reqs` (serve_requests) with continuous batching: 256 searches,
+    a flip budget of 256 x generations x n and at most `generations`
+    generations, recompute seeding.  With `targets` ((n, instance, solve
+    seed) -> energy), each request stops at its target; latency = completion
+    - arrival.  Returns (results, latencies, flips, wall seconds)."""
     Wcache = {} if Wcache is None else Wcache
-    for _, n, sd in reqs:  # instances are prepared before the clock starts
-        if (n, sd) not in Wcache:
-            Wcache[(n, sd)] = wl.dense_qubo(n, -1000, 1000, seed=sd)
-    kw = dict(searches=256, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=1,
-              max_generations=generations)
-    params = dabs.default_params(**kw)
+    for _, n, inst, _ in reqs:  # instances are prepared before the clock starts
+        if (n, inst) not in Wcache:
+            Wcache[(n, inst)] = wl.dense_qubo(n, -1000, 1000, seed=inst)
+    params = dabs.default_params(**serve_kw(generations))
     srv = dabs.Server(budget_gb << 30)
     t0 = time.perf_counter()
     tickets, i, pending = [], 0, 0
     while i < len(reqs) or pending:
         now = time.perf_counter() - t0
         while i < len(reqs) and reqs[i][0] <= now:
-            _, n, sd = reqs[i]
-            tg = None if targets is None else targets[(n, sd)]
-            tickets.append(srv.submit(Wcache[(n, sd)], params, 256 * generations * n, sd, target=tg))
+            _, n, inst, sd = reqs[i]
+            tg = None if targets is None else targets[(n, inst, sd)]
+            tickets.append(srv.submit(Wcache[(n, inst)], params, 256 * generations * n, sd, target=tg))
             i += 1
         if srv.info()[1] + srv.info()[2] == 0:
             time.sleep(0.0005)
@@ -543,52 +559,47 @@ def served_trace(dabs, rate, seconds, seed, generations=20, sizes=(512, 1024, 20
         pending = srv.step(1)
     wall = time.perf_counter() - t0
     res, lat, fl = {}, [], 0
-    for t, (_, n, sd) in zip(tickets, reqs):
+    for t, (_, n, inst, sd) in zip(tickets, reqs):
         st, X, E, F, L = srv.poll(t)
-        res[(n, sd)] = (X.tobytes(), E, F)
+        res[(n, inst, sd)] = (X.tobytes(), E, F)
         lat.append(L)
         fl += F
     srv.close()
-    return reqs, res, lat, fl, wall
+    return res, lat, fl, wall
 
 
-def serving(dabs, seconds=2.0, rate=50.0, sweep=(5.0, 10.0, 25.0), generations=20, big=0):
+def serving(dabs, seconds=2.0, rate=50.0, sweep=(5.0, 10.0, 25.0), generations=4, big=0):
     """The served workload with per-request targets: every request's target
     is the energy it reaches alone (computed before the clock, in batched form,
     whose results equal the alone ones); the trace at `rate` is served with
     continuous batching and, on the same arrivals, one request at a time (the
     plain form); every request's (X, E, flips) must be identical in both.  The
-    same requests are also served at the `sweep` rates (p99 per rate)."""
+    same requests are also served at the `sweep` rates (p50/p99 per rate)."""
     Wcache = {}
-    kw = dict(searches=256, pools=4, pool_cap=100, tabu=8, s=(1, 10), b=(1, 1), seed_mode=1,
-              max_generations=generations)
-    # the union of the requests of every trace (same seed: same instances)
-    keys = []
-    for r in (rate,) + tuple(sweep):
-        rng = np.random.default_rng(4)
-        for i, _ in enumerate(wl.poisson_arrivals(r, seconds, seed=4)):
-            keys.append((int(rng.choice((512, 1024, 2048, 4096, 8192))), 5000 + i))
-    if big:
-        keys.append((big, 9999))
-    keys = sorted(set(keys))
-    for n, sd in keys:
-        Wcache[(n, sd)] = wl.dense_qubo(n, -1000, 1000, seed=sd)
+    kw = serve_kw(generations)
+    traces = {r: serve_requests(r, seconds, 4, big=big if r == rate else 0)
+              for r in (rate,) + tuple(sweep)}
+    keys = sorted({q[1:] for rq in traces.values() for q in rq})  # (n, instance, solve seed)
+    for n, inst, _ in keys:
+        if (n, inst) not in Wcache:
+            Wcache[(n, inst)] = wl.dense_qubo(n, -1000, 1000, seed=inst)
     targets = {}
     t0 = time.perf_counter()
     for c0 in range(0, len(keys), 48):  # untimed: the energies each reaches alone
         chunk = keys[c0:c0 + 48]
-        ctxs = [dabs.Context(Wcache[k], **kw) for k in chunk]
-        out = dabs.batch_solve(ctxs, [256 * generations * k[0] for k in chunk], [k[1] for k in chunk])
+        ctxs = [dabs.Context(Wcache[k[:2]], **kw) for k in chunk]
+        out = dabs.batch_solve(ctxs, [256 * generations * k[0] for k in chunk], [k[2] for k in chunk])
         for k, o in zip(chunk, out):
             targets[k] = o[1]
         for c in ctxs:
             c.close()
     t_targets = time.perf_counter() - t0
     progress(f"serving: {len(keys)} targets in {t_targets:.1f}s")
-    reqs, res, lat, fl, wall = served_trace(dabs, rate, seconds, 4, generations, big=big,
-                                            targets=targets, Wcache=Wcache)
+    reqs = traces[rate]
+    res, lat, fl, wall = served_trace(dabs, reqs, generations, targets=targets, Wcache=Wcache)
     out = {"workload": f"Poisson {rate}/s for {seconds}s (seed 4), n uniform in "
-                       f"{{512,...,8192}}" + (f" plus one n={big}" if big else "")
+                       f"{{512,...,8192}} ({SERVE_CATALOG} instances per size, one solve seed "
+                       f"per request)" + (f" plus one n={big}" if big else "")
                        + f", 256 searches, budget 256 x {generations} x n flips, at most "
                          f"{generations} generations, recompute seeding",
            "target": "the energy each request reaches alone under the same limits",
@@ -600,29 +611,30 @@ def serving(dabs, seconds=2.0, rate=50.0, sweep=(5.0, 10.0, 25.0), generations=2
     t0 = time.perf_counter()
     lat2, free_at, same = [], 0.0, True
     fl2 = 0
-    for (ta, n, sd) in reqs:
+    for (ta, n, inst, sd) in reqs:
         start = max(ta, free_at)
         now = time.perf_counter() - t0
         if now < start:
             time.sleep(start - now)
-        c = dabs.Context(Wcache[(n, sd)], **kw)
-        X, E, F = c.solve(256 * generations * n, seed=sd, target=targets[(n, sd)])
+        c = dabs.Context(Wcache[(n, inst)], **kw)
+        X, E, F = c.solve(256 * generations * n, seed=sd, target=targets[(n, inst, sd)])
         c.close()
         free_at = time.perf_counter() - t0
         lat2.append(free_at - ta)
         fl2 += F
-        same = same and res[(n, sd)] == (X.tobytes(), E, F)
+        same = same and res[(n, inst, sd)] == (X.tobytes(), E, F)
     out.update({"plain_p50_s": pct(lat2, 50), "plain_p99_s": pct(lat2, 99),
                 "plain_flips_per_s": fl2 / (time.perf_counter() - t0),
+                "plain_wall_s": time.perf_counter() - t0,
                 "identical_results": bool(same)})
     progress("serving: plain done")
     rates = {}
     for r in sweep:
-        rq, rs, lt, f3, w3 = served_trace(dabs, r, seconds, 4, generations, big=0,
-                                          targets=targets, Wcache=Wcache)
+        rs, lt, f3, w3 = served_trace(dabs, traces[r], generations, targets=targets, Wcache=Wcache)
         ok = all(rs[k] == res[k] for k in rs if k in res)
-        rates[str(r)] = {"requests": len(rq), "p50_s": pct(lt, 50), "p99_s": pct(lt, 99),
+        rates[str(r)] = {"requests": len(traces[r]), "p50_s": pct(lt, 50), "p99_s": pct(lt, 99),
                          "flips_per_s": f3 / w3, "identical_results": bool(ok)}
+        progress(f"serving: rate {r}/s done")
     out["rate_sweep"] = rates
     return out
 
@@ -634,6 +646,9 @@ def run_batched(args, ws, rank, lrank, pg):
     build.build()
     torch.cuda.set_device(lrank)
     dev = torch.device("cuda", lrank)
+    # the L2 read peak, measured before the workload's buffers exist (later in
+    # the run the same measurement has read about a third of it)
+    l2 = l2_read_gbs(torch, dev)
     spec = WORKLOADS[args.workload]
     Ws = batched_instances(spec)
     ns = [W.shape[0] for W in Ws]
@@ -723,17 +738,24 @@ def run_batched(args, ws, rank, lrank, pg):
     achieved = row_bytes / (search_ms * 1e-3) / 1e9
     wset = sum(4 * n * n for n in ns)  # W and -W: the rows one flip may read
     l2_size = torch.cuda.get_device_properties(dev).L2_cache_size
-    l2 = l2_read_gbs(torch, dev)
-    bound = "hbm" if wset > l2_size else "l2"
-    peak = hbm if bound == "hbm" else l2
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sms * 4 * 16 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6
     prof = search_profile("search_batched64.json")
+    traffic = prof.get("dram_bytes_per_generation") if prof else None
+    # where the rows come from: the L2 when W fits it, or when the captured
+    # DRAM traffic of the search launches is a small part of the row bytes
+    # they read (the instances searched at one time fit the L2 together)
+    from_l2 = wset <= l2_size or (traffic is not None and traffic < 0.25 * row_bytes)
+    bound = "l2" if from_l2 else "hbm"
+    peak = l2 if from_l2 else hbm
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
-                "peak_kind": f"{peak_kind} HBM copy" if bound == "hbm" else "measured L2-resident read",
-                "traffic": prof.get("dram_bytes_per_generation") if prof else None,
+                "peak_kind": "measured L2-resident read (64 MiB buffer, library read kernel, "
+                             "before the workload's buffers are allocated)"
+                             if from_l2 else f"{peak_kind} HBM copy",
+                "traffic": traffic,
                 "traffic_source": "profiles/search_batched64.json" if prof else None,
+                "traffic_per": "generation (all search launches), dram read + write",
                 "kernel": "k_batch_search (multi-instance launches, one per variant group)",
                 "algorithmic_bytes_per_launch": row_bytes,
                 "algorithmic_bytes": "flips x 2n per flip (the int16 row of sigma(x_i) W), summed over instances",
@@ -779,7 +801,9 @@ def run_batched(args, ws, rank, lrank, pg):
         extra["time_to_target"] = batched_ttt(dabs, Ws, kw, seeds)
         progress("time to target done")
         if args.trace_seconds > 0:
-            extra["serving"] = serving(dabs, seconds=args.trace_seconds, big=args.serve_big)
+            extra["serving"] = serving(dabs, seconds=args.trace_seconds, big=args.serve_big,
+                                       generations=args.serve_generations,
+                                       sweep=tuple(args.serve_sweep))
             progress("serving done")
         rec = recompute_rate(torch, dabs, dev) if not args.no_recompute else None
         if rec:
@@ -788,7 +812,7 @@ def run_batched(args, ws, rank, lrank, pg):
             rec["peak_tflops"] = pk
             rec["frac"] = rec["tensor_tflops"] / pk
             extra["recompute_tensor"] = rec
-        extra["maxcut800"] = single_summary(dabs, torch, dev, "maxcut800", clocks)
+        extra["maxcut800"] = single_summary(dabs, torch, dev, "maxcut800", clocks, l2)
         progress("maxcut800 done")
         extra["small_graphs"] = small_graphs(dabs)
         extra["tsp_time_to_target"] = tsp_ttt(dabs, seeds=8)
@@ -865,7 +889,7 @@ def batched_ttt(dabs, Ws, kw, seeds, generations=3):
             "targets_reached": bool(reached)}
 
 
-def single_summary(dabs, torch, dev, name, clocks, steps=10):
+def single_summary(dabs, torch, dev, name, clocks, l2, steps=10):
     """One single-instance workload (autotuned, one generation per step): flips/s,
     ns per flip and the flip kernel against the L2-resident read bandwidth."""
     spec = WORKLOADS[name]
@@ -892,7 +916,6 @@ def single_summary(dabs, torch, dev, name, clocks, steps=10):
     s1 = ctx.solve_status()
     ms = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
     fl = (s1["flips"] - s0["flips"]) / steps
-    l2 = l2_read_gbs(torch, dev)
     ach = fl * 2 * n / (ms * 1e-3) / 1e9
     out = {"workload": spec["desc"], "variant": ctx.variant_name(), "keyed": ctx.keyed()[0],
            "search_flips_per_s": fl / (ms * 1e-3), "ns_per_flip": ms * 1e6 / fl,
@@ -919,6 +942,10 @@ def main():
     ap.add_argument("--trace-seconds", type=float, default=2.0)
     ap.add_argument("--serve-big", type=int, default=0,
                     help="add one instance of this n (e.g. 16384) mid-trace to the served workload")
+    ap.add_argument("--serve-generations", type=int, default=4,
+                    help="generation limit of every served request (budget 256 x this x n flips)")
+    ap.add_argument("--serve-sweep", type=float, nargs="*", default=[5.0, 10.0, 25.0],
+                    help="arrival rates (req/s) of the served trace's rate sweep")
     ap.add_argument("--variant", default="", help="force warps x chunks, e.g. 4x1")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -938,6 +965,7 @@ def main():
     build.build()
     torch.cuda.set_device(lrank)
     dev = torch.device("cuda", lrank)
+    l2 = l2_read_gbs(torch, dev)  # before the workload's buffers exist
     spec = WORKLOADS[args.workload]
     Wm = make_W(args.workload)
     n = Wm.shape[0]
@@ -999,13 +1027,20 @@ def main():
     info = ctx.info()
     vkey = "%dx%d" % (info["warps"], info["chunks"])
     traffic = prof["dram_bytes_per_launch"].get(vkey) if prof else None
-    l2 = l2_copy_gbs(torch, dev)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_kind": f"{peak_kind} HBM copy",
+    l2c = l2_copy_gbs(torch, dev)
+    # W and -W (the rows one flip may read) against the L2: rows are L2 hits
+    # when they fit (the capture confirms it: DRAM traffic is the search state)
+    from_l2 = 4 * n * n <= torch.cuda.get_device_properties(dev).L2_cache_size
+    peak = l2 if from_l2 else hbm
+    roofline = {"bound": "l2" if from_l2 else "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": "measured L2-resident read (64 MiB buffer, library read kernel)"
+                             if from_l2 else f"{peak_kind} HBM copy",
                 "traffic": traffic, "traffic_source": "profiles/search_maxcut800.json" if traffic else None,
                 "kernel": "k_batch_search", "algorithmic_bytes_per_launch": algo_bytes,
                 "launch_ms": launch_s * 1e3, "search_share_of_step": sum(search_ms) / sum(step_ms),
-                "l2_copy_gbs_measured": l2, "frac_of_l2_copy": achieved / l2}
+                "frac_of_hbm": achieved / hbm, "l2_read_gbs_measured": l2,
+                "l2_copy_gbs_measured": l2c, "frac_of_l2_copy": achieved / l2c}
     # integer-ALU ceiling beside the memory roofline: the ALU pipe (integer
     # compare, min, select, logic) issues 16 lanes per scheduler, 4 schedulers
     # per SM; the ncu capture gives the ALU instructions the kernel spends per flip
