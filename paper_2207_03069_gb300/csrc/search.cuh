@@ -201,17 +201,18 @@ struct Searcher {
       if (lane == 0)
         sm->red[buf][warp] = make_int4(v[0], K > 1 ? v[K > 1 ? 1 : 0] : 0, K > 2 ? v[K > 2 ? 2 : 0] : 0, 0);
       __syncthreads();
-      int4 r = sm->red[buf][0];
-#pragma unroll
-      for (int w = 1; w < NW; ++w) {
-        const int4 o = sm->red[buf][w];
-        r.x = min(r.x, o.x); r.y = min(r.y, o.y); r.z = min(r.z, o.z);
-      }
-      v[0] = r.x;
-      if constexpr (K > 1) v[K > 1 ? 1 : 0] = r.y;
-      if constexpr (K > 2) v[K > 2 ? 2 : 0] = r.z;
+      // lane w < NW takes warp w's slot; one more warp reduction combines them
+      const int4 r = slot(make_int4(INT_MAX, INT_MAX, INT_MAX, 0));
+      v[0] = __reduce_min_sync(FULL, r.x);
+      if constexpr (K > 1) v[K > 1 ? 1 : 0] = __reduce_min_sync(FULL, r.y);
+      if constexpr (K > 2) v[K > 2 ? 2 : 0] = __reduce_min_sync(FULL, r.z);
       buf ^= 1;
     }
+  }
+  // groups of warps, after the barrier of a round: warp `lane`'s slot in the
+  // lanes below NW, `neutral` in the others
+  __device__ __forceinline__ int4 slot(int4 neutral) const {
+    return lane < NW ? sm->red[buf][lane < NW ? lane : 0] : neutral;
   }
   template <int K>
   __device__ __forceinline__ void gminu(uint32_t (&v)[K]) {
@@ -221,15 +222,9 @@ struct Searcher {
       if (lane == 0)
         sm->red[buf][warp] = make_int4((int)v[0], K > 1 ? (int)v[K > 1 ? 1 : 0] : 0, 0, 0);
       __syncthreads();
-      uint32_t r0 = (uint32_t)sm->red[buf][0].x, r1 = (uint32_t)sm->red[buf][0].y;
-#pragma unroll
-      for (int w = 1; w < NW; ++w) {
-        const int4 o = sm->red[buf][w];
-        r0 = min(r0, (uint32_t)o.x);
-        r1 = min(r1, (uint32_t)o.y);
-      }
-      v[0] = r0;
-      if constexpr (K > 1) v[K > 1 ? 1 : 0] = r1;
+      const int4 r = slot(make_int4(-1, -1, 0, 0));  // UINT_MAX
+      v[0] = __reduce_min_sync(FULL, (uint32_t)r.x);
+      if constexpr (K > 1) v[K > 1 ? 1 : 0] = __reduce_min_sync(FULL, (uint32_t)r.y);
       buf ^= 1;
     }
   }
@@ -243,21 +238,11 @@ struct Searcher {
     if constexpr (NW == 1) return;  // a single warp: the warp values are the group's
     if (lane == 0) sm->red[buf][warp] = make_int4(v[0], K > 1 ? v[K - 1] : 0, pv, (int)pk);
     __syncthreads();
-    int4 r = sm->red[buf][0];
-#pragma unroll
-    for (int w = 1; w < NW; ++w) {
-      const int4 o = sm->red[buf][w];
-      r.x = min(r.x, o.x);
-      r.y = min(r.y, o.y);
-      if (o.z < r.z || (o.z == r.z && (uint32_t)o.w < (uint32_t)r.w)) {
-        r.z = o.z;
-        r.w = o.w;
-      }
-    }
-    v[0] = r.x;
-    if constexpr (K > 1) v[K - 1] = r.y;
-    pv = r.z;
-    pk = (uint32_t)r.w;
+    const int4 r = slot(make_int4(INT_MAX, INT_MAX, INT_MAX, -1));
+    v[0] = __reduce_min_sync(FULL, r.x);
+    if constexpr (K > 1) v[K - 1] = __reduce_min_sync(FULL, r.y);
+    pv = __reduce_min_sync(FULL, r.z);
+    pk = __reduce_min_sync(FULL, r.z == pv ? (uint32_t)r.w : UINT_MAX);
     buf ^= 1;
   }
   // Step 1's key for the group minimum m (groups of warps: a round of its own,
@@ -437,21 +422,40 @@ struct Searcher {
         for (int c = 0; c < CH; ++c) sm->tot[c][warp] = wt[c];
       }
       __syncthreads();
-      int total = 0;
+      // the counts in ascending bit order (chunk, then warp): entry j =
+      // c NW + w; lane l holds entries l EPL .. l EPL + EPL - 1, and one
+      // prefix over the lanes locates the kk-th candidate's entry
+      constexpr int NE = CH * NW, EPL = (NE + 31) / 32;
+      const int* tf = &sm->tot[0][0];
+      int te[EPL];
+      int ls = 0;
 #pragma unroll
-      for (int c = 0; c < CH; ++c)
+      for (int e = 0; e < EPL; ++e) {
+        const int j = lane * EPL + e;
+        te[e] = j < NE ? tf[j < NE ? j : 0] : 0;
+        ls += te[e];
+      }
+      int incl = ls;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) total += sm->tot[c][w];
-      int kk = (int)uniform_below(u, (uint32_t)total);
-      bool found = false;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int total = __shfl_sync(FULL, incl, 31);
+      const int kk = (int)uniform_below(u, (uint32_t)total);
+      const unsigned bl = __ballot_sync(FULL, incl > kk);  // none when there is no candidate
+      int js = lane * EPL, r = kk - (incl - ls);
 #pragma unroll
-      for (int c = 0; c < CH; ++c)
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const int tw = sm->tot[c][w];
-          if (!found && kk < tw) { csel = c; wsel = w; rel = kk; found = true; }
-          if (!found) kk -= tw;
-        }
+      for (int e = 0; e < EPL - 1; ++e)
+        if (r >= te[e] && js == lane * EPL + e) { r -= te[e]; ++js; }
+      const int src = bl ? __ffs(bl) - 1 : 0;
+      js = __shfl_sync(FULL, js, src);
+      r = __shfl_sync(FULL, r, src);
+      if (bl) {
+        csel = js / NW;
+        wsel = js % NW;
+        rel = r;
+      }
     }
     uint32_t key = 0;
     int dv = 0;  // groups of warps: the pick's stored d value (see flip_after)
