@@ -42,6 +42,13 @@ struct Cfg {
   // variants' launches) and groups of warps write it after the update
   // (flip_after), which measured faster there.
   static constexpr bool EARLY = EARLY_ && NW_ == 1;
+  // RandomMin draws the next iteration's uniforms while row i is in flight,
+  // except in the variants held to 128 registers with 32 bits per thread,
+  // where the extra live draws would spill
+  static constexpr bool PREDRAW = !(NW_ >= 8 && CH_ == 4);
+  // the same variants keep sigma(x_k) as packed signed bytes (four per
+  // register) instead of one register per bit
+  static constexpr bool SG8 = NW_ >= 8 && CH_ == 4;
   static constexpr int NT = 32 * NW;           // threads per search
   static constexpr int EPT = 8 * CH;           // bits per thread
   static constexpr int SPAN = 8 * NT;          // bits per chunk
@@ -95,7 +102,9 @@ struct Searcher {
   static_assert(EPT <= 32, "register-resident variants hold at most 32 bits per thread");
   // --- state (registers) ---
   int d[EPT];          // Delta (INT_MAX for bits >= n)
-  int sg[EPT];         // sigma(x_k) = 2 x_k - 1
+  // sigma(x_k) = 2 x_k - 1 (times 2^kb in the keyed form), one register per
+  // bit; or, with Cfg::SG8, +-1 as signed bytes, bit k in byte k % 4 of sg[k / 4]
+  int sg[C::SG8 ? EPT / 4 : EPT];
   uint32_t xb[NMW];    // X bits
   uint32_t bb[NMW];    // BEST bits
   uint32_t vb[NMW];    // valid bits (k < n)
@@ -153,6 +162,18 @@ struct Searcher {
     }
     return v[0];
   }
+  // sigma(x_k) of register position Q flips
+  template <int Q>
+  __device__ __forceinline__ void flip_sigma() {
+    if constexpr (C::SG8) sg[Q / 4] ^= (int)(0xFEu << (8 * (Q % 4)));  // 0x01 <-> 0xFF
+    else sg[Q] = -sg[Q];
+  }
+  // sigma(x_k) at register position p (a constant once unrolled): +-1 from
+  // its packed byte, or the stored value
+  __device__ __forceinline__ int sigma_of(int p) const {
+    if constexpr (C::SG8) return (int)(signed char)((uint32_t)sg[p >> 2] >> (8 * (p & 3)));
+    else return sg[p];
+  }
   // Eq. (5) at a run-time position after the row update (groups of warps,
   // where Delta_i is known to every thread): d = v, sigma flips
   __device__ __forceinline__ void set_flipped(int p, int v) {
@@ -161,7 +182,7 @@ struct Searcher {
   case q:                                   \
     if constexpr (q < EPT) {                \
       d[q < EPT ? q : 0] = v;               \
-      sg[q < EPT ? q : 0] = -sg[q < EPT ? q : 0]; \
+      flip_sigma<(q < EPT ? q : 0)>();      \
     }                                       \
     break;
       DABS_CASES(DABS_SET)
@@ -182,7 +203,7 @@ struct Searcher {
       const int o = d[qq];                                                    \
       di = C::KEY ? (o >> kb) : o;                                            \
       d[qq] = (C::KEY ? -di * (1 << kb) + ((i << 1) | (xi ^ 1)) : -di) + corr; \
-      sg[qq] = -sg[qq];                                                       \
+      flip_sigma<qq>();                                                       \
     }                                                                         \
     break;
       DABS_CASES(DABS_FLIP)
@@ -373,7 +394,10 @@ struct Searcher {
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int p = 8 * c + e;
-        d[p] += w16(rv[c], e) * sg[p];
+        if constexpr (C::SG8 && C::KEY)
+          d[p] += (w16(rv[c], e) * sigma_of(p)) << kb;
+        else
+          d[p] += w16(rv[c], e) * sigma_of(p);
       }
     }
     E += di;
@@ -953,7 +977,7 @@ struct Searcher {
       if constexpr (C::EARLY) di = commit(i, xi);
       if (phase == PH_MAIN) {
         if (ALGO != TWONEIGHBOR) tabu_push(i, tau);
-        if (ALGO == RANDOMMIN && it + 1 < Tmain) {
+        if (C::PREDRAW && ALGO == RANDOMMIN && it + 1 < Tmain) {
           randmin_draw(flips + 1, rr);  // draws of the next iteration
           rr_ready = true;
         }
@@ -1179,7 +1203,7 @@ struct Searcher {
       if constexpr (C::EARLY) di = commit(i, xi);
       if (phase == PH_MAIN) {
         if (ALGO != TWONEIGHBOR) tabu_push(i, tau);
-        if (ALGO == RANDOMMIN && it + 1 < Tmain) {
+        if (C::PREDRAW && ALGO == RANDOMMIN && it + 1 < Tmain) {
           randmin_draw(flips + 1, rr);  // draws of the next iteration
           rr_ready = true;
         }
@@ -1222,7 +1246,12 @@ struct Searcher {
           d[p] = valid ? vals[e] * (1 << kb) + (((base + e) << 1) | xk) : INT_MAX;
         else
           d[p] = valid ? vals[e] : INT_MAX;
-        sg[p] = (xk && valid ? 1 : -1) * (C::KEY ? (1 << kb) : 1);
+        if constexpr (C::SG8) {
+          if (e % 4 == 0) sg[p / 4] = 0;
+          sg[p / 4] |= (int)((xk && valid ? 0x01u : 0xFFu) << (8 * (p % 4)));
+        } else {
+          sg[p] = (xk && valid ? 1 : -1) * (C::KEY ? (1 << kb) : 1);
+        }
         if (valid) {
           vb[0] |= 1u << p;
           xb[0] |= ((xbyte >> e) & 1u) << p;
