@@ -42,12 +42,9 @@ struct Cfg {
   // variants' launches) and groups of warps write it after the update
   // (flip_after), which measured faster there.
   static constexpr bool EARLY = EARLY_ && NW_ == 1;
-  // RandomMin draws the next iteration's uniforms while row i is in flight,
-  // except in the variants held to 128 registers with 32 bits per thread,
-  // where the extra live draws would spill
-  static constexpr bool PREDRAW = !(NW_ >= 8 && CH_ == 4);
-  // the same variants keep sigma(x_k) as packed signed bytes (four per
-  // register) instead of one register per bit
+  // the variants held to 128 registers with 32 bits per thread keep
+  // sigma(x_k) as packed signed bytes (four per register) instead of one
+  // register per bit
   static constexpr bool SG8 = NW_ >= 8 && CH_ == 4;
   static constexpr int NT = 32 * NW;           // threads per search
   static constexpr int EPT = 8 * CH;           // bits per thread
@@ -653,8 +650,6 @@ struct Searcher {
     uint32_t fup = 0, rup = 0, fdn = 1u << 21;
     int rdn = 0;
     uint32_t rnd0 = 0, rnd1 = 0;  // 32 MaxMin/PositiveMin draws, one per lane
-    uint4 rr[CH];                 // RandomMin draws of the current iteration
-    bool rr_ready = false;
     const int cwin = n < 32 ? n : 32;
     // RandomMin's floor c = 32/n in units of 2^-16, rounded up
     const uint32_t c16 = ((1u << 21) + (uint32_t)n - 1) / (uint32_t)n;
@@ -917,8 +912,8 @@ struct Searcher {
         } else {  // RANDOMMIN
           uint32_t thr = (uint32_t)(cube_of(fup) >> 16);
           thr = thr < c16 ? c16 : (thr > 65536u ? 65536u : thr);
-          if (!rr_ready) randmin_draw(flips, rr);
-          rr_ready = false;
+          uint4 rr[CH];  // this iteration's draws
+          randmin_draw(flips, rr);
           const uint32_t Cm = mask_of([&](int p) { return randmin_hit(rr, p, thr); }) & F;
           int cmc[CH];
           chunk_min(Cm, cmc);
@@ -975,13 +970,7 @@ struct Searcher {
       row_load(i, xi, rv);
       // independent of row i: overlaps its load latency
       if constexpr (C::EARLY) di = commit(i, xi);
-      if (phase == PH_MAIN) {
-        if (ALGO != TWONEIGHBOR) tabu_push(i, tau);
-        if (C::PREDRAW && ALGO == RANDOMMIN && it + 1 < Tmain) {
-          randmin_draw(flips + 1, rr);  // draws of the next iteration
-          rr_ready = true;
-        }
-      }
+      if (phase == PH_MAIN && ALGO != TWONEIGHBOR) tabu_push(i, tau);
       row_apply(rv, di);
       if constexpr (!C::EARLY) flip_after(i, di, xi);
       if constexpr (NW > 1 && ALGO == TWONEIGHBOR) {
@@ -1030,8 +1019,6 @@ struct Searcher {
     uint32_t fup = 0, rup = 0, fdn = 1u << 21;
     int rdn = 0;
     uint32_t rnd0 = 0, rnd1 = 0;  // 32 MaxMin/PositiveMin draws, one per lane
-    uint4 rr[CH];                 // RandomMin draws of the current iteration
-    bool rr_ready = false;
     const int cwin = n < 32 ? n : 32;
     // RandomMin's floor c = 32/n in units of 2^-16, rounded up
     const uint32_t c16 = ((1u << 21) + (uint32_t)n - 1) / (uint32_t)n;
@@ -1175,8 +1162,8 @@ struct Searcher {
         } else {  // RANDOMMIN
           uint32_t thr = (uint32_t)(cube_of(fup) >> 16);
           thr = thr < c16 ? c16 : (thr > 65536u ? 65536u : thr);
-          if (!rr_ready) randmin_draw(flips, rr);
-          rr_ready = false;
+          uint4 rr[CH];  // this iteration's draws
+          randmin_draw(flips, rr);
           const uint32_t Cm = mask_of([&](int p) { return randmin_hit(rr, p, thr); }) & F;
           int cmc[CH];
           chunk_min(Cm, cmc);
@@ -1201,13 +1188,7 @@ struct Searcher {
       // independent of row i: overlaps its load latency
       int di = sk >> kb;  // groups of warps: from the selection
       if constexpr (C::EARLY) di = commit(i, xi);
-      if (phase == PH_MAIN) {
-        if (ALGO != TWONEIGHBOR) tabu_push(i, tau);
-        if (C::PREDRAW && ALGO == RANDOMMIN && it + 1 < Tmain) {
-          randmin_draw(flips + 1, rr);  // draws of the next iteration
-          rr_ready = true;
-        }
-      }
+      if (phase == PH_MAIN && ALGO != TWONEIGHBOR) tabu_push(i, tau);
       row_apply(rv, di);
       if constexpr (!C::EARLY) flip_after(i, di, xi);
       if (phase == PH_MAIN && ++it == Tmain) {
