@@ -51,12 +51,13 @@ bool params_ok(const dabs_params* p) {
 // band on this GPU (n <= 256, 512, 1024, 2048, 4096, 8192, 16384).  Alone
 // (one instance's searches, about one wave), 4 warps x 4 chunks is fastest
 // for 2048 < n <= 4096; with many instances in flight (batched, served) 8
-// warps x 2 chunks is: twice the warps per SM hide more of the per-flip
-// latency (measured on 64 instances of n in [256, 4096]: 12% less time per
-// generation).  Server admission (batch.cu) counts warps with the second order.
+// warps x 2 chunks is, and 8 warps x 1 chunk for 1024 < n <= 2048: more
+// warps per SM hide more of the per-flip latency (measured on 64 instances
+// of n in [256, 4096]: 12% and 3% less time per generation).  Server
+// admission (batch.cu) counts warps with the second order.
 bool default_variant(int n, SearchVariant* v, bool many) {
   static const int alone[][2] = {{1, 1}, {1, 2}, {1, 4}, {4, 2}, {4, 4}, {8, 4}, {16, 4}};
-  static const int batched[][2] = {{1, 1}, {1, 2}, {1, 4}, {4, 2}, {8, 2}, {8, 4}, {16, 4}};
+  static const int batched[][2] = {{1, 1}, {1, 2}, {1, 4}, {8, 1}, {8, 2}, {8, 4}, {16, 4}};
   for (auto& o : many ? batched : alone) {
     SearchVariant q;
     if (launch_search(o[0], o[1], nullptr, nullptr, &q) && q.cap >= n) {
