@@ -198,11 +198,16 @@ void dabs_batch_destroy(dabs_batch* b);
 /* ---- served form: request queue with continuous batching ----------------
  * A server owns a queue of solve requests.  dabs_server_step admits queued
  * requests (first come, first served) while the device bytes of their
- * contexts fit the HBM budget, advances every admitted request by the given
- * number of generations in batched form, then retires finished requests and
- * frees their device memory, so requests that arrive while others run join
- * at the next round.  Each request's result equals dabs_solve alone.
- * Latency = completion (detected at the end of a round) minus submission. */
+ * contexts fit the HBM budget and advances the admitted ones in rounds of
+ * the given number of generations in batched form.  Requests run in two
+ * size classes (n <= 2048, n > 2048), each with its own stream and rounds,
+ * so small requests are not held at the pace of the largest one's
+ * generations; requests that arrive while a class's round runs join at its
+ * next round.  A finished request's context is kept and reused (a new W
+ * loaded into it) by a later request of the same n and parameters, and
+ * freed when the budget needs its bytes.  Each request's result equals
+ * dabs_solve alone.  Latency = completion (detected at the end of a round)
+ * minus submission. */
 typedef struct dabs_server dabs_server;
 int dabs_server_create(size_t hbm_budget_bytes, dabs_server** out);
 void dabs_server_destroy(dabs_server* s);
@@ -210,7 +215,10 @@ void dabs_server_destroy(dabs_server* s);
  * request alone exceeds the budget or n > DABS_N_MAX.  Does not block. */
 int dabs_server_submit(dabs_server* s, const int16_t* W, int32_t n, const dabs_params* p,
                        uint64_t budget, uint64_t seed, int64_t target, uint64_t* ticket);
-/* One scheduling round (synchronous); *pending = queued + running requests. */
+/* One scheduling step: retires the requests of every class whose round has
+ * ended, admits queued requests and starts a round in every class with work
+ * and none in flight; when no round had ended, it first waits for one (so
+ * every call advances the solve).  *pending = queued + running requests. */
 int dabs_server_step(dabs_server* s, int32_t generations, int32_t* pending);
 /* status: 0 queued, 1 running, 2 done (outputs written, best_X n bytes),
  * negative = the request failed with that DABS_E_* code. */

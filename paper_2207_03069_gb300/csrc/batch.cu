@@ -14,6 +14,8 @@
 // contexts freed as they finish.
 #include <algorithm>
 #include <chrono>
+#include <cstring>
+#include <thread>
 #include <deque>
 #include <new>
 #include <map>
@@ -637,15 +639,38 @@ size_t ctx_bytes(int32_t n, const dabs_params& p) {
 
 }  // namespace
 
+// A size class of requests advanced together: its own batcher (and stream),
+// the requests it runs, those admitted while its generation was in flight,
+// and that generation's end event (after the copies of the control blocks).
+// Small and large requests sit in different classes, so the small ones are
+// not held at the pace of the largest one's generations: the classes' rounds
+// overlap on the GPU.
+struct ServeClass {
+  Batcher batch;
+  std::vector<Request*> running;  // in batch.active order
+  std::vector<Request*> joining;
+  bool dirty = false, inflight = false;
+  cudaEvent_t ev = nullptr;
+};
+
+constexpr int kServeClasses = 3;
+int serve_class(int32_t n) { return n <= 2048 ? 0 : (n <= 4096 ? 1 : 2); }
+
 struct dabs_server {
-  size_t budget = 0, used = 0;
+  size_t budget = 0, used = 0;  // device bytes of running and idle contexts
   int64_t max_warps = 0, running_warps = 0;
   uint64_t next = 1;
   std::deque<Request*> queue;
-  std::vector<Request*> running;
   std::map<uint64_t, std::unique_ptr<Request>> all;
-  Batcher batch;
-  bool dirty = false;
+  ServeClass cls[kServeClasses];
+  // contexts of finished requests, kept for the next request of the same n
+  // and parameters (a new W is loaded into them); freed when the budget needs
+  // their bytes, so that a retirement does not wait on the device
+  struct Idle {
+    dabs_ctx* ctx;
+    size_t bytes;
+  };
+  std::deque<Idle> idle;
 };
 
 extern "C" int dabs_server_create(size_t hbm_budget_bytes, dabs_server** out) {
@@ -660,10 +685,13 @@ extern "C" int dabs_server_create(size_t hbm_budget_bytes, dabs_server** out) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   s->max_warps = 2LL * 32 * (sms > 0 ? sms : 152);  // about two full waves of warps
-  const int rc = s->batch.init();
-  if (rc) {
-    delete s;
-    return rc;
+  for (ServeClass& c : s->cls) {
+    int rc = c.batch.init();
+    if (!rc) rc = check(cudaEventCreateWithFlags(&c.ev, cudaEventDisableTiming));
+    if (rc) {
+      dabs_server_destroy(s);
+      return rc;
+    }
   }
   *out = s;
   return DABS_OK;
@@ -671,9 +699,12 @@ extern "C" int dabs_server_create(size_t hbm_budget_bytes, dabs_server** out) {
 
 extern "C" void dabs_server_destroy(dabs_server* s) {
   if (!s) return;
-  s->batch.sync_all();
+  for (ServeClass& c : s->cls) c.batch.sync_all();
   for (auto& kv : s->all)
     if (kv.second->ctx) dabs_destroy(kv.second->ctx);
+  for (auto& i : s->idle) dabs_destroy(i.ctx);
+  for (ServeClass& c : s->cls)
+    if (c.ev) cudaEventDestroy(c.ev);
   delete s;
 }
 
@@ -702,79 +733,174 @@ extern "C" int dabs_server_submit(dabs_server* s, const int16_t* W, int32_t n, c
   return DABS_OK;
 }
 
-// One scheduling round: admit queued requests while the HBM budget allows,
-// advance every running request by `generations` generations (batched), then
-// retire the finished ones and free their device memory.  *pending receives
-// the number of queued plus running requests.
-extern "C" int dabs_server_step(dabs_server* s, int32_t generations, int32_t* pending) {
-  if (!s || generations < 1) return DABS_E_INVALID_ARG;
-  int rc = DABS_OK;
-  // first come, first served while the HBM budget holds and the running
-  // searches do not exceed the warp cap (admitting every waiting request at
-  // once would only share the GPU among them and delay all of them)
-  while (!s->queue.empty() && s->used + s->queue.front()->bytes <= s->budget &&
-         (s->running.empty() || s->max_warps <= 0 ||
-          s->running_warps + s->queue.front()->warps <= s->max_warps)) {
+namespace {
+
+bool same_params(const dabs_params& a, const dabs_params& b) {
+  return std::memcmp(&a, &b, sizeof(dabs_params)) == 0;
+}
+
+// retires the finished requests of every class whose generation has ended
+// (wait: block until one has); returns how many classes ended
+int serve_collect(dabs_server* s, bool wait, int* ended) {
+  *ended = 0;
+  for (;;) {
+    for (ServeClass& c : s->cls) {
+      if (!c.inflight) continue;
+      const cudaError_t q = cudaEventQuery(c.ev);
+      if (q == cudaErrorNotReady) continue;
+      int rc = check(q);
+      if (rc) return rc;
+      c.inflight = false;
+      ++*ended;
+      c.batch.collect_search_time();
+      std::vector<Request*> still;
+      for (Request* r : c.running) {
+        dabs_ctx* x = r->ctx;
+        if (!x->h_ctrl->done) {  // copied after the generation
+          still.push_back(r);
+          continue;
+        }
+        const uint64_t flips = x->h_ctrl->flips_total;
+        r->best_X.resize(r->n);
+        x->stream = x->own;
+        rc = dabs_solve_best(x, r->best_X.data(), &r->best_E);
+        r->flips = flips;
+        r->t_done = now_s();
+        r->state = rc ? rc : 2;
+        r->ctx = nullptr;
+        s->idle.push_back({x, r->bytes});
+        s->running_warps -= r->warps;
+        r->W.clear();
+        r->W.shrink_to_fit();
+        c.dirty = true;
+      }
+      c.running.swap(still);
+    }
+    if (*ended || !wait) return DABS_OK;
+    bool any = false;
+    for (ServeClass& c : s->cls) any = any || c.inflight;
+    if (!any) return DABS_OK;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+// admits queued requests, first come first served, while their bytes fit the
+// budget (idle contexts freed oldest first to make room) and the warp cap
+// holds; a context of the same n and parameters is reused
+int serve_admit(dabs_server* s) {
+  for (;;) {
+    if (s->queue.empty()) return DABS_OK;
     Request* r = s->queue.front();
+    int nrun = 0;
+    for (ServeClass& c : s->cls) nrun += (int)(c.running.size() + c.joining.size());
+    if (nrun > 0 && s->max_warps > 0 && s->running_warps + r->warps > s->max_warps) return DABS_OK;
+    // a reusable context: its bytes are already counted
+    dabs_ctx* x = nullptr;
+    for (size_t i = 0; i < s->idle.size(); ++i)
+      if (s->idle[i].ctx->n == r->n && same_params(s->idle[i].ctx->p, r->p)) {
+        x = s->idle[i].ctx;
+        s->idle.erase(s->idle.begin() + (long)i);
+        break;
+      }
+    if (!x) {
+      while (s->used + r->bytes > s->budget && !s->idle.empty()) {
+        dabs_destroy(s->idle.front().ctx);
+        s->used -= s->idle.front().bytes;
+        s->idle.pop_front();
+      }
+      if (s->used + r->bytes > s->budget) return DABS_OK;
+    }
     s->queue.pop_front();
-    rc = dabs_create(r->W.data(), r->n, &r->p, &r->ctx);
+    int rc;
+    if (x) {
+      rc = dabs_load_weights(x, r->W.data());
+      if (rc) {
+        dabs_destroy(x);
+        s->used -= r->bytes;
+        x = nullptr;
+      }
+    }
+    if (!x) {
+      rc = dabs_create(r->W.data(), r->n, &r->p, &x);
+      if (rc) {
+        r->state = rc;
+        r->t_done = now_s();
+        continue;
+      }
+      s->used += r->bytes;
+    }
+    // the solve starts on the context's own stream; then it joins its class
+    rc = dabs_solve_begin(x, r->seed, r->budget, r->target);
+    if (!rc) rc = check(cudaStreamSynchronize(x->own));
     if (rc) {
       r->state = rc;
       r->t_done = now_s();
+      s->idle.push_back({x, r->bytes});
       continue;
     }
-    cudaStreamSynchronize(r->ctx->stream);
-    r->ctx->stream = s->batch.stream;
-    if ((rc = dabs_solve_begin(r->ctx, r->seed, r->budget, r->target))) {
-      r->state = rc;
-      dabs_destroy(r->ctx);
-      r->ctx = nullptr;
-      continue;
-    }
+    ServeClass& c = s->cls[serve_class(r->n)];
+    x->stream = c.batch.stream;
+    r->ctx = x;
     r->state = 1;
     r->t_start = now_s();
-    s->used += r->bytes;
     s->running_warps += r->warps;
-    s->running.push_back(r);
-    s->dirty = true;
+    c.joining.push_back(r);
   }
-  if (!s->running.empty()) {
-    if (s->dirty) {
-      s->batch.active.clear();
-      for (Request* r : s->running) s->batch.active.push_back(r->ctx);
-      if ((rc = s->batch.rebuild())) return rc;
-      s->dirty = false;
+}
+
+// starts `generations` generations in every class with work and none in flight
+int serve_launch(dabs_server* s, int generations) {
+  int rc;
+  for (ServeClass& c : s->cls) {
+    if (c.inflight) continue;
+    if (!c.joining.empty()) {
+      c.running.insert(c.running.end(), c.joining.begin(), c.joining.end());
+      c.joining.clear();
+      c.dirty = true;
+    }
+    if (c.running.empty()) continue;
+    if (c.dirty) {
+      c.batch.active.clear();
+      for (Request* r : c.running) c.batch.active.push_back(r->ctx);
+      if ((rc = c.batch.rebuild())) return rc;
+      c.dirty = false;
     }
     for (int q = 0; q < generations; ++q)
-      if ((rc = s->batch.generation())) return rc;
-    std::vector<DevCtrl> cs;
-    if ((rc = read_done(s->batch.active, cs, s->batch.stream))) return rc;
-    s->batch.collect_search_time();
-    std::vector<Request*> still;
-    for (size_t i = 0; i < s->running.size(); ++i) {
-      Request* r = s->running[i];
-      if (!cs[i].done) {
-        still.push_back(r);
-        continue;
-      }
-      r->best_X.resize(r->n);
-      dabs_ctx* c = r->ctx;
-      c->stream = c->own;
-      rc = dabs_solve_best(c, r->best_X.data(), &r->best_E);
-      r->flips = cs[i].flips_total;
-      r->t_done = now_s();
-      r->state = rc ? rc : 2;
-      dabs_destroy(c);
-      r->ctx = nullptr;
-      s->used -= r->bytes;
-      s->running_warps -= r->warps;
-      r->W.clear();
-      r->W.shrink_to_fit();
-      s->dirty = true;
-    }
-    s->running.swap(still);
+      if ((rc = c.batch.generation())) return rc;
+    for (Request* r : c.running)
+      if ((rc = check(cudaMemcpyAsync(r->ctx->h_ctrl, r->ctx->ctrl, sizeof(DevCtrl),
+                                      cudaMemcpyDeviceToHost, c.batch.stream))))
+        return rc;
+    if ((rc = check(cudaEventRecord(c.ev, c.batch.stream)))) return rc;
+    c.inflight = true;
   }
-  if (pending) *pending = (int32_t)(s->queue.size() + s->running.size());
+  return DABS_OK;
+}
+
+}  // namespace
+
+// One scheduling step: retire the requests of every class whose round has
+// ended, admit queued requests, and start a round of `generations`
+// generations in every class with work and no round in flight.  When no
+// round had ended, the step first waits for one, so every call advances the
+// solve; rounds of different classes overlap on the device.  *pending
+// receives the number of queued plus running requests.
+extern "C" int dabs_server_step(dabs_server* s, int32_t generations, int32_t* pending) {
+  if (!s || generations < 1) return DABS_E_INVALID_ARG;
+  int ended = 0, rc;
+  if ((rc = serve_collect(s, false, &ended))) return rc;
+  if ((rc = serve_admit(s))) return rc;
+  if ((rc = serve_launch(s, generations))) return rc;
+  if (!ended) {
+    if ((rc = serve_collect(s, true, &ended))) return rc;
+    if ((rc = serve_admit(s))) return rc;
+    if ((rc = serve_launch(s, generations))) return rc;
+  }
+  if (pending) {
+    size_t p = s->queue.size();
+    for (ServeClass& c : s->cls) p += c.running.size() + c.joining.size();
+    *pending = (int32_t)p;
+  }
   return DABS_OK;
 }
 
@@ -806,6 +932,10 @@ extern "C" int dabs_server_info(const dabs_server* s, size_t* used_bytes, int32_
   if (!s) return DABS_E_INVALID_ARG;
   if (used_bytes) *used_bytes = s->used;
   if (queued) *queued = (int32_t)s->queue.size();
-  if (running) *running = (int32_t)s->running.size();
+  if (running) {
+    size_t r = 0;
+    for (const ServeClass& c : s->cls) r += c.running.size() + c.joining.size();
+    *running = (int32_t)r;
+  }
   return DABS_OK;
 }
