@@ -174,6 +174,22 @@ struct Searcher {
   // Eq. (5) at a run-time position after the row update (groups of warps,
   // where Delta_i is known to every thread): d = v, sigma flips
   __device__ __forceinline__ void set_flipped(int p, int v) {
+    if constexpr (NW > 1 && EPT <= 16) {
+      // groups of warps: the other warps wait for this write at the next
+      // round, so no indirect branch (a jump table costs over a hundred
+      // cycles with one active lane) -- a select per register instead (with
+      // 32 registers per thread the selects cost more than the branch)
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const bool hit = q == p;
+        d[q] = hit ? v : d[q];
+        if constexpr (C::SG8)
+          sg[q / 4] ^= hit ? (int)(0xFEu << (8 * (q % 4))) : 0;
+        else
+          sg[q] = hit ? -sg[q] : sg[q];
+      }
+      return;
+    }
     switch (p) {
 #define DABS_SET(q)                         \
   case q:                                   \
