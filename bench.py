@@ -170,6 +170,14 @@ def l2_copy_gbs(torch, dev):
     return 2 * a.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
 
 
+def rows_from_l2(wset, l2_size, traffic, row_bytes):
+    """Where the flip kernel's rows come from: the L2 when W and -W fit it, or
+    when the captured DRAM traffic of the search launches (bytes, None when
+    no capture matches the kernel) is under a quarter of the row bytes they
+    read (the instances searched at one time fit the L2 together)."""
+    return wset <= l2_size or (traffic is not None and traffic < 0.25 * row_bytes)
+
+
 def l2_read_gbs(torch, dev, mib=64, reps=20):
     """Read bandwidth of a buffer that stays in L2 (64 MiB of the 129 MB L2),
     measured by the library's read kernel (dabs_measure_read_gbs): the L2 peak
@@ -742,10 +750,7 @@ def run_batched(args, ws, rank, lrank, pg):
     alu_peak = sms * 4 * 16 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6
     prof = search_profile("search_batched64.json")
     traffic = prof.get("dram_bytes_per_generation") if prof else None
-    # where the rows come from: the L2 when W fits it, or when the captured
-    # DRAM traffic of the search launches is a small part of the row bytes
-    # they read (the instances searched at one time fit the L2 together)
-    from_l2 = wset <= l2_size or (traffic is not None and traffic < 0.25 * row_bytes)
+    from_l2 = rows_from_l2(wset, l2_size, traffic, row_bytes)
     bound = "l2" if from_l2 else "hbm"
     peak = l2 if from_l2 else hbm
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -1,7 +1,8 @@
-"""Host side of the served workload in the benchmark (CPU): the request trace
-is reproducible, the same request index carries the same instance and solve
+"""Host side of the benchmark (CPU): the served workload's request trace is
+reproducible, the same request index carries the same instance and solve
 seed at every arrival rate (so targets computed once serve every rate), the
-instances come from a bounded catalog, and the large request lands mid-trace."""
+instances come from a bounded catalog, and the large request lands
+mid-trace; the roofline's choice of the memory the rows come from."""
 import os
 import sys
 
@@ -49,3 +50,11 @@ def test_large_request_mid_trace():
     big = [q for q in reqs if q[1] == 16384]
     assert len(big) == 1 and big[0][0] == 2.0
     assert [q[0] for q in reqs] == sorted(q[0] for q in reqs)
+
+
+def test_rows_from_l2():
+    L2 = 135_528_448
+    assert bench.rows_from_l2(4 * 800 * 800, L2, None, 13e9)          # W fits the L2
+    assert not bench.rows_from_l2(673_181_040, L2, None, 96e9)       # too big, no capture
+    assert bench.rows_from_l2(673_181_040, L2, 1.5e9, 96e9)          # captured: DRAM 1.6% of rows
+    assert not bench.rows_from_l2(673_181_040, L2, 40e9, 96e9)       # rows streamed from HBM
