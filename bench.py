@@ -90,13 +90,23 @@ def search_profile(fname="search_maxcut800.json"):
         return None
     with open(path) as f:
         prof = json.load(f)
-    h = hashlib.sha256()
-    for fn in ("search.cuh", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_2207_03069_gb300", "csrc", fn), "rb") as f:
-            h.update(f.read())
-    if prof.get("kernel_sha256") != h.hexdigest():
+    if prof.get("kernel_sha256") != kernel_hash():
         return None
     return prof
+
+
+def kernel_hash():
+    """sha256 of the search kernel's source (search.cuh, common.cuh) without
+    its // comments and blank lines: a capture stays valid across comment
+    edits, not across code changes."""
+    h = hashlib.sha256()
+    for fn in ("search.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2207_03069_gb300", "csrc", fn), encoding="utf-8") as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
+    return h.hexdigest()
 
 
 class ClockSampler:

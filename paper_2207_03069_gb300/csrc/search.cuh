@@ -5,9 +5,10 @@
 // phase's selector), Step 3 (E += Delta_i, Delta_k += W_ik sigma(x_i) sigma(x_k)
 // for k != i by Eq. (4), Delta_i = -Delta_i by Eq. (5)).
 //
-// The phases (Straight, Greedy, main search) run in one loop with a single
-// reduction site for Step 1 and a single flip site, which keeps the kernel's
-// code small (instruction-cache friendly) whatever the algorithm mix.
+// The phases (Straight, Greedy, main search) run in one loop per main
+// algorithm (run_algo / run_key are templates on it), with one flip site;
+// the launch order groups a launch's slots by algorithm, so an SM mostly runs
+// one loop body (instruction cache).
 //
 // Register layout: thread t of a group (NT = 32 NW threads) owns, for chunk
 // c = 0..CH-1, the eight consecutive bits k = c*8*NT + 8t + e (e = 0..7).  One
@@ -22,9 +23,13 @@
 // second pass finds the arg-min.
 //
 // Reductions use the warp reduce instructions and, for NW > 1, one
-// shared-memory slot round per reduction (double-buffered, one barrier).
-// Ties resolve to the lowest bit index (CyclicMin: the first bit in cyclic
-// order from the window start).
+// shared-memory slot round per reduction (double-buffered, one barrier), in
+// which lane w reads warp w's slot and a second warp reduction combines
+// them.  Ties resolve to the lowest bit index (CyclicMin: the first bit in
+// cyclic order from the window start).
+//
+// sigma(x_k) is one register per bit, or (4-chunk variants of 8 and 16
+// warps, held to 128 registers) four signed bytes per register.
 #pragma once
 #include "common.cuh"
 #include "kernels.cuh"
