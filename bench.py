@@ -782,6 +782,11 @@ def run_batched(args, ws, rank, lrank, pg):
                         "algorithmic_lane_ops_per_flip": "2n (Step 1 compare, Eq. (4) multiply-add)",
                         "frac_algorithmic": sum(f * 2 * n for f, n in zip(per_inst, ns))
                         / (sum(step_ms) * 1e-3) / alu_peak}}
+    cap8 = (prof or {}).get("capture_8x2_full") or {}
+    if cap8.get("pipe_pct_of_peak"):
+        # the dominant launch's pipe use from the same capture: the bound that binds
+        roofline["alu"]["alu_pipe_pct_of_peak_ncu"] = cap8["pipe_pct_of_peak"].get("alu")
+        roofline["alu"]["ncu_launch"] = "k_batch_search<8, 2> (2048 < n <= 4096), one launch"
 
     # ---------------- end to end through the C ABI with host buffers
     pinned = []
